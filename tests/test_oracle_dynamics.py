@@ -1,0 +1,147 @@
+"""Pins of the oracle's Markov chain (Eq. 8, Eq. 9, Sec. 4.2) against exact
+enumeration, limits with closed-form outcomes and exchange statistics."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import Oracle, philox4x32_10
+from oracle.enumerate import exact_averages
+from oracle.jstar import jstar, jtot
+
+
+def _binned(x, nbins=50):
+    x = np.asarray(x)
+    b = x[: (x.size // nbins) * nbins].reshape(nbins, -1).mean(axis=1)
+    return b.mean(), b.std(ddof=1) / math.sqrt(nbins)
+
+
+@pytest.mark.parametrize("L,q,sigma,c,ratios", [
+    (8, 3, 0.5, 2, (0.08, 0.15, 0.3, 0.6)),
+    (10, 2, 0.8, 1, (0.1, 0.2, 0.4, 0.8)),
+])
+def test_pt_matches_exact_enumeration(L, q, sigma, c, ratios):
+    """PT chains sample exp(-beta H): <E>, <E^2>, <M>, <M^2> per slot agree with
+    exact enumeration over all q^L states within 3 binned standard errors."""
+    J = jstar(L, sigma)
+    temps = np.array(ratios) * jtot(L, sigma)
+    o = Oracle(L, q, sigma, temps, seed=12345, c=c)
+    burn, nmeas = 500, 60_000
+    for _ in range(burn):
+        o.step()
+    E = np.zeros((nmeas, o.R))
+    M = np.zeros((nmeas, o.R))
+    for n in range(nmeas):
+        o.step()
+        E[n] = o.running_energy()
+        M[n] = o.magnetisation()
+    ex = exact_averages(L, q, J, c, 1.0 / temps)
+    # the binned SE is floored by sqrt(Var/N) from the exact variance: a cold
+    # slot that never leaves its ground state has a zero sample variance
+    var = {"E": ex["E2"] - ex["E"] ** 2, "M": ex["M2"] - ex["M"] ** 2}
+    for t in range(o.R):
+        for name, series in (("E", E[:, t]), ("E2", E[:, t] ** 2), ("M", M[:, t]), ("M2", M[:, t] ** 2)):
+            mean, se = _binned(series)
+            base = name[0]
+            scale = abs(2 * ex[base][t]) if name.endswith("2") else 1.0
+            se = max(se, scale * math.sqrt(max(var[base][t], 0.0) / nmeas))
+            assert abs(mean - ex[name][t]) < 3.0 * se + 1e-12, (t, name, mean, ex[name][t], se)
+    st = o.stats()
+    assert st["near_metro"].sum() == 0 and st["near_exch"] == 0
+    assert np.all(st["acc_swap"] > 0)
+    # running energy bookkeeping equals the plain double sum
+    np.testing.assert_allclose(o.running_energy(), o.energy(), rtol=1e-11, atol=1e-11)
+
+
+def test_infinite_temperature_follows_generator():
+    """beta -> 0: every proposal is accepted (u <= 1 = exp(-0)), so one sweep
+    maps s_k to b_k = (a + 1 + floor(x0 (q-1) / 2^32)) mod q with x0 the first
+    Philox word of counter (k, t, 0, 1)."""
+    L, q, R, seed = 50, 5, 3, 777
+    o = Oracle(L, q, 0.5, np.full(R, 1e300), seed=seed)
+    s0 = o.spins()
+    o.sweep(1, mode="direct")
+    key = np.array([seed & 0xFFFFFFFF, seed >> 32], np.uint32)
+    exp = s0.copy()
+    for t in range(R):
+        for k in range(L):
+            x0 = int(philox4x32_10(np.array([k, t, 0, 1], np.uint32), key)[0])
+            exp[t, k] = (int(exp[t, k]) + 1 + ((x0 * (q - 1)) >> 32)) % q
+    np.testing.assert_array_equal(o.spins(), exp)
+    assert o.stats()["acc_flip"].tolist() == [L] * R
+
+
+def test_initial_spins_follow_generator():
+    """Initial spins are floor(x0 q / 2^32) of Philox counter (i, t, 0, 0)."""
+    L, q, R, seed = 40, 7, 2, 2**40 + 5
+    o = Oracle(L, q, 0.3, np.ones(R), seed=seed)
+    key = np.array([seed & 0xFFFFFFFF, seed >> 32], np.uint32)
+    exp = np.array([[(int(philox4x32_10(np.array([i, t, 0, 0], np.uint32), key)[0]) * q) >> 32
+                     for i in range(L)] for t in range(R)], dtype=np.uint8)
+    np.testing.assert_array_equal(o.spins(), exp)
+
+
+@pytest.mark.parametrize("c", [1, 2])
+def test_zero_temperature_ground_state_is_frozen(c):
+    """beta -> infinity from the ordered state: every flip costs dE = c Jtot > 0,
+    so nothing is ever accepted and E stays -(c/2) L Jtot."""
+    L, q, sigma = 64, 4, 0.6
+    o = Oracle(L, q, sigma, np.full(2, 1e-6), seed=5, c=c)
+    o.set_spins(np.zeros((2, L), np.uint8))
+    for _ in range(20):
+        o.step(mode="direct")
+    assert np.all(o.spins() == 0)
+    assert o.stats()["acc_flip"].sum() == 0
+    np.testing.assert_allclose(o.energy(), -0.5 * c * L * jtot(L, sigma), rtol=1e-12)
+
+
+@pytest.mark.parametrize("c", [1, 2])
+def test_infinite_temperature_mean_energy(c):
+    """beta = 0: spins are uniform and independent, <E> = -(c/2) (L/q) Jtot."""
+    L, q, sigma = 48, 3, 0.5
+    o = Oracle(L, q, sigma, np.full(4, 1e300), seed=9, c=c)
+    E = []
+    for _ in range(3000):
+        o.sweep(1)
+        E.append(o.running_energy())
+    E = np.array(E).ravel()
+    mean, se = _binned(E)
+    assert abs(mean - (-0.5 * c * L * jtot(L, sigma) / q)) < 3 * se
+
+
+def test_field_mode_equals_direct_mode():
+    """Incremental local fields and the direct O(L) sum give the same chain."""
+    L, q, sigma = 64, 3, 0.5
+    temps = np.geomspace(0.05, 1.0, 8) * jtot(L, sigma)
+    a = Oracle(L, q, sigma, temps, seed=1)
+    b = Oracle(L, q, sigma, temps, seed=1)
+    for _ in range(200):
+        a.step(mode="field")
+        b.step(mode="direct")
+    np.testing.assert_array_equal(a.spins(), b.spins())
+    np.testing.assert_allclose(a.running_energy(), b.running_energy(), rtol=1e-11)
+    np.testing.assert_allclose(a.fields().sum(axis=1), jtot(L, sigma), rtol=1e-11)
+    assert a.stats()["near_metro"].sum() == 0
+
+
+def test_exchange_acceptance_rate():
+    """Two slots, no sweeps: from the state with D < 0 a swap is accepted with
+    probability p = exp(D), after which D > 0 and the next swap always returns.
+    The long-run accepted fraction is 2p / (1 + p) (Eq. 9); a flipped sign in D
+    would give p = 1."""
+    L, q, sigma = 16, 3, 0.5
+    rng = np.random.default_rng(0)
+    S = np.stack([np.zeros(L, np.uint8), rng.integers(0, q, L).astype(np.uint8)])
+    o = Oracle(L, q, sigma, np.array([1.0, 3.0]), seed=4)
+    o.set_spins(S)  # slot 0 (cold) holds the ground state: D < 0
+    E = o.running_energy()
+    D = (1.0 - 1.0 / 3.0) * (E[0] - E[1])
+    assert D < 0
+    p = math.exp(D)
+    n = 40_000
+    for _ in range(n):
+        o.exchange()
+    st = o.stats()
+    frac = st["acc_swap"][0] / st["att_swap"][0]
+    expect = 2 * p / (1 + p)
+    assert abs(frac - expect) < 4 * math.sqrt(expect * (1 - expect) / n) + 1e-3, (frac, expect)
