@@ -1,0 +1,380 @@
+"""Benchmark: spin-flip attempts/s of parallel-tempering Metropolis on the
+long-range q-state Potts chain (arXiv:1308.5426), one JSON line on rank 0.
+
+Default workload: eight independent plain-FP64 PT chains, L=1024, q=5,
+sigma=0.4, R=64 temperatures geometric in T/Jtot in [0.05, 1], seeds 1..8,
+energy and magnetisation measured every 10 sweeps.  One step = 10 x (one sweep
+of every slot + one exchange step) + one measurement, over all 8 chains.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload chains|precision]
+
+--impl reference times the CPU oracle (plain C, FP64, local-field mode) on
+the host cores on a bounded sample of the same workload.
+Under torchrun (N > 1) every rank runs its own eight chains (seeds offset by
+8 x rank): the chains are independent, so the work shards with no data-path
+collective and the scaling is weak.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SWEEPS_PER_STEP = 10
+L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="chains", choices=["chains", "precision"])
+    ap.add_argument("--precision", default=None, choices=[None, "fp64", "fp32"])
+    ap.add_argument("--no-fp32-compare", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_specs(name, rank, precision):
+    from paper_1308_5426_gb300 import workloads
+    if name == "chains":
+        specs = workloads.chains_jobs()
+        for s in specs:
+            s.seed += 8 * rank
+            s.precision = precision or "fp64"
+        desc = {"workload": "8 independent PT chains, L=1024 q=5 sigma=0.4 R=64, T/Jtot geometric 0.05-1, "
+                            "exchange every sweep, E/M every 10 sweeps",
+                "L": 1024, "q": 5, "sigma": 0.4, "R": 64, "chains": 8}
+    else:
+        s = workloads.precision_job(precision or "fp32")
+        s.seed += rank
+        specs = [s]
+        desc = {"workload": "one PT job, L=4096 q=8 sigma=0.2 R=128, T/Jtot geometric 0.02-0.5, "
+                            "exchange every sweep, E/M every 10 sweeps, FP32 rebuild every 100 sweeps",
+                "L": 4096, "q": 8, "sigma": 0.2, "R": 128, "chains": 1}
+    return specs, desc
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- peaks
+def peaks():
+    p = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+    except (OSError, ValueError):
+        pass
+    return p
+
+
+def alu_peak(kind, sm_max_mhz):
+    """ALU peaks from unit counts and the maximum SM clock: 152 SMs; FP32: 128
+    lanes/clk/SM; FP64: the nominal 1.25 TFLOP/s of GB300 is 2 FMA/clk/SM at
+    2070 MHz, i.e. 2 FP64 adds/clk/SM."""
+    f = (sm_max_mhz or 2070.0) * 1e6
+    lanes = {"fp64": 2.0, "fp32": 128.0}[kind]
+    return 152 * lanes * f  # adds per second
+
+
+# ----------------------------------------------------------------- CPU baseline
+def cpu_baseline(specs, seconds):
+    """The oracle as it stands (local-field mode, FP64), one replica per POSIX
+    thread over all host cores, on a bounded sample: the first chain, as many
+    sweeps as fit in about `seconds`."""
+    import oracle
+    s = specs[0]
+    temps = s.ratios * oracle.jtot(s.L, s.sigma)
+    cores = os.cpu_count() or 1
+    o = oracle.Oracle(s.L, s.q, s.sigma, temps, s.seed)
+    t0 = time.perf_counter()
+    o.step(mode="field", nthreads=cores)
+    t1 = time.perf_counter()
+    per = max(t1 - t0, 1e-4)
+    n = max(1, min(2000, int(seconds / per)))
+    t0 = time.perf_counter()
+    for _ in range(n):
+        o.step(mode="field", nthreads=cores)
+    dt = time.perf_counter() - t0
+    att = n * s.L * s.R
+    return {"value": att / dt, "unit": "attempts/s", "cores": cores, "kind": "oracle",
+            "sample": "chain 1 of the workload (L=%d q=%d R=%d), %d sweeps + exchanges, FP64 local-field "
+                      "mode, %.1f s" % (s.L, s.q, s.R, n, dt)}
+
+
+def run_reference(args, specs, desc, rank, world):
+    """--impl reference: the CPU oracle, K steps, each a bounded sample."""
+    if rank != 0:
+        return 0
+    import oracle
+    s = specs[0]
+    temps = s.ratios * oracle.jtot(s.L, s.sigma)
+    cores = os.cpu_count() or 1
+    o = oracle.Oracle(s.L, s.q, s.sigma, temps, s.seed)
+    for _ in range(args.warmup):
+        o.step(mode="field", nthreads=cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(mode="field", nthreads=cores)
+    dt = time.perf_counter() - t0
+    att = args.steps * s.L * s.R
+    v = att / dt
+    line = {"impl": "reference", "metric": "spin-flip attempts/s", "value": v, "unit": "attempts/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": desc,
+            "cpu_baseline": {"value": v, "unit": "attempts/s", "cores": cores, "kind": "oracle",
+                             "sample": "each step: one sweep + exchange of chain 1 (L=%d q=%d R=%d), FP64 "
+                                       "local-field mode, %d threads" % (s.L, s.q, s.R, cores)},
+            "e2e": {"value": v, "unit": "attempts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------- GPU arm
+def make_jobs(plr, specs, stream):
+    return [plr.Job(s.L, s.q, s.sigma, s.ratios * plr.jtot(s.L, s.sigma), s.seed, precision=s.precision,
+                    stream=stream) for s in specs]
+
+
+def timed_device(plr, torch, specs, steps, warmup, dev, with_events=True):
+    st = torch.cuda.Stream(device=dev)
+    jobs = make_jobs(plr, specs, st.cuda_stream)
+    batch = plr.Batch(jobs, stream=st.cuda_stream)
+    nslots = batch.nslots
+    Eb = torch.empty(nslots, dtype=torch.float64, device=dev)
+    Mb = torch.empty(nslots, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    att_step = SWEEPS_PER_STEP * sum(s.L * s.R for s in specs)
+
+    def step(sweep_ev=None):
+        for _ in range(SWEEPS_PER_STEP):
+            if sweep_ev is not None:
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(st)
+                batch.sweep(1)
+                b.record(st)
+                sweep_ev.append((a, b))
+            else:
+                batch.sweep(1)
+            batch.exchange()
+        batch.measure_device(Eb.data_ptr(), Mb.data_ptr())
+
+    for _ in range(warmup):
+        step()
+    batch.sync()
+    acc0 = sum(int(j.stats()["acc_flip"].sum()) for j in jobs)
+    step_ev, sweep_ev = [], []
+    torch.cuda.synchronize(dev)
+    for _ in range(steps):
+        with torch.cuda.stream(st):
+            flush.zero_()  # L2 flush between timed steps, outside the step's events
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        step(sweep_ev if with_events else None)
+        b.record(st)
+        step_ev.append((a, b))
+    torch.cuda.synchronize(dev)
+    acc1 = sum(int(j.stats()["acc_flip"].sum()) for j in jobs)
+    step_ms = sum(a.elapsed_time(b) for a, b in step_ev)
+    sweep_ms = [a.elapsed_time(b) for a, b in sweep_ev]
+    out = {"step_ms": step_ms, "att_step": att_step, "acceptance": (acc1 - acc0) / (steps * att_step),
+           "sweep_ms": sweep_ms, "steps": steps}
+    batch.close()
+    for j in jobs:
+        j.close()
+    return out
+
+
+def timed_e2e(plr, torch, specs, steps, warmup, dev):
+    """Through the public API with host buffers: each step restores every
+    chain from a pinned host checkpoint (H2D), runs 10 sweeps + exchanges,
+    measures into host arrays (D2H) and checkpoints back (D2H)."""
+    st = torch.cuda.Stream(device=dev)
+    jobs = make_jobs(plr, specs, st.cuda_stream)
+    batch = plr.Batch(jobs, stream=st.cuda_stream)
+    sizes = [j.state_size() for j in jobs]
+    bufs = [torch.empty(n, dtype=torch.uint8, pin_memory=True) for n in sizes]
+    for j, b, n in zip(jobs, bufs, sizes):
+        j.get_state_into(b.data_ptr(), n)
+    E = np.zeros(batch.nslots)
+    M = np.zeros(batch.nslots)
+    att_step = SWEEPS_PER_STEP * sum(s.L * s.R for s in specs)
+
+    def step():
+        for j, b, n in zip(jobs, bufs, sizes):
+            j.set_state_from(b.data_ptr(), n)
+        batch.run(SWEEPS_PER_STEP, SWEEPS_PER_STEP)
+        E[:], M[:] = batch.measure()
+        for j, b, n in zip(jobs, bufs, sizes):
+            j.get_state_into(b.data_ptr(), n)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step()
+    torch.cuda.synchronize(dev)
+    dt = time.perf_counter() - t0
+    h2d = sum(sizes)
+    d2h = sum(sizes) + 2 * 8 * batch.nslots
+    batch.close()
+    for j in jobs:
+        j.close()
+    return {"value": steps * att_step / dt, "unit": "attempts/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    specs, desc = workload_specs(args.workload, rank, args.precision)
+    if args.impl == "reference":
+        return run_reference(args, specs, desc, rank, world)
+
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    import paper_1308_5426_gb300 as plr
+    from paper_1308_5426_gb300 import _lib
+    _lib.load()
+
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    res = timed_device(plr, torch, specs, args.steps, args.warmup, dev)
+    ck = clocks.stop()
+    step_ms = res["step_ms"]
+    if world > 1:
+        t = torch.tensor([step_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms = float(t.item())
+    total_att = world * args.steps * res["att_step"]
+    value = total_att / (step_ms / 1e3)
+
+    # roofline of the sweep kernel (the dominant kernel)
+    prec = specs[0].precision
+    A = res["acceptance"]
+    L = specs[0].L
+    att_launch = sum(s.L * s.R for s in specs)
+    sweep_avg_s = float(np.mean(res["sweep_ms"])) / 1e3
+    flops_launch = att_launch * A * 2 * L  # the rank-1 field updates: 2L adds per accepted flip
+    peak_adds = alu_peak(prec, ck.get("sm_max_mhz"))
+    achieved = flops_launch / sweep_avg_s
+    traffic = None
+    roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_adds / 1e12, "unit": "TFLOP/s",
+            "frac": achieved / peak_adds, "traffic": traffic, "kernel": "sweep_kernel<%s>" %
+            ("double" if prec == "fp64" else "float"),
+            "work": "A*2L %s adds per attempt, A=%.4f measured; %d attempts per launch" % (prec, A, att_launch),
+            "peak_source": "unit counts x max SM clock (2 FP64 / 128 FP32 add lanes per SM per clock, 152 SMs)",
+            "sweep_ms_avg": sweep_avg_s * 1e3}
+
+    extra = {}
+    if args.workload == "chains" and not args.no_fp32_compare and prec == "fp64":
+        specs32, _ = workload_specs(args.workload, rank, "fp32")
+        r32 = timed_device(plr, torch, specs32, max(3, args.steps // 3), args.warmup, dev, with_events=False)
+        extra["fp32_same_workload"] = {"value": world * r32["steps"] * r32["att_step"] / (r32["step_ms"] / 1e3),
+                                       "unit": "attempts/s", "acceptance": r32["acceptance"]}
+
+    e2e = timed_e2e(plr, torch, specs, max(3, args.steps // 3), 1, dev)
+    if world > 1:
+        t = torch.tensor([e2e["value"]], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MIN)
+        e2e["value"] = float(t.item()) * world
+
+    if rank == 0:
+        cpu = cpu_baseline(specs, args.cpu_seconds) if world == 1 else None
+        launches = args.steps * (SWEEPS_PER_STEP * 2 + 1)
+        desc = dict(desc)
+        desc["precision"] = prec
+        desc["l2"] = "flushed between timed steps (512 MB write)"
+        desc["parallelism"] = "one CTA per temperature slot; %d slots per GPU" % sum(s.R for s in specs)
+        line = {"metric": "spin-flip attempts/s", "value": value, "unit": "attempts/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if prec == "fp64" else "f32", "data": "synthetic", "config": desc,
+                "clocks": ck, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
+                "cpu_baseline": cpu, "acceptance": A}
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,202 @@
+/*
+ * potts_lr -- parallel-tempering Metropolis simulation of the one-dimensional
+ * q-state Potts chain with long-range periodic couplings, on one GB300 GPU
+ * (sm_103a).  C ABI: plain pointers and sizes, no C++ or framework types.
+ *
+ * The model (A. Boer, arXiv:1308.5426):
+ *   spins s_i in {0..q-1}, i = 0..L-1                       (Sec. 2, Eq. 1; the
+ *                                                             paper's 1..q minus one)
+ *   H = -(c/2) sum_{i != j} J*(|i-j|) delta(s_i, s_j)       (Eq. 2; pair factor c:
+ *        c = 2 is the ordered double sum as printed, c = 1 counts each pair once
+ *        as the paper's energy listing of Sec. 4.2 does)
+ *   J*(r) = r^-s + L^-s [zeta(s, 1 + r/L) + zeta(s, 1 - r/L)],  s = 1 + sigma
+ *                                                            (Eq. 5-7), J*(0) = 0
+ *   Metropolis: sites k = 0..L-1 in order, proposal uniform over the other q-1
+ *     states, accept iff dE <= 0 or u < exp(-beta dE)          (Eq. 8, Sec. 4.2)
+ *   exchange: stage 0 pairs (t, t+1) with t even, then stage 1 with t odd;
+ *     D = (beta_t - beta_{t+1})(E_t - E_{t+1}), accept iff D >= 0 or u < exp(D)
+ *                                                            (Eq. 9, Sec. 4.2)
+ *   M = (q N_max / L - 1) / (q - 1)                            (Eq. 10)
+ * Temperature slots t = 0..R-1 keep their temperatures; configurations move
+ * between slots on accepted exchanges.  All outputs are in slot order.
+ *
+ * Random numbers: Philox4x32-10 with key (seed_lo, seed_hi) and counters
+ * (i, t, 0, 0) for the initial spins, (k, t, n, 1) for the Metropolis draw of
+ * site k in slot t at absolute sweep n, (t, stage, m, 2) for exchange m.  A job
+ * is therefore a pure function of its arguments and its call sequence, the
+ * same alone or batched with others, and resumable bit-exactly.
+ *
+ * Precision modes:
+ *   POTTS_LR_FP64 -- local fields h[x][i] = sum_{j != i} J*(|i-j|) delta(x, s_j)
+ *     in FP64; every accept decision is the FP64 decision (decided in FP32
+ *     where the FP32 margin is provably large enough, else in FP64).
+ *   POTTS_LR_FP32 -- fields in FP32, decisions in FP32, running energy in FP64;
+ *     every recompute_every sweeps the fields are rebuilt as H = C . onehot(S)
+ *     on the tensor cores (C = J*(|i-j|) split into BF16 hi + lo parts, FP32
+ *     accumulation) and the energy is re-anchored from the spins.
+ *
+ * Errors: every int-returning call returns POTTS_LR_OK (0) or one of the codes
+ * below; potts_lr_last_error() gives a message for the calling thread.  A call
+ * that fails leaves the handle unchanged unless its description says otherwise.
+ *
+ * Ownership and threads: a handle owns all of its device memory; arrays passed
+ * in are copied (or read before the call returns).  A handle must not be used
+ * from two threads at once; distinct handles are independent.
+ */
+#ifndef POTTS_LR_H
+#define POTTS_LR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define POTTS_LR_OK 0
+#define POTTS_LR_EINVAL 1   /* argument out of range */
+#define POTTS_LR_ENOMEM 2   /* device or host allocation failed */
+#define POTTS_LR_ECUDA 3    /* CUDA runtime error (message has the detail) */
+#define POTTS_LR_ETIMEOUT 4 /* a bounded device wait expired; results invalid */
+#define POTTS_LR_ESTATE 5   /* checkpoint buffer does not match the handle */
+
+#define POTTS_LR_FP64 0
+#define POTTS_LR_FP32 1
+
+#define POTTS_LR_MAX_Q 16
+
+typedef struct potts_lr potts_lr_t;
+
+typedef struct {
+    int precision;       /* POTTS_LR_FP64 (default) or POTTS_LR_FP32 */
+    int recompute_every; /* FP32 mode: tensor-core field rebuild every K sweeps
+                            (default 100; 0 = only on explicit request) */
+    int pair_factor;     /* c in Eq. 2: 2 (default) or 1 */
+    void* cuda_stream;   /* cudaStream_t to run on; NULL = a stream the handle creates */
+} potts_lr_opts;
+
+/* Fill *opts with the defaults above. */
+int potts_lr_default_opts(potts_lr_opts* opts);
+
+/*
+ * Create a job: R temperature slots of an L-site chain with q states, coupling
+ * exponent sigma (Eq. 4-6), absolute temperatures temps[0..R-1] (k_B = 1,
+ * Sec. 3; host array, copied), Philox seed.  Draws the initial spins, builds the
+ * FP64 J* table and the exact local fields, and computes the initial energies.
+ * Errors: EINVAL for L < 2, L > 65536, q < 2, q > 16, sigma <= 0 or not finite,
+ * R < 1 or R > 4096, a non-positive or non-finite temperature, pair_factor not
+ * 1 or 2, unknown precision; ENOMEM; ECUDA.  On error *out is set to NULL.
+ */
+int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint64_t seed,
+                    const potts_lr_opts* opts, potts_lr_t** out);
+
+/* n full Metropolis sweeps of every slot (L attempts per slot per sweep, Eq. 8),
+ * asynchronous on the handle's stream.  In FP32 mode a tensor-core field
+ * rebuild runs after every recompute_every-th sweep.  n >= 0. */
+int potts_lr_sweep(potts_lr_t* h, int n);
+
+/* One exchange step (Eq. 9): stage 0 then stage 1, asynchronous. */
+int potts_lr_exchange(potts_lr_t* h);
+
+/* Energy (Eq. 2) and magnetisation (Eq. 10) of every slot, computed on the GPU
+ * from the packed spins (energy = -(c/2) sum_r J*(r) N_r, N_r the number of
+ * sites i with s_i = s_{(i+r) mod L}).  E and M are caller-owned host arrays
+ * of R doubles (either may be NULL).  Synchronises the handle's stream. */
+int potts_lr_measure(potts_lr_t* h, double* E, double* M);
+
+/* As potts_lr_measure, but E and M are device arrays of R doubles and the call
+ * is asynchronous (usable inside a captured CUDA graph). */
+int potts_lr_measure_device(potts_lr_t* h, double* E, double* M);
+
+/* Rebuild the local fields from the spins: FP32 mode -- split-BF16 tensor-core
+ * product H = C . onehot(S) with FP32 accumulation; FP64 mode -- direct FP64
+ * sums.  Re-anchors the running energies from the spins.  Asynchronous. */
+int potts_lr_fields_recompute(potts_lr_t* h);
+
+/* Largest |h - h_exact| / Jtot over all fields of all slots, h_exact the FP64
+ * direct rebuild of the current spins (the FP32 drift measure).  Synchronises. */
+int potts_lr_fields_error(potts_lr_t* h, double* max_err);
+
+/* Checkpoint.  With buf == NULL sets *len to the size needed.  Otherwise
+ * writes the complete state (spins, fields, energies, slot map, counters) into
+ * buf (*len bytes available, *len set to bytes written); ESTATE if too small.
+ * Synchronises. */
+int potts_lr_get_state(potts_lr_t* h, void* buf, size_t* len);
+
+/* Restore a checkpoint written by potts_lr_get_state of a handle created with
+ * the same L, q, R and precision; ESTATE if it does not match.  Continuing
+ * from a restored state reproduces the uninterrupted run bit for bit. */
+int potts_lr_set_state(potts_lr_t* h, const void* buf, size_t len);
+
+/* Spins of every slot, out[t*L + i] in 0..q-1 (host array of R*L bytes). Syncs. */
+int potts_lr_get_spins(potts_lr_t* h, uint8_t* out);
+
+/* Local fields of every slot as doubles, out[(t*q + x)*L + i] (host array of
+ * R*q*L doubles). Syncs. */
+int potts_lr_get_fields(potts_lr_t* h, double* out);
+
+/* Running energies (the value the exchange step uses) of every slot. Syncs. */
+int potts_lr_get_energy(potts_lr_t* h, double* E);
+
+/* Counters since create, host arrays (any may be NULL): acc_flip[R] accepted
+ * Metropolis flips per slot; acc_swap[R] accepted exchanges of pair (t, t+1)
+ * (entry R-1 is 0); near_ties[2] = {Metropolis, exchange} decisions whose FP64
+ * margin |beta dE + ln u| (resp. |D - ln u|) was below 1e-9. Syncs. */
+int potts_lr_stats(potts_lr_t* h, uint64_t* acc_flip, uint64_t* acc_swap, uint64_t* near_ties);
+
+/* Sweep and exchange counts since create. */
+int potts_lr_counters(potts_lr_t* h, uint32_t* nsweep, uint32_t* nexch);
+
+/* Wait for all work queued on the handle's stream. */
+int potts_lr_sync(potts_lr_t* h);
+
+void potts_lr_destroy(potts_lr_t* h);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* potts_lr_last_error(void);
+
+/* The FP64 coupling table of Eq. 6 (Hurwitz zeta by Euler-Maclaurin):
+ * out[r] = J*(r) for r = 0..L-1, out[0] = 0; host array of L doubles. */
+int potts_lr_jstar(int L, double sigma, double* out);
+
+/*
+ * Batching: run many jobs (any mix of L, q, sigma, R, precision) together.  One
+ * batch step is one sweep of every slot of every job followed by one exchange
+ * step of every job (the FP32 rebuild runs for each job on its own schedule).
+ * The steps are launched as one CUDA graph per chunk of steps, captured on the
+ * first run and replayed afterwards.  Each job's results are bit-identical to
+ * running it alone with the same call sequence.  The jobs must outlive the
+ * batch and must not be used on their own while a batch run is in flight.
+ */
+typedef struct potts_lr_batch potts_lr_batch_t;
+
+/* jobs: host array of n handles (copied). Errors: EINVAL (n < 1, NULL job,
+ * a job listed twice), ENOMEM, ECUDA. */
+int potts_lr_batch_create(potts_lr_t* const* jobs, int n, void* cuda_stream, potts_lr_batch_t** out);
+
+/* nsteps batch steps, asynchronous on the batch stream; steps_per_graph is the
+ * chunk captured into one graph (0 = default 10). */
+int potts_lr_batch_run(potts_lr_batch_t* b, int nsteps, int steps_per_graph);
+
+/* The parts of a batch step as separate asynchronous launches on the batch
+ * stream: n sweeps of every slot of every job (one kernel launch per precision
+ * class, FP32 rebuilds as they fall due), and one exchange step of every job
+ * (one launch).  batch_run is equivalent to alternating these. */
+int potts_lr_batch_sweep(potts_lr_batch_t* b, int n);
+int potts_lr_batch_exchange(potts_lr_batch_t* b);
+
+/* Energies and magnetisations of every slot of every job, in job order then
+ * slot order (sum of the jobs' R entries each), one kernel launch.
+ * potts_lr_batch_measure: host arrays, synchronises.
+ * potts_lr_batch_measure_device: device arrays, asynchronous. */
+int potts_lr_batch_measure(potts_lr_batch_t* b, double* E, double* M);
+int potts_lr_batch_measure_device(potts_lr_batch_t* b, double* E, double* M);
+
+int potts_lr_batch_sync(potts_lr_batch_t* b);
+void potts_lr_batch_destroy(potts_lr_batch_t* b);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* POTTS_LR_H */

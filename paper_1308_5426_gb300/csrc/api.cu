@@ -1,0 +1,822 @@
+// Host side of the potts_lr C ABI: argument checks, the device arena of a job,
+// launch sequencing, checkpoints and graph-captured batching.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <unordered_set>
+#include <vector>
+
+#include "../../include/potts_lr.h"
+#include "potts_internal.h"
+
+using namespace plr;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where)
+{
+    return fail(POTTS_LR_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define PLR_CUDA(call)                                          \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);     \
+    } while (0)
+
+constexpr size_t kSmemBudget = 220 * 1024;  // dynamic shared memory a sweep CTA may take
+constexpr uint32_t kStateMagic = 0x31524c50u; // "PLR1"
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct StateHeader {
+    uint32_t magic, version;
+    int32_t L, q, R, precision, c, Lpad;
+    uint64_t seed;
+    uint32_t nsweep, nexch;
+};
+
+}  // namespace
+
+struct potts_lr {
+    int L, q, R, W, Lpad, precision, K, c;
+    double sigma, jtot;
+    uint64_t seed;
+    cudaStream_t stream;
+    bool own_stream;
+    void* arena;
+    size_t wsize;                 // field word size
+    JobDev hj;                    // host copy of the device descriptor
+    JobDev* dj;                   // device descriptor
+    int2* dwork;                  // {0, t}, t = 0..R-1
+    uint32_t nsweep, nexch;       // host mirrors of the counters
+    size_t sweep_smem, measure_smem, direct_smem;
+    double* pinned;               // 2R doubles of pinned host memory for measure
+};
+
+struct potts_lr_batch {
+    std::vector<potts_lr_t*> jobs;
+    cudaStream_t stream;
+    bool own_stream;
+    JobDev* djobs;
+    void* arena;
+    struct Group {
+        int precision;
+        int2* dwork;
+        int nwork;
+        size_t smem;
+    };
+    std::vector<Group> groups;
+    std::vector<int> fp32_jobs;  // jobs that need the conditional rebuild
+    int2* dmeas;                 // (job, slot) of every slot, job order
+    int nmeas;
+    size_t meas_smem;
+    double* meas_buf;            // device staging: 2 * nmeas doubles
+    std::vector<int> meas_off;   // first row of each job
+    cudaGraphExec_t exec;
+    int exec_steps;
+    cudaEvent_t ev;
+};
+
+namespace {
+
+int check_opts(const potts_lr_opts* o)
+{
+    if (o->precision != POTTS_LR_FP64 && o->precision != POTTS_LR_FP32)
+        return fail(POTTS_LR_EINVAL, "precision must be POTTS_LR_FP64 or POTTS_LR_FP32");
+    if (o->pair_factor != 1 && o->pair_factor != 2) return fail(POTTS_LR_EINVAL, "pair_factor must be 1 or 2");
+    if (o->recompute_every < 0) return fail(POTTS_LR_EINVAL, "recompute_every must be >= 0");
+    return POTTS_LR_OK;
+}
+
+// Field rebuild of one job: FP32 mode on the tensor cores where the shape is
+// supported (else the FP64 direct sums rounded to FP32), FP64 mode by direct
+// sums; then the energies are re-anchored from the spins.  job_dev is the
+// job's descriptor in device memory (its own, or its entry in a batch table).
+cudaError_t rebuild_launch(const potts_lr_t* h, const JobDev* job_dev, int cond, cudaStream_t st)
+{
+    cudaError_t e = cudaErrorNotSupported;
+    if (h->precision == POTTS_LR_FP32) e = launch_fields_tc(job_dev, h->L, h->q, h->R, cond, st);
+    if (e == cudaErrorNotSupported) {
+        (void)cudaGetLastError();
+        e = launch_fields_direct(job_dev, h->L, h->R, 0, cond, h->direct_smem, st);
+    }
+    if (e != cudaSuccess) return e;
+    return launch_measure(job_dev, h->dwork, h->R, 1, cond, h->measure_smem, st);
+}
+
+int rebuild(potts_lr_t* h)
+{
+    cudaError_t e = rebuild_launch(h, h->dj, 0, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "field rebuild");
+    return POTTS_LR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* potts_lr_last_error(void) { return g_err; }
+
+int potts_lr_default_opts(potts_lr_opts* opts)
+{
+    if (!opts) return fail(POTTS_LR_EINVAL, "opts is NULL");
+    opts->precision = POTTS_LR_FP64;
+    opts->recompute_every = 100;
+    opts->pair_factor = 2;
+    opts->cuda_stream = nullptr;
+    return POTTS_LR_OK;
+}
+
+int potts_lr_jstar(int L, double sigma, double* out)
+{
+    if (L < 2 || L > kMaxL) return fail(POTTS_LR_EINVAL, "L must be in [2, %d]", kMaxL);
+    if (!(sigma > 0.0) || !std::isfinite(sigma)) return fail(POTTS_LR_EINVAL, "sigma must be positive and finite");
+    if (!out) return fail(POTTS_LR_EINVAL, "out is NULL");
+    jstar_table(L, sigma, out);
+    return POTTS_LR_OK;
+}
+
+void potts_lr_destroy(potts_lr_t* h)
+{
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->arena) cudaFree(h->arena);
+    if (h->pinned) cudaFreeHost(h->pinned);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint64_t seed,
+                    const potts_lr_opts* opts, potts_lr_t** out)
+{
+    if (!out) return fail(POTTS_LR_EINVAL, "out is NULL");
+    *out = nullptr;
+    potts_lr_opts o;
+    potts_lr_default_opts(&o);
+    if (opts) o = *opts;
+    int rc = check_opts(&o);
+    if (rc) return rc;
+    if (L < 2 || L > kMaxL) return fail(POTTS_LR_EINVAL, "L must be in [2, %d]", kMaxL);
+    if (q < 2 || q > kMaxQ) return fail(POTTS_LR_EINVAL, "q must be in [2, %d]", kMaxQ);
+    if (!(sigma > 0.0) || !std::isfinite(sigma)) return fail(POTTS_LR_EINVAL, "sigma must be positive and finite");
+    if (R < 1 || R > 4096) return fail(POTTS_LR_EINVAL, "R must be in [1, 4096]");
+    if (!temps) return fail(POTTS_LR_EINVAL, "temps is NULL");
+    for (int t = 0; t < R; ++t)
+        if (!(temps[t] > 0.0) || !std::isfinite(temps[t]))
+            return fail(POTTS_LR_EINVAL, "temperature %d is not positive and finite", t);
+
+    potts_lr_t* h = new (std::nothrow) potts_lr();
+    if (!h) return fail(POTTS_LR_ENOMEM, "host allocation failed");
+    h->L = L;
+    h->q = q;
+    h->R = R;
+    h->W = (L + 7) / 8;
+    h->Lpad = (L + 31) & ~31;
+    h->precision = o.precision;
+    h->K = o.precision == POTTS_LR_FP32 ? o.recompute_every : 0;
+    h->c = o.pair_factor;
+    h->sigma = sigma;
+    h->seed = seed;
+    h->wsize = o.precision == POTTS_LR_FP64 ? 8 : 4;
+    if (o.cuda_stream) {
+        h->stream = (cudaStream_t)o.cuda_stream;
+        h->own_stream = false;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete h;
+            return cuda_fail(e, "cudaStreamCreateWithFlags");
+        }
+        h->own_stream = true;
+    }
+
+    // host tables
+    std::vector<double> J(L);
+    jstar_table(L, sigma, J.data());
+    double jt = 0.0;
+    for (int r = 1; r < L; ++r) jt += J[r];
+    h->jtot = jt;
+    std::vector<double> J64d(2 * (size_t)h->Lpad, 0.0);
+    std::vector<float> J32d(2 * (size_t)h->Lpad, 0.0f);
+    for (int m = 0; m < 2 * L; ++m) {
+        J64d[m] = J[m % L];
+        J32d[m] = (float)J[m % L];
+    }
+    std::vector<double> beta(R);
+    for (int t = 0; t < R; ++t) beta[t] = 1.0 / temps[t];
+    std::vector<int> map(R);
+    std::vector<int2> work(R);
+    for (int t = 0; t < R; ++t) {
+        map[t] = t;
+        work[t] = make_int2(0, t);
+    }
+
+    // arena layout
+    const size_t Lp = (size_t)h->Lpad;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o2 = off;
+        off += align256(bytes);
+        return o2;
+    };
+    const size_t o_J64 = take(2 * Lp * 8), o_J32 = take(2 * Lp * 4);
+    const size_t o_spins = take((size_t)R * h->W * 4);
+    const size_t o_fields = take((size_t)R * q * Lp * h->wsize);
+    const size_t o_E = take((size_t)R * 8), o_map = take((size_t)R * 4), o_beta = take((size_t)R * 8);
+    const size_t o_nsw = take((size_t)R * 4), o_nex = take(4);
+    const size_t o_accf = take((size_t)R * 8), o_accs = take((size_t)R * 8), o_near = take(16);
+    const size_t o_mE = take((size_t)R * 8), o_mM = take((size_t)R * 8), o_err = take(8);
+    const size_t o_job = take(sizeof(JobDev)), o_work = take((size_t)R * sizeof(int2));
+    cudaError_t e = cudaMalloc(&h->arena, off);
+    if (e != cudaSuccess) {
+        potts_lr_destroy(h);
+        return fail(e == cudaErrorMemoryAllocation ? POTTS_LR_ENOMEM : POTTS_LR_ECUDA, "cudaMalloc(%zu): %s", off,
+                    cudaGetErrorString(e));
+    }
+    e = cudaMallocHost((void**)&h->pinned, 2 * (size_t)R * sizeof(double));
+    if (e != cudaSuccess) {
+        potts_lr_destroy(h);
+        return fail(POTTS_LR_ENOMEM, "cudaMallocHost: %s", cudaGetErrorString(e));
+    }
+    char* base = (char*)h->arena;
+    JobDev& j = h->hj;
+    std::memset(&j, 0, sizeof(j));
+    j.L = L;
+    j.q = q;
+    j.Lpad = h->Lpad;
+    j.W = h->W;
+    j.R = R;
+    j.c = h->c;
+    j.precision = h->precision;
+    j.recompute_every = h->K;
+    j.key0 = (uint32_t)(seed & 0xffffffffu);
+    j.key1 = (uint32_t)(seed >> 32);
+    j.jtot = jt;
+    j.J64d = (const double*)(base + o_J64);
+    j.J32d = (const float*)(base + o_J32);
+    j.spins = (uint32_t*)(base + o_spins);
+    j.fields = (void*)(base + o_fields);
+    j.E = (double*)(base + o_E);
+    j.map = (int*)(base + o_map);
+    j.beta = (const double*)(base + o_beta);
+    j.nsweep = (uint32_t*)(base + o_nsw);
+    j.nexch = (uint32_t*)(base + o_nex);
+    j.acc_flip = (unsigned long long*)(base + o_accf);
+    j.acc_swap = (unsigned long long*)(base + o_accs);
+    j.near = (unsigned long long*)(base + o_near);
+    j.meas_E = (double*)(base + o_mE);
+    j.meas_M = (double*)(base + o_mM);
+    j.err_bits = (unsigned long long*)(base + o_err);
+    // residency of the sweep kernel's working set
+    const size_t hbytes = (size_t)q * Lp * h->wsize, jbytes = 2 * Lp * h->wsize, rest = Lp + 3 * kSiteBlock * 4;
+    j.h_smem = (hbytes + jbytes + rest <= kSmemBudget) ? 1 : 0;
+    j.j_smem = (jbytes + rest + (j.h_smem ? hbytes : 0) <= kSmemBudget) ? 1 : 0;
+    if (!j.h_smem && hbytes + rest <= kSmemBudget) j.h_smem = 1;  // fields first, table from L2
+    j.j_smem = (jbytes + rest + (j.h_smem ? hbytes : 0) <= kSmemBudget) ? 1 : 0;
+    h->dj = (JobDev*)(base + o_job);
+    h->dwork = (int2*)(base + o_work);
+    h->sweep_smem = sweep_smem_bytes(j);
+    h->measure_smem = measure_smem_bytes(L, h->W);
+    h->direct_smem = direct_smem_bytes(L, q);
+
+    cudaStream_t st = h->stream;
+    int rc2 = POTTS_LR_OK;
+    do {
+        if ((e = cudaMemsetAsync(h->arena, 0, off, st)) != cudaSuccess) break;
+        if ((e = cudaMemcpyAsync((void*)j.J64d, J64d.data(), 2 * Lp * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
+        if ((e = cudaMemcpyAsync((void*)j.J32d, J32d.data(), 2 * Lp * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
+        if ((e = cudaMemcpyAsync((void*)j.beta, beta.data(), (size_t)R * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
+        if ((e = cudaMemcpyAsync(j.map, map.data(), (size_t)R * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
+        if ((e = cudaMemcpyAsync(h->dj, &j, sizeof(JobDev), cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
+        if ((e = cudaMemcpyAsync(h->dwork, work.data(), (size_t)R * sizeof(int2), cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
+        if ((e = launch_init_spins(h->dj, 0, L, h->W, R, st)) != cudaSuccess) break;
+        if ((e = launch_fields_direct(h->dj, L, R, 0, 0, h->direct_smem, st)) != cudaSuccess) break;
+        if ((e = launch_measure(h->dj, h->dwork, R, 1, 0, h->measure_smem, st)) != cudaSuccess) break;
+        e = cudaStreamSynchronize(st);
+    } while (0);
+    if (e != cudaSuccess) rc2 = cuda_fail(e, "potts_lr_create");
+    if (rc2) {
+        potts_lr_destroy(h);
+        return rc2;
+    }
+    h->nsweep = 0;
+    h->nexch = 0;
+    *out = h;
+    return POTTS_LR_OK;
+}
+
+int potts_lr_sweep(potts_lr_t* h, int n)
+{
+    if (!h) return fail(POTTS_LR_EINVAL, "handle is NULL");
+    if (n < 0) return fail(POTTS_LR_EINVAL, "n must be >= 0");
+    while (n > 0) {
+        int chunk = n;
+        if (h->K > 0) chunk = std::min(n, h->K - (int)(h->nsweep % (uint32_t)h->K));
+        cudaError_t e = launch_sweep(h->dj, h->dwork, h->R, chunk, h->precision, h->sweep_smem, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "sweep kernel");
+        h->nsweep += (uint32_t)chunk;
+        n -= chunk;
+        if (h->K > 0 && h->nsweep % (uint32_t)h->K == 0) {
+            int rc = rebuild(h);
+            if (rc) return rc;
+        }
+    }
+    return POTTS_LR_OK;
+}
+
+int potts_lr_exchange(potts_lr_t* h)
+{
+    if (!h) return fail(POTTS_LR_EINVAL, "handle is NULL");
+    cudaError_t e = launch_exchange(h->dj, 1, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "exchange kernel");
+    h->nexch++;
+    return POTTS_LR_OK;
+}
+
+int potts_lr_measure_device(potts_lr_t* h, double* E, double* M)
+{
+    if (!h) return fail(POTTS_LR_EINVAL, "handle is NULL");
+    cudaError_t e = launch_measure(h->dj, h->dwork, h->R, 0, 0, h->measure_smem, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "measure kernel");
+    const size_t b = (size_t)h->R * sizeof(double);
+    if (E) PLR_CUDA(cudaMemcpyAsync(E, h->hj.meas_E, b, cudaMemcpyDeviceToDevice, h->stream));
+    if (M) PLR_CUDA(cudaMemcpyAsync(M, h->hj.meas_M, b, cudaMemcpyDeviceToDevice, h->stream));
+    return POTTS_LR_OK;
+}
+
+int potts_lr_measure(potts_lr_t* h, double* E, double* M)
+{
+    if (!h) return fail(POTTS_LR_EINVAL, "handle is NULL");
+    cudaError_t e = launch_measure(h->dj, h->dwork, h->R, 0, 0, h->measure_smem, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "measure kernel");
+    const size_t b = (size_t)h->R * sizeof(double);
+    PLR_CUDA(cudaMemcpyAsync(h->pinned, h->hj.meas_E, b, cudaMemcpyDeviceToHost, h->stream));
+    PLR_CUDA(cudaMemcpyAsync(h->pinned + h->R, h->hj.meas_M, b, cudaMemcpyDeviceToHost, h->stream));
+    PLR_CUDA(cudaStreamSynchronize(h->stream));
+    if (E) std::memcpy(E, h->pinned, b);
+    if (M) std::memcpy(M, h->pinned + h->R, b);
+    return POTTS_LR_OK;
+}
+
+int potts_lr_fields_recompute(potts_lr_t* h)
+{
+    if (!h) return fail(POTTS_LR_EINVAL, "handle is NULL");
+    return rebuild(h);
+}
+
+int potts_lr_fields_error(potts_lr_t* h, double* max_err)
+{
+    if (!h || !max_err) return fail(POTTS_LR_EINVAL, "NULL argument");
+    PLR_CUDA(cudaMemsetAsync(h->hj.err_bits, 0, 8, h->stream));
+    cudaError_t e = launch_fields_direct(h->dj, h->L, h->R, 1, 0, h->direct_smem, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "fields check");
+    unsigned long long bits = 0;
+    PLR_CUDA(cudaMemcpyAsync(&bits, h->hj.err_bits, 8, cudaMemcpyDeviceToHost, h->stream));
+    PLR_CUDA(cudaStreamSynchronize(h->stream));
+    std::memcpy(max_err, &bits, 8);
+    return POTTS_LR_OK;
+}
+
+int potts_lr_sync(potts_lr_t* h)
+{
+    if (!h) return fail(POTTS_LR_EINVAL, "handle is NULL");
+    PLR_CUDA(cudaStreamSynchronize(h->stream));
+    return POTTS_LR_OK;
+}
+
+int potts_lr_counters(potts_lr_t* h, uint32_t* nsweep, uint32_t* nexch)
+{
+    if (!h) return fail(POTTS_LR_EINVAL, "handle is NULL");
+    if (nsweep) *nsweep = h->nsweep;
+    if (nexch) *nexch = h->nexch;
+    return POTTS_LR_OK;
+}
+
+static size_t state_bytes(const potts_lr_t* h)
+{
+    const size_t R = h->R;
+    return sizeof(StateHeader) + R * 4 /*map*/ + R * 8 /*E*/ + R * h->W * 4 /*spins*/ +
+           R * h->q * (size_t)h->Lpad * h->wsize /*fields*/ + R * 4 /*nsweep*/ + R * 8 /*acc_flip*/ +
+           R * 8 /*acc_swap*/ + 16 /*near*/;
+}
+
+int potts_lr_get_state(potts_lr_t* h, void* buf, size_t* len)
+{
+    if (!h || !len) return fail(POTTS_LR_EINVAL, "NULL argument");
+    const size_t need = state_bytes(h);
+    if (!buf) {
+        *len = need;
+        return POTTS_LR_OK;
+    }
+    if (*len < need) return fail(POTTS_LR_ESTATE, "checkpoint buffer too small (%zu < %zu)", *len, need);
+    StateHeader hd;
+    std::memset(&hd, 0, sizeof(hd));
+    hd.magic = kStateMagic;
+    hd.version = 1;
+    hd.L = h->L;
+    hd.q = h->q;
+    hd.R = h->R;
+    hd.precision = h->precision;
+    hd.c = h->c;
+    hd.Lpad = h->Lpad;
+    hd.seed = h->seed;
+    hd.nsweep = h->nsweep;
+    hd.nexch = h->nexch;
+    char* p = (char*)buf;
+    std::memcpy(p, &hd, sizeof(hd));
+    p += sizeof(hd);
+    const size_t R = h->R;
+    const JobDev& j = h->hj;
+    struct Piece {
+        const void* src;
+        size_t bytes;
+    } pieces[] = {{j.map, R * 4},
+                  {j.E, R * 8},
+                  {j.spins, R * h->W * 4},
+                  {j.fields, R * h->q * (size_t)h->Lpad * h->wsize},
+                  {j.nsweep, R * 4},
+                  {j.acc_flip, R * 8},
+                  {j.acc_swap, R * 8},
+                  {j.near, 16}};
+    for (const Piece& pc : pieces) {
+        PLR_CUDA(cudaMemcpyAsync(p, pc.src, pc.bytes, cudaMemcpyDeviceToHost, h->stream));
+        p += pc.bytes;
+    }
+    PLR_CUDA(cudaStreamSynchronize(h->stream));
+    *len = need;
+    return POTTS_LR_OK;
+}
+
+int potts_lr_set_state(potts_lr_t* h, const void* buf, size_t len)
+{
+    if (!h || !buf) return fail(POTTS_LR_EINVAL, "NULL argument");
+    if (len != state_bytes(h)) return fail(POTTS_LR_ESTATE, "checkpoint size %zu does not match %zu", len, state_bytes(h));
+    StateHeader hd;
+    std::memcpy(&hd, buf, sizeof(hd));
+    if (hd.magic != kStateMagic || hd.version != 1 || hd.L != h->L || hd.q != h->q || hd.R != h->R ||
+        hd.precision != h->precision || hd.Lpad != h->Lpad)
+        return fail(POTTS_LR_ESTATE, "checkpoint does not match this job's L, q, R or precision");
+    const char* p = (const char*)buf + sizeof(hd);
+    const size_t R = h->R;
+    const JobDev& j = h->hj;
+    // validate the slot map before touching the device
+    std::vector<int> map(R);
+    std::memcpy(map.data(), p, R * 4);
+    std::vector<char> seen(R, 0);
+    for (size_t t = 0; t < R; ++t) {
+        if (map[t] < 0 || (size_t)map[t] >= R || seen[map[t]]) return fail(POTTS_LR_ESTATE, "corrupt slot map");
+        seen[map[t]] = 1;
+    }
+    struct Piece {
+        void* dst;
+        size_t bytes;
+    } pieces[] = {{j.map, R * 4},
+                  {j.E, R * 8},
+                  {j.spins, R * h->W * 4},
+                  {j.fields, R * h->q * (size_t)h->Lpad * h->wsize},
+                  {j.nsweep, R * 4},
+                  {j.acc_flip, R * 8},
+                  {j.acc_swap, R * 8},
+                  {j.near, 16}};
+    for (const Piece& pc : pieces) {
+        PLR_CUDA(cudaMemcpyAsync(pc.dst, p, pc.bytes, cudaMemcpyHostToDevice, h->stream));
+        p += pc.bytes;
+    }
+    PLR_CUDA(cudaMemcpyAsync(j.nexch, &hd.nexch, 4, cudaMemcpyHostToDevice, h->stream));
+    PLR_CUDA(cudaStreamSynchronize(h->stream));
+    h->nsweep = hd.nsweep;
+    h->nexch = hd.nexch;
+    return POTTS_LR_OK;
+}
+
+int potts_lr_get_spins(potts_lr_t* h, uint8_t* out)
+{
+    if (!h || !out) return fail(POTTS_LR_EINVAL, "NULL argument");
+    std::vector<uint32_t> packed((size_t)h->R * h->W);
+    std::vector<int> map(h->R);
+    PLR_CUDA(cudaMemcpyAsync(packed.data(), h->hj.spins, packed.size() * 4, cudaMemcpyDeviceToHost, h->stream));
+    PLR_CUDA(cudaMemcpyAsync(map.data(), h->hj.map, (size_t)h->R * 4, cudaMemcpyDeviceToHost, h->stream));
+    PLR_CUDA(cudaStreamSynchronize(h->stream));
+    for (int t = 0; t < h->R; ++t) {
+        const uint32_t* w = packed.data() + (size_t)map[t] * h->W;
+        for (int i = 0; i < h->L; ++i) out[(size_t)t * h->L + i] = (uint8_t)((w[i >> 3] >> (4 * (i & 7))) & 15u);
+    }
+    return POTTS_LR_OK;
+}
+
+int potts_lr_get_fields(potts_lr_t* h, double* out)
+{
+    if (!h || !out) return fail(POTTS_LR_EINVAL, "NULL argument");
+    const size_t per = (size_t)h->q * h->Lpad;
+    std::vector<char> raw((size_t)h->R * per * h->wsize);
+    std::vector<int> map(h->R);
+    PLR_CUDA(cudaMemcpyAsync(raw.data(), h->hj.fields, raw.size(), cudaMemcpyDeviceToHost, h->stream));
+    PLR_CUDA(cudaMemcpyAsync(map.data(), h->hj.map, (size_t)h->R * 4, cudaMemcpyDeviceToHost, h->stream));
+    PLR_CUDA(cudaStreamSynchronize(h->stream));
+    for (int t = 0; t < h->R; ++t)
+        for (int x = 0; x < h->q; ++x)
+            for (int i = 0; i < h->L; ++i) {
+                const size_t src = (size_t)map[t] * per + (size_t)x * h->Lpad + i;
+                out[((size_t)t * h->q + x) * h->L + i] =
+                    h->wsize == 8 ? ((const double*)raw.data())[src] : (double)((const float*)raw.data())[src];
+            }
+    return POTTS_LR_OK;
+}
+
+int potts_lr_get_energy(potts_lr_t* h, double* E)
+{
+    if (!h || !E) return fail(POTTS_LR_EINVAL, "NULL argument");
+    std::vector<double> Er(h->R);
+    std::vector<int> map(h->R);
+    PLR_CUDA(cudaMemcpyAsync(Er.data(), h->hj.E, (size_t)h->R * 8, cudaMemcpyDeviceToHost, h->stream));
+    PLR_CUDA(cudaMemcpyAsync(map.data(), h->hj.map, (size_t)h->R * 4, cudaMemcpyDeviceToHost, h->stream));
+    PLR_CUDA(cudaStreamSynchronize(h->stream));
+    for (int t = 0; t < h->R; ++t) E[t] = Er[map[t]];
+    return POTTS_LR_OK;
+}
+
+int potts_lr_stats(potts_lr_t* h, uint64_t* acc_flip, uint64_t* acc_swap, uint64_t* near_ties)
+{
+    if (!h) return fail(POTTS_LR_EINVAL, "handle is NULL");
+    const size_t b = (size_t)h->R * 8;
+    if (acc_flip) PLR_CUDA(cudaMemcpyAsync(acc_flip, h->hj.acc_flip, b, cudaMemcpyDeviceToHost, h->stream));
+    if (acc_swap) PLR_CUDA(cudaMemcpyAsync(acc_swap, h->hj.acc_swap, b, cudaMemcpyDeviceToHost, h->stream));
+    if (near_ties) PLR_CUDA(cudaMemcpyAsync(near_ties, h->hj.near, 16, cudaMemcpyDeviceToHost, h->stream));
+    PLR_CUDA(cudaStreamSynchronize(h->stream));
+    return POTTS_LR_OK;
+}
+
+// ---------------------------------------------------------------- batching
+
+void potts_lr_batch_destroy(potts_lr_batch_t* b)
+{
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->ev) cudaEventDestroy(b->ev);
+    if (b->arena) cudaFree(b->arena);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+int potts_lr_batch_create(potts_lr_t* const* jobs, int n, void* cuda_stream, potts_lr_batch_t** out)
+{
+    if (!out) return fail(POTTS_LR_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!jobs || n < 1) return fail(POTTS_LR_EINVAL, "need at least one job");
+    std::unordered_set<const void*> seen;
+    for (int i = 0; i < n; ++i) {
+        if (!jobs[i]) return fail(POTTS_LR_EINVAL, "job %d is NULL", i);
+        if (!seen.insert(jobs[i]).second) return fail(POTTS_LR_EINVAL, "job %d listed twice", i);
+    }
+    potts_lr_batch_t* b = new (std::nothrow) potts_lr_batch();
+    if (!b) return fail(POTTS_LR_ENOMEM, "host allocation failed");
+    b->jobs.assign(jobs, jobs + n);
+    if (cuda_stream) {
+        b->stream = (cudaStream_t)cuda_stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete b;
+            return cuda_fail(e, "cudaStreamCreateWithFlags");
+        }
+        b->own_stream = true;
+    }
+    cudaError_t e = cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        potts_lr_batch_destroy(b);
+        return cuda_fail(e, "cudaEventCreate");
+    }
+    // work tables per precision, longest slots first (the largest L q costs most)
+    std::vector<JobDev> hjobs(n);
+    std::vector<std::vector<int2>> works(2);
+    std::vector<size_t> smem(2, 0);
+    for (int i = 0; i < n; ++i) {
+        hjobs[i] = jobs[i]->hj;
+        const int p = jobs[i]->precision;
+        for (int t = 0; t < jobs[i]->R; ++t) works[p].push_back(make_int2(i, t));
+        smem[p] = std::max(smem[p], jobs[i]->sweep_smem);
+        if (p == POTTS_LR_FP32 && jobs[i]->K > 0) b->fp32_jobs.push_back(i);
+    }
+    for (int p = 0; p < 2; ++p)
+        std::stable_sort(works[p].begin(), works[p].end(), [&](const int2& x, const int2& y) {
+            const potts_lr_t* a = jobs[x.x];
+            const potts_lr_t* c = jobs[y.x];
+            return (long long)a->L * (a->q + 8) > (long long)c->L * (c->q + 8);
+        });
+    std::vector<int2> mwork;
+    for (int i = 0; i < n; ++i) {
+        b->meas_off.push_back((int)mwork.size());
+        for (int t = 0; t < jobs[i]->R; ++t) mwork.push_back(make_int2(i, t));
+        b->meas_smem = std::max(b->meas_smem, jobs[i]->measure_smem);
+    }
+    b->nmeas = (int)mwork.size();
+    size_t bytes = align256(n * sizeof(JobDev));
+    const size_t o_w0 = bytes;
+    bytes += align256(works[0].size() * sizeof(int2) + 8);
+    const size_t o_w1 = bytes;
+    bytes += align256(works[1].size() * sizeof(int2) + 8);
+    const size_t o_m = bytes;
+    bytes += align256(mwork.size() * sizeof(int2));
+    const size_t o_mb = bytes;
+    bytes += align256(2 * mwork.size() * sizeof(double));
+    e = cudaMalloc(&b->arena, bytes);
+    if (e != cudaSuccess) {
+        potts_lr_batch_destroy(b);
+        return fail(POTTS_LR_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    }
+    b->djobs = (JobDev*)b->arena;
+    b->dmeas = (int2*)((char*)b->arena + o_m);
+    b->meas_buf = (double*)((char*)b->arena + o_mb);
+    const size_t ow[2] = {o_w0, o_w1};
+    for (int p = 0; p < 2; ++p) {
+        if (works[p].empty()) continue;
+        potts_lr_batch_t::Group g;
+        g.precision = p;
+        g.dwork = (int2*)((char*)b->arena + ow[p]);
+        g.nwork = (int)works[p].size();
+        g.smem = smem[p];
+        b->groups.push_back(g);
+        e = cudaMemcpyAsync(g.dwork, works[p].data(), works[p].size() * sizeof(int2), cudaMemcpyHostToDevice,
+                            b->stream);
+        if (e != cudaSuccess) break;
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->djobs, hjobs.data(), n * sizeof(JobDev), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->dmeas, mwork.data(), mwork.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+        potts_lr_batch_destroy(b);
+        return cuda_fail(e, "potts_lr_batch_create");
+    }
+    *out = b;
+    return POTTS_LR_OK;
+}
+
+static cudaError_t batch_enqueue_sweeps(potts_lr_batch_t* b)
+{
+    cudaError_t e;
+    for (const auto& g : b->groups)
+        if ((e = launch_sweep(b->djobs, g.dwork, g.nwork, 1, g.precision, g.smem, b->stream)) != cudaSuccess) return e;
+    for (int i : b->fp32_jobs)
+        if ((e = rebuild_launch(b->jobs[i], b->djobs + i, 1, b->stream)) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+static cudaError_t batch_enqueue_step(potts_lr_batch_t* b)
+{
+    cudaError_t e = batch_enqueue_sweeps(b);
+    if (e != cudaSuccess) return e;
+    return launch_exchange(b->djobs, (int)b->jobs.size(), b->stream);
+}
+
+static int batch_begin(potts_lr_batch_t* b)
+{
+    for (potts_lr_t* h : b->jobs) {
+        if (h->stream == b->stream) continue;
+        PLR_CUDA(cudaEventRecord(b->ev, h->stream));
+        PLR_CUDA(cudaStreamWaitEvent(b->stream, b->ev, 0));
+    }
+    return POTTS_LR_OK;
+}
+
+static int batch_end(potts_lr_batch_t* b)
+{
+    PLR_CUDA(cudaEventRecord(b->ev, b->stream));
+    for (potts_lr_t* h : b->jobs)
+        if (h->stream != b->stream) PLR_CUDA(cudaStreamWaitEvent(h->stream, b->ev, 0));
+    return POTTS_LR_OK;
+}
+
+int potts_lr_batch_sweep(potts_lr_batch_t* b, int n)
+{
+    if (!b) return fail(POTTS_LR_EINVAL, "batch is NULL");
+    if (n < 0) return fail(POTTS_LR_EINVAL, "n must be >= 0");
+    int rc = batch_begin(b);
+    if (rc) return rc;
+    for (int s = 0; s < n; ++s) {
+        cudaError_t e = batch_enqueue_sweeps(b);
+        if (e != cudaSuccess) return cuda_fail(e, "batch sweep");
+    }
+    for (potts_lr_t* h : b->jobs) h->nsweep += (uint32_t)n;
+    return batch_end(b);
+}
+
+int potts_lr_batch_exchange(potts_lr_batch_t* b)
+{
+    if (!b) return fail(POTTS_LR_EINVAL, "batch is NULL");
+    int rc = batch_begin(b);
+    if (rc) return rc;
+    cudaError_t e = launch_exchange(b->djobs, (int)b->jobs.size(), b->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batch exchange");
+    for (potts_lr_t* h : b->jobs) h->nexch += 1u;
+    return batch_end(b);
+}
+
+// measure every slot of every job into meas_E / meas_M of each job, then
+// gather them into E / M (device arrays, job order)
+static int batch_measure_enqueue(potts_lr_batch_t* b, double* E, double* M, cudaMemcpyKind kind)
+{
+    int rc = batch_begin(b);
+    if (rc) return rc;
+    cudaError_t e = launch_measure(b->djobs, b->dmeas, b->nmeas, 0, 0, b->meas_smem, b->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batch measure");
+    for (size_t i = 0; i < b->jobs.size(); ++i) {
+        const potts_lr_t* h = b->jobs[i];
+        const size_t bytes = (size_t)h->R * sizeof(double);
+        if (E) PLR_CUDA(cudaMemcpyAsync(E + b->meas_off[i], h->hj.meas_E, bytes, kind, b->stream));
+        if (M) PLR_CUDA(cudaMemcpyAsync(M + b->meas_off[i], h->hj.meas_M, bytes, kind, b->stream));
+    }
+    return batch_end(b);
+}
+
+int potts_lr_batch_measure_device(potts_lr_batch_t* b, double* E, double* M)
+{
+    if (!b) return fail(POTTS_LR_EINVAL, "batch is NULL");
+    return batch_measure_enqueue(b, E, M, cudaMemcpyDeviceToDevice);
+}
+
+int potts_lr_batch_measure(potts_lr_batch_t* b, double* E, double* M)
+{
+    if (!b) return fail(POTTS_LR_EINVAL, "batch is NULL");
+    int rc = batch_measure_enqueue(b, b->meas_buf, b->meas_buf + b->nmeas, cudaMemcpyDeviceToDevice);
+    if (rc) return rc;
+    const size_t bytes = (size_t)b->nmeas * sizeof(double);
+    std::vector<double> host(2 * (size_t)b->nmeas);
+    PLR_CUDA(cudaMemcpyAsync(host.data(), b->meas_buf, 2 * bytes, cudaMemcpyDeviceToHost, b->stream));
+    PLR_CUDA(cudaStreamSynchronize(b->stream));
+    if (E) std::memcpy(E, host.data(), bytes);
+    if (M) std::memcpy(M, host.data() + b->nmeas, bytes);
+    return POTTS_LR_OK;
+}
+
+int potts_lr_batch_run(potts_lr_batch_t* b, int nsteps, int steps_per_graph)
+{
+    if (!b) return fail(POTTS_LR_EINVAL, "batch is NULL");
+    if (nsteps < 0) return fail(POTTS_LR_EINVAL, "nsteps must be >= 0");
+    if (steps_per_graph <= 0) steps_per_graph = 10;
+    int rc = batch_begin(b);  // order after each job's pending work
+    if (rc) return rc;
+    if (nsteps >= steps_per_graph && (!b->exec || b->exec_steps != steps_per_graph)) {
+        if (b->exec) {
+            cudaGraphExecDestroy(b->exec);
+            b->exec = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        PLR_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed));
+        cudaError_t e = cudaSuccess;
+        for (int s = 0; s < steps_per_graph && e == cudaSuccess; ++s) e = batch_enqueue_step(b);
+        cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+        if (e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return cuda_fail(e, "batch capture");
+        }
+        if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&b->exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            b->exec = nullptr;
+            return cuda_fail(e, "cudaGraphInstantiate");
+        }
+        b->exec_steps = steps_per_graph;
+    }
+    int left = nsteps;
+    while (left >= steps_per_graph) {
+        PLR_CUDA(cudaGraphLaunch(b->exec, b->stream));
+        left -= steps_per_graph;
+    }
+    for (; left > 0; --left) {
+        cudaError_t e = batch_enqueue_step(b);
+        if (e != cudaSuccess) return cuda_fail(e, "batch step");
+    }
+    for (potts_lr_t* h : b->jobs) {
+        h->nsweep += (uint32_t)nsteps;
+        h->nexch += (uint32_t)nsteps;
+    }
+    return batch_end(b);
+}
+
+int potts_lr_batch_sync(potts_lr_batch_t* b)
+{
+    if (!b) return fail(POTTS_LR_EINVAL, "batch is NULL");
+    PLR_CUDA(cudaStreamSynchronize(b->stream));
+    return POTTS_LR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,70 @@
+// Internal declarations shared by the CUDA translation units of libpotts_lr.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace plr {
+
+constexpr int kSweepThreads = 256;  // threads of one sweep CTA (one CTA per slot)
+constexpr int kSiteBlock = 32;      // sites decided by one warp between field updates
+constexpr int kAuxThreads = 256;    // threads of the init / measure / rebuild CTAs
+constexpr int kMaxQ = 16;           // largest q (4-bit packed spins)
+constexpr int kMaxL = 65536;        // largest L (16-bit positions in the direct rebuild)
+
+// Everything a kernel needs to know about one job, resident in device memory.
+// Arrays indexed by "replica" follow the configuration; arrays indexed by
+// "slot" belong to a temperature.  map[slot] = replica currently at that slot.
+struct JobDev {
+    int L, q, Lpad, W, R, c, precision;
+    int recompute_every;  // FP32 mode: rebuild fields after sweeps n with (n+1) % K == 0
+    int h_smem, j_smem;   // sweep kernel: fields / coupling table staged in shared memory
+    uint32_t key0, key1;  // Philox key (seed low, high)
+    double jtot;          // sum_r J*(r)
+    const double* J64d;   // doubled table: J64d[m] = J*(m mod L), m = 0..2L-1
+    const float* J32d;    // the same in FP32
+    uint32_t* spins;      // [replica][W] packed, 4 bits per spin, spin i at bits 4(i%8) of word i/8
+    void* fields;         // [replica][q][Lpad], double (FP64) or float (FP32)
+    double* E;            // running energy per replica
+    int* map;             // slot -> replica
+    const double* beta;   // per slot
+    uint32_t* nsweep;     // sweeps done, per slot
+    uint32_t* nexch;      // exchange steps done [1]
+    unsigned long long* acc_flip;  // per slot
+    unsigned long long* acc_swap;  // per pair (t, t+1), R entries
+    unsigned long long* near;      // [2]: Metropolis, exchange near ties
+    double* meas_E;       // per slot, written by the measure kernel
+    double* meas_M;
+    unsigned long long* err_bits;  // fields_error result (double bits, max)
+};
+
+// ---- host-side helpers (jstar.cpp) ----
+void jstar_table(int L, double sigma, double* out);
+
+// ---- launchers (each returns the cudaError_t of the launch) ----
+// work[i] = {job index, slot}; one CTA per work item
+cudaError_t launch_init_spins(const JobDev* jobs_dev, int job, int L, int W, int R, cudaStream_t st);
+cudaError_t launch_sweep(const JobDev* jobs_dev, const int2* work, int nwork, int nsweeps, int precision,
+                         size_t smem_bytes, cudaStream_t st);
+cudaError_t launch_exchange(const JobDev* jobs_dev, int njobs, cudaStream_t st);
+// "cond" arguments: when nonzero the kernel does nothing unless the job's
+// sweep counter is a positive multiple of its recompute_every (a rebuild that
+// is due), which lets a captured CUDA graph carry the rebuild every step.
+// anchor: 0 = measure only, 1 = measure and re-anchor the running energy.
+cudaError_t launch_measure(const JobDev* jobs_dev, const int2* work, int nwork, int anchor, int cond,
+                           size_t smem_bytes, cudaStream_t st);
+// FP64 direct rebuild of the fields of every replica of job jobs_dev[0]
+// (grid over element tiles x replicas).  mode 0: write fields; mode 1: compare
+// with the stored fields and fold max |diff| / jtot into err_bits.
+cudaError_t launch_fields_direct(const JobDev* job_dev, int L, int R, int mode, int cond, size_t smem_bytes,
+                                 cudaStream_t st);
+// FP32 mode: the split-BF16 tensor-core rebuild H = C . onehot(S) of job
+// jobs_dev[0]; returns cudaErrorNotSupported if the shape is outside its tiling.
+cudaError_t launch_fields_tc(const JobDev* job_dev, int L, int q, int R, int cond, cudaStream_t st);
+
+size_t sweep_smem_bytes(const JobDev& j);
+size_t measure_smem_bytes(int L, int W);
+size_t direct_smem_bytes(int L, int q);
+
+}  // namespace plr
