@@ -195,6 +195,13 @@ int potts_lr_batch_measure_device(potts_lr_batch_t* b, double* E, double* M);
 int potts_lr_batch_sync(potts_lr_batch_t* b);
 void potts_lr_batch_destroy(potts_lr_batch_t* b);
 
+/* Measurement utility (the paper has no counterpart): throughput of this
+ * GPU's FP64 add pipe (what = 0, adds/s), FP32 add pipe (what = 1, adds/s) or
+ * shared memory (what = 2, bytes/s loaded + stored), measured with CUDA
+ * events on the current device; the roofline denominators of the sweep
+ * kernel.  Synchronous; allocates 16 bytes of device memory for the call. */
+int potts_lr_probe(int what, double* value);
+
 #ifdef __cplusplus
 }
 #endif

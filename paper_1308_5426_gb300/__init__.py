@@ -32,6 +32,15 @@ def jtot(L: int, sigma: float) -> float:
     return float(jstar(L, sigma)[1:].sum())
 
 
+def probe(what: str) -> float:
+    """Measured throughput of this GPU: "fp64_add", "fp32_add" (adds/s) or
+    "smem" (shared-memory bytes/s) -- roofline denominators."""
+    lib = _lib.load()
+    v = ctypes.c_double()
+    _lib.check(lib.potts_lr_probe({"fp64_add": 0, "fp32_add": 1, "smem": 2}[what], ctypes.byref(v)))
+    return v.value
+
+
 class Job:
     """One PT job on the GPU (potts_lr_create).
 

@@ -75,7 +75,7 @@ struct potts_lr_batch {
     JobDev* djobs;
     void* arena;
     struct Group {
-        int precision;
+        int precision, h_smem, j_smem;
         int2* dwork;
         int nwork;
         size_t smem;
@@ -282,12 +282,18 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
     j.meas_E = (double*)(base + o_mE);
     j.meas_M = (double*)(base + o_mM);
     j.err_bits = (unsigned long long*)(base + o_err);
-    // residency of the sweep kernel's working set
-    const size_t hbytes = (size_t)q * Lp * h->wsize, jbytes = 2 * Lp * h->wsize, rest = Lp + 3 * kSiteBlock * 4;
-    j.h_smem = (hbytes + jbytes + rest <= kSmemBudget) ? 1 : 0;
-    j.j_smem = (jbytes + rest + (j.h_smem ? hbytes : 0) <= kSmemBudget) ? 1 : 0;
-    if (!j.h_smem && hbytes + rest <= kSmemBudget) j.h_smem = 1;  // fields first, table from L2
-    j.j_smem = (jbytes + rest + (j.h_smem ? hbytes : 0) <= kSmemBudget) ? 1 : 0;
+    // residency of the sweep kernel's working set: fields and table in shared
+    // memory when they fit, else fields first, else the table, else neither
+    {
+        const int opts_hs[4] = {1, 1, 0, 0}, opts_js[4] = {1, 0, 1, 0};
+        for (int v = 0; v < 4; ++v) {
+            if (sweep_smem_bytes_for(h->precision, L, h->Lpad, q, opts_hs[v], opts_js[v]) <= kSmemBudget) {
+                j.h_smem = opts_hs[v];
+                j.j_smem = opts_js[v];
+                break;
+            }
+        }
+    }
     h->dj = (JobDev*)(base + o_job);
     h->dwork = (int2*)(base + o_work);
     h->sweep_smem = sweep_smem_bytes(j);
@@ -327,7 +333,8 @@ int potts_lr_sweep(potts_lr_t* h, int n)
     while (n > 0) {
         int chunk = n;
         if (h->K > 0) chunk = std::min(n, h->K - (int)(h->nsweep % (uint32_t)h->K));
-        cudaError_t e = launch_sweep(h->dj, h->dwork, h->R, chunk, h->precision, h->sweep_smem, h->stream);
+        cudaError_t e = launch_sweep(h->dj, h->dwork, h->R, chunk, h->precision, h->hj.h_smem, h->hj.j_smem,
+                                     h->sweep_smem, h->stream);
         if (e != cudaSuccess) return cuda_fail(e, "sweep kernel");
         h->nsweep += (uint32_t)chunk;
         n -= chunk;
@@ -602,19 +609,19 @@ int potts_lr_batch_create(potts_lr_t* const* jobs, int n, void* cuda_stream, pot
         potts_lr_batch_destroy(b);
         return cuda_fail(e, "cudaEventCreate");
     }
-    // work tables per precision, longest slots first (the largest L q costs most)
+    // work tables per kernel variant (precision, residency), longest slots first
     std::vector<JobDev> hjobs(n);
-    std::vector<std::vector<int2>> works(2);
-    std::vector<size_t> smem(2, 0);
+    std::vector<std::vector<int2>> works(8);
+    std::vector<size_t> smem(8, 0);
     for (int i = 0; i < n; ++i) {
         hjobs[i] = jobs[i]->hj;
-        const int p = jobs[i]->precision;
-        for (int t = 0; t < jobs[i]->R; ++t) works[p].push_back(make_int2(i, t));
-        smem[p] = std::max(smem[p], jobs[i]->sweep_smem);
-        if (p == POTTS_LR_FP32 && jobs[i]->K > 0) b->fp32_jobs.push_back(i);
+        const int v = jobs[i]->precision * 4 + jobs[i]->hj.h_smem * 2 + jobs[i]->hj.j_smem;
+        for (int t = 0; t < jobs[i]->R; ++t) works[v].push_back(make_int2(i, t));
+        smem[v] = std::max(smem[v], jobs[i]->sweep_smem);
+        if (jobs[i]->precision == POTTS_LR_FP32 && jobs[i]->K > 0) b->fp32_jobs.push_back(i);
     }
-    for (int p = 0; p < 2; ++p)
-        std::stable_sort(works[p].begin(), works[p].end(), [&](const int2& x, const int2& y) {
+    for (int v = 0; v < 8; ++v)
+        std::stable_sort(works[v].begin(), works[v].end(), [&](const int2& x, const int2& y) {
             const potts_lr_t* a = jobs[x.x];
             const potts_lr_t* c = jobs[y.x];
             return (long long)a->L * (a->q + 8) > (long long)c->L * (c->q + 8);
@@ -627,10 +634,11 @@ int potts_lr_batch_create(potts_lr_t* const* jobs, int n, void* cuda_stream, pot
     }
     b->nmeas = (int)mwork.size();
     size_t bytes = align256(n * sizeof(JobDev));
-    const size_t o_w0 = bytes;
-    bytes += align256(works[0].size() * sizeof(int2) + 8);
-    const size_t o_w1 = bytes;
-    bytes += align256(works[1].size() * sizeof(int2) + 8);
+    size_t ow[8];
+    for (int v = 0; v < 8; ++v) {
+        ow[v] = bytes;
+        bytes += align256(works[v].size() * sizeof(int2) + 8);
+    }
     const size_t o_m = bytes;
     bytes += align256(mwork.size() * sizeof(int2));
     const size_t o_mb = bytes;
@@ -643,16 +651,17 @@ int potts_lr_batch_create(potts_lr_t* const* jobs, int n, void* cuda_stream, pot
     b->djobs = (JobDev*)b->arena;
     b->dmeas = (int2*)((char*)b->arena + o_m);
     b->meas_buf = (double*)((char*)b->arena + o_mb);
-    const size_t ow[2] = {o_w0, o_w1};
-    for (int p = 0; p < 2; ++p) {
-        if (works[p].empty()) continue;
+    for (int v = 0; v < 8; ++v) {
+        if (works[v].empty()) continue;
         potts_lr_batch_t::Group g;
-        g.precision = p;
-        g.dwork = (int2*)((char*)b->arena + ow[p]);
-        g.nwork = (int)works[p].size();
-        g.smem = smem[p];
+        g.precision = v >> 2;
+        g.h_smem = (v >> 1) & 1;
+        g.j_smem = v & 1;
+        g.dwork = (int2*)((char*)b->arena + ow[v]);
+        g.nwork = (int)works[v].size();
+        g.smem = smem[v];
         b->groups.push_back(g);
-        e = cudaMemcpyAsync(g.dwork, works[p].data(), works[p].size() * sizeof(int2), cudaMemcpyHostToDevice,
+        e = cudaMemcpyAsync(g.dwork, works[v].data(), works[v].size() * sizeof(int2), cudaMemcpyHostToDevice,
                             b->stream);
         if (e != cudaSuccess) break;
     }
@@ -673,7 +682,9 @@ static cudaError_t batch_enqueue_sweeps(potts_lr_batch_t* b)
 {
     cudaError_t e;
     for (const auto& g : b->groups)
-        if ((e = launch_sweep(b->djobs, g.dwork, g.nwork, 1, g.precision, g.smem, b->stream)) != cudaSuccess) return e;
+        if ((e = launch_sweep(b->djobs, g.dwork, g.nwork, 1, g.precision, g.h_smem, g.j_smem, g.smem, b->stream)) !=
+            cudaSuccess)
+            return e;
     for (int i : b->fp32_jobs)
         if ((e = rebuild_launch(b->jobs[i], b->djobs + i, 1, b->stream)) != cudaSuccess) return e;
     return cudaSuccess;

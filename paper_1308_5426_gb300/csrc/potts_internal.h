@@ -45,8 +45,9 @@ void jstar_table(int L, double sigma, double* out);
 // ---- launchers (each returns the cudaError_t of the launch) ----
 // work[i] = {job index, slot}; one CTA per work item
 cudaError_t launch_init_spins(const JobDev* jobs_dev, int job, int L, int W, int R, cudaStream_t st);
+// the kernel variant (precision, fields in smem, table in smem) is uniform per launch
 cudaError_t launch_sweep(const JobDev* jobs_dev, const int2* work, int nwork, int nsweeps, int precision,
-                         size_t smem_bytes, cudaStream_t st);
+                         int h_smem, int j_smem, size_t smem_bytes, cudaStream_t st);
 cudaError_t launch_exchange(const JobDev* jobs_dev, int njobs, cudaStream_t st);
 // "cond" arguments: when nonzero the kernel does nothing unless the job's
 // sweep counter is a positive multiple of its recompute_every (a rebuild that
@@ -64,6 +65,7 @@ cudaError_t launch_fields_direct(const JobDev* job_dev, int L, int R, int mode, 
 cudaError_t launch_fields_tc(const JobDev* job_dev, int L, int q, int R, int cond, cudaStream_t st);
 
 size_t sweep_smem_bytes(const JobDev& j);
+size_t sweep_smem_bytes_for(int precision, int L, int Lpad, int q, int h_smem, int j_smem);
 size_t measure_smem_bytes(int L, int W);
 size_t direct_smem_bytes(int L, int q);
 

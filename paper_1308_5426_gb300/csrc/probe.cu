@@ -1,0 +1,101 @@
+// Throughput probes for roofline denominators: FP64 add, FP32 add and
+// shared-memory bandwidth of this GPU, measured with CUDA events on a private
+// stream.  Each probe kernel runs long independent dependency chains at full
+// occupancy so that the pipe (not latency) is the limit.
+#include <cstring>
+
+#include "../../include/potts_lr.h"
+#include "potts_internal.h"
+
+namespace plr {
+namespace {
+
+constexpr int kProbeThreads = 256;
+constexpr int kProbeIters = 4096;
+
+template <typename T>
+__global__ void __launch_bounds__(kProbeThreads) add_probe(T* out, T seed)
+{
+    // 8 independent accumulator chains per thread, 2 adds each per iteration
+    T a[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) a[c] = seed * (T)(threadIdx.x + c);
+    const T d0 = seed * (T)1e-3, d1 = seed * (T)-1e-3;
+    for (int it = 0; it < kProbeIters; ++it) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            a[c] += d0;
+            a[c] += d1;
+        }
+    }
+    T s = 0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) s += a[c];
+    if (s == (T)123456.789) out[0] = s;  // keeps the chains alive
+}
+
+__global__ void __launch_bounds__(kProbeThreads) smem_probe(float* out, int iters)
+{
+    // each warp streams float loads and stores over its own 4 KB of shared memory
+    __shared__ float buf[kProbeThreads * 4];
+    const int tid = threadIdx.x;
+    for (int i = tid; i < kProbeThreads * 4; i += kProbeThreads) buf[i] = (float)i;
+    __syncthreads();
+    const int w = tid >> 5, lane = tid & 31;
+    volatile float* base = buf + w * 128;  // every access goes to shared memory
+    float acc = 0.0f;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const float v = base[r * 32 + lane];
+            acc += v;
+            base[((r + 1) & 3) * 32 + lane] = v + 1.0f;
+        }
+    }
+    if (acc == 123456.0f) out[0] = acc;
+}
+
+}  // namespace
+}  // namespace plr
+
+using namespace plr;
+
+extern "C" int potts_lr_probe(int what, double* value)
+{
+    if (!value || what < 0 || what > 2) return POTTS_LR_EINVAL;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return POTTS_LR_ECUDA;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return POTTS_LR_ECUDA;
+    cudaStream_t st;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return POTTS_LR_ECUDA;
+    void* out = nullptr;
+    cudaEvent_t e0, e1;
+    int rc = POTTS_LR_OK;
+    if (cudaMalloc(&out, 16) != cudaSuccess) {
+        cudaStreamDestroy(st);
+        return POTTS_LR_ENOMEM;
+    }
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int blocks = sms * 8;  // 2048 threads per SM
+    const int smem_iters = 1 << 16;
+    double work = 0.0;
+    for (int rep = 0; rep < 2; ++rep) {  // first pass warms up
+        cudaEventRecord(e0, st);
+        if (what == 0) add_probe<double><<<blocks, kProbeThreads, 0, st>>>((double*)out, 1.0);
+        else if (what == 1) add_probe<float><<<blocks, kProbeThreads, 0, st>>>((float*)out, 1.0f);
+        else smem_probe<<<blocks, kProbeThreads, 0, st>>>((float*)out, smem_iters);
+        cudaEventRecord(e1, st);
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) rc = POTTS_LR_ECUDA;
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (what <= 1) work = (double)blocks * kProbeThreads * kProbeIters * 16.0;  // adds
+    else work = (double)blocks * kProbeThreads * smem_iters * 4.0 * 2.0 * 4.0; // bytes (load + store)
+    *value = ms > 0.0f ? work / (ms * 1e-3) : 0.0;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    cudaStreamDestroy(st);
+    return rc;
+}

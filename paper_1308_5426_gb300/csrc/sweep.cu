@@ -1,21 +1,26 @@
 // Metropolis sweep of the long-range Potts chain (Eq. 8, Sec. 4.2 of the paper)
 // with local fields h[x][i] = sum_{j != i} J*(|i-j|) delta(x, s_j).
 //
-// One CTA per temperature slot.  The slot's spins (and, when they fit, its
-// fields and the doubled coupling table) are staged in shared memory.  Sites
-// are processed in blocks of 32:
-//   1. warp 0, lane l owns site k = k0 + l: draws its Philox numbers, proposes
-//      b, and reads d_l = h[a][k] - h[b][k] from the fields, which are current
-//      up to the previous block;
-//   2. the 32 decisions are then taken in site order; after an accepted flip
-//      j -> (a_j -> b_j) every later lane l corrects its d_l by
-//      J*(l - j) ([a_l = b_j] - [a_l = a_j] - [b_l = b_j] + [b_l = a_j]),
-//      which is exactly the change the rank-1 field update of flip j makes at
-//      site k_l -- so each decision sees the same dE as a strictly sequential
-//      sweep (dE = c (h[a][k] - h[b][k]), Eq. 2 and 8);
-//   3. all threads apply the block's accepted flips to the fields:
-//      h[a_j][i] -= J*(|i-k_j|), h[b_j][i] += J*(|i-k_j|), in flip order.
-// The periodic distance is read from the doubled table J*((i - k) mod L).
+// One CTA per temperature slot; 8 warps.  Sites are taken in blocks of 32 in
+// order k = 0..L-1.  Warp 0 decides a block; warps 1..7 meanwhile apply the
+// previous block's accepted flips to the fields (the rank-1 updates
+// h[a][i] -= J*(|i-k|), h[b][i] += J*(|i-k|)), except at the 32 sites of the
+// block being decided, which warp 0 brings up to date itself first.  One CTA
+// barrier per block.
+//
+// Deciding a block of 32 sites exactly as a sequential sweep would: lane l
+// holds site k0 + l, its proposal b_l, -ln u_l and d_l = h[a_l][k] - h[b_l][k]
+// (dE = c d, Eq. 2/8).  All undecided lanes evaluate their rule at once; the
+// first lane that accepts is then certain to accept (nothing before it
+// changed), every lane before it is certain to reject.  After an accepted flip
+// j, each later lane corrects d_l by J*(l-j)([a_l=b_j]-[a_l=a_j]-[b_l=b_j]+[b_l=a_j])
+// -- the change flip j makes to h at site k_l -- and the scan continues after j.
+// So a block costs one round per accepted flip, not one per site.
+//
+// FP64 mode decides in FP32 with a margin that bounds every FP32 rounding
+// (|d32 - d64| <= 1.2e-5 Jtot, see decide_fp64_filter); only when the margin is
+// too small does the lane rebuild d in FP64 and apply the FP64 rule
+// u < exp(-beta dE) itself.  FP32 mode decides in FP32.
 #include <cmath>
 
 #include "philox.cuh"
@@ -26,156 +31,275 @@ namespace plr {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kWarps = kSweepThreads / 32;
+enum : int { kReject = 0, kAccept = 1, kUnsure = 2 };
 
-// FP64-mode decision: the exact FP64 rule "dE <= 0 or u < exp(-beta dE)".
-// It is decided in FP32 when the FP32 margin is far wider than the rounding of
-// the FP32 evaluation (|x - (-ln u)| > 1e-6 + 1e-5 max(x, -ln u); the FP32
-// errors of x and -ln u are below 1e-6 relative), else in FP64.  A decision
-// with |beta dE + ln u| < 1e-9 is counted as a near tie.
-__device__ __forceinline__ bool decide64(double d, double cb, double c, double u, float nlu,
-                                         unsigned long long& near)
+template <typename T>
+struct SweepSmem {
+    // carve-up of the dynamic shared memory (must match sweep_smem_bytes)
+    static size_t bytes(int L, int Lpad, int q, bool hs, bool js)
+    {
+        (void)L;
+        size_t b = 0;
+        if (js) b += (size_t)Lpad * sizeof(T);
+        if (hs) b += (size_t)q * Lpad * sizeof(T);
+        b += (size_t)Lpad;                       // spins
+        b += 2 * 2 * kSiteBlock * sizeof(int);   // double-buffered flip lists
+        b += 32 * sizeof(float);                 // J* at distances 0..31 in FP32
+        b += kWarps * sizeof(double) + 16;       // reduction scratch, counts
+        return (b + 15) & ~(size_t)15;
+    }
+};
+
+// FP64 rule, evaluated exactly: dE <= 0 or u < exp(-beta dE); near-tie count.
+__device__ __forceinline__ bool decide_fp64_exact(double d, double cb, double u, unsigned long long& near)
 {
-    const double dE = c * d;
-    if (dE <= 0.0) return true;
+    if (d <= 0.0) return true;
     const double x = cb * d;  // beta * c * d
-    const float xf = (float)x;
-    const float m = 1e-6f + 1e-5f * fmaxf(xf, nlu);
-    if (xf < nlu - m) return true;
-    if (xf > nlu + m) return false;
     const bool acc = u < exp(-x);
     if (fabs(x + log(u)) < 1e-9) ++near;
     return acc;
 }
 
-// FP32-mode decision: dE <= 0 or beta dE < -ln u, in FP32.
-__device__ __forceinline__ bool decide32(float d, float cb, float nlu)
+// FP32 filter of the FP64 rule.  d32 is within errd of the FP64 d (errd = 1.2e-5 Jtot
+// bounds the conversion and up to 32 FP32 corrections of magnitude <= 3 Jtot,
+// each rounded to 2^-24, with a factor 2 to spare); x and -ln u are within
+// 1.2e-7 relative of their FP64 values.
+__device__ __forceinline__ int decide_fp64_filter(float d, float cb, float nlu, float errd)
 {
-    if (d <= 0.0f) return true;
-    return cb * d < nlu;
+    if (d <= -errd) return kAccept;
+    if (d < errd) return kUnsure;
+    const float x = cb * d;
+    const float m = cb * errd + 1e-6f * (x + nlu + 1.0f);
+    if (x < nlu - m) return kAccept;
+    if (x > nlu + m) return kReject;
+    return kUnsure;
 }
 
+// Rank-1 updates of the flips (pk, pab)[0..nf), in flip order, on every
+// element except [x0, x0 + nx): h[a][i] -= J*((i-k) mod L), h[b][i] += J*((i-k) mod L).
+// The elements form one index space j = 0..L-nx-1 (i = j, or j + nx past x0);
+// worker u of nw = kSweepThreads - 32 takes j = u + nw m (stride 1 across a
+// warp: conflict-free shared-memory access) four at a time, and applies all
+// flips to those four before moving on, so four independent read-modify-write
+// chains are in flight and the flip list is read once per four elements.
 template <typename T>
-__global__ void __launch_bounds__(kSweepThreads) sweep_kernel(const JobDev* __restrict__ jobs,
+__device__ __forceinline__ void apply_flips(T* __restrict__ h, const T* __restrict__ J, int L, int Lpad,
+                                            const int* pk, const int* pab, int nf, int x0, int nx, int u)
+{
+    constexpr int nw = kSweepThreads - 32;
+    const int n = L - nx;
+    int j = u;
+    for (; j + 3 * nw < n; j += 4 * nw) {
+        int idx[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int jj = j + e * nw;
+            idx[e] = jj < x0 ? jj : jj + nx;
+        }
+        for (int f = 0; f < nf; ++f) {
+            const int kf = pk[f], af = pab[f] >> 8, bf = pab[f] & 255;
+            T* __restrict__ ha = h + (size_t)af * Lpad;
+            T* __restrict__ hb = h + (size_t)bf * Lpad;
+            T v[4], xa[4], xb[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                int r = idx[e] - kf;
+                r += r < 0 ? L : 0;
+                v[e] = J[r];
+                xa[e] = ha[idx[e]];
+                xb[e] = hb[idx[e]];
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                ha[idx[e]] = xa[e] - v[e];
+                hb[idx[e]] = xb[e] + v[e];
+            }
+        }
+    }
+    for (; j < n; j += nw) {
+        const int i = j < x0 ? j : j + nx;
+        for (int f = 0; f < nf; ++f) {
+            const int kf = pk[f], af = pab[f] >> 8, bf = pab[f] & 255;
+            int r = i - kf;
+            r += r < 0 ? L : 0;
+            const T v = J[r];
+            h[(size_t)af * Lpad + i] -= v;
+            h[(size_t)bf * Lpad + i] += v;
+        }
+    }
+}
+
+template <typename T, bool HS, bool JS>
+__global__ void __launch_bounds__(kSweepThreads, 4) sweep_kernel(const JobDev* __restrict__ jobs,
                                                               const int2* __restrict__ work, int nsweeps)
 {
+    constexpr bool kFP64 = sizeof(T) == 8;
     extern __shared__ __align__(16) unsigned char smem[];
     const int2 wk = work[blockIdx.x];
-    const JobDev& jb = jobs[wk.x];
+    const JobDev* jp = jobs + wk.x;
     const int t = wk.y;
-    const int L = jb.L, q = jb.q, Lpad = jb.Lpad, W = jb.W;
-    const int rep = jb.map[t];
-    const double beta = jb.beta[t];
+    const int L = jp->L, q = jp->q, Lpad = jp->Lpad, W = jp->W, c = jp->c;
+    const uint32_t key0 = jp->key0, key1 = jp->key1;
+    const int rep = jp->map[t];
+    const double beta = jp->beta[t];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-    const T* Jg = (sizeof(T) == 8) ? (const T*)(const void*)jb.J64d : (const T*)(const void*)jb.J32d;
-    T* hg = (T*)jb.fields + (size_t)rep * q * Lpad;
-    uint32_t* spins = jb.spins + (size_t)rep * W;
+    const T* __restrict__ Jg = kFP64 ? (const T*)(const void*)jp->J64d : (const T*)(const void*)jp->J32d;
+    T* __restrict__ hg = (T*)jp->fields + (size_t)rep * q * Lpad;
+    uint32_t* __restrict__ spins = jp->spins + (size_t)rep * W;
 
-    // shared-memory carve-up (must match sweep_smem_bytes)
     size_t off = 0;
-    const T* Jd = Jg;
-    if (jb.j_smem) {
-        T* p = (T*)(smem + off);
-        for (int m = tid; m < 2 * L; m += kSweepThreads) p[m] = Jg[m];
-        Jd = p;
-        off += (size_t)2 * Lpad * sizeof(T);
+    T* Js = nullptr;
+    if constexpr (JS) {
+        Js = (T*)(smem + off);
+        off += (size_t)Lpad * sizeof(T);
     }
-    T* h = hg;
-    if (jb.h_smem) {
-        h = (T*)(smem + off);
-        const size_t n = (size_t)q * Lpad;
-        for (size_t e = tid; e < n; e += kSweepThreads) h[e] = hg[e];
-        off += n * sizeof(T);
+    T* hs = nullptr;
+    if constexpr (HS) {
+        hs = (T*)(smem + off);
+        off += (size_t)q * Lpad * sizeof(T);
     }
     uint8_t* s = smem + off;
     off += (size_t)Lpad;
-    int* fk = (int*)(smem + off);   // flip sites of the current block
-    int* fab = fk + kSiteBlock;     // (a << 8) | b
-    int* nfl = fab + kSiteBlock;    // number of flips
+    int* lk = (int*)(smem + off);      // [2][32] flip sites
+    int* lab = lk + 2 * kSiteBlock;    // [2][32] (a << 8) | b
+    float* Jn = (float*)(lab + 2 * kSiteBlock);  // J*(r), r < 32, FP32
+    double* red = (double*)(((uintptr_t)(Jn + 32) + 7) & ~(uintptr_t)7);
+    int* lcnt = (int*)(red + kWarps);  // [2] flip counts
 
+    if constexpr (JS)
+        for (int m = tid; m < Lpad; m += kSweepThreads) Js[m] = m < L ? Jg[m] : (T)0;
+    if constexpr (HS) {
+        const int n = q * Lpad;
+        for (int e = tid; e < n; e += kSweepThreads) hs[e] = hg[e];
+    }
     for (int i = tid; i < L; i += kSweepThreads) s[i] = (uint8_t)((spins[i >> 3] >> (4 * (i & 7))) & 15u);
+    if (tid < 32) Jn[tid] = tid < L ? (float)jp->J64d[tid] : 0.0f;
+    if (tid < 2) lcnt[tid] = 0;
     __syncthreads();
 
-    const uint32_t n0 = jb.nsweep[t];
-    const int c = jb.c;
+    T* __restrict__ h = HS ? hs : hg;
+    const T* __restrict__ J = JS ? (const T*)Js : Jg;  // J[r], r = 0..L-1 (J[0] = 0)
+
+    const uint32_t n0 = jp->nsweep[t];
     const double cb64 = beta * (double)c;
     const float cb32 = (float)cb64;
-    double dE_sum = 0.0;               // per lane of warp 0
+    const float errd = (float)(1.2e-5 * jp->jtot);
+    const int nblk = (L + kSiteBlock - 1) / kSiteBlock;
+    const int total = nsweeps * nblk;
+
+    double dE_acc = 0.0;                 // FP32 mode: running energy change (lane-local)
     unsigned long long nacc = 0, nnear = 0;
 
-    for (int it = 0; it < nsweeps; ++it) {
-        const uint32_t n = n0 + (uint32_t)it;
-        for (int k0 = 0; k0 < L; k0 += kSiteBlock) {
-            if (warp == 0) {
+    for (int g = 0; g <= total; ++g) {
+        const int pb = (g + 1) & 1;                // list of block g-1 (pending)
+        const int npend = g > 0 ? lcnt[pb] : 0;
+        const int* pk = lk + pb * kSiteBlock;
+        const int* pab = lab + pb * kSiteBlock;
+        const int k0 = g < total ? (g % nblk) * kSiteBlock : 0;
+        const int nv = g < total ? min(kSiteBlock, L - k0) : 0;
+
+        if (warp == 0) {
+            if (g < total) {
                 const int k = k0 + lane;
-                const int nv = min(kSiteBlock, L - k0);
                 const bool valid = lane < nv;
+                // bring this block's sites up to date with block g-1's flips
+                if (valid) {
+                    for (int f = 0; f < npend; ++f) {
+                        const int kf = pk[f], af = pab[f] >> 8, bf = pab[f] & 255;
+                        int r = k - kf;
+                        r += r < 0 ? L : 0;
+                        const T v = J[r];
+                        h[(size_t)af * Lpad + k] -= v;
+                        h[(size_t)bf * Lpad + k] += v;
+                    }
+                }
+                const uint32_t n = n0 + (uint32_t)(g / nblk);
                 int a = 0, b = 0;
-                double u = 1.0;
-                float nlu = 0.0f;
-                T d = (T)0;
+                float nlu = 0.0f, d32 = 0.0f;
+                double u = 1.0, base = 0.0;
                 if (valid) {
                     a = s[k];
-                    const U4 x = philox10(U4{(uint32_t)k, (uint32_t)t, n, kTagMetro}, jb.key0, jb.key1);
+                    const U4 x = philox10(U4{(uint32_t)k, (uint32_t)t, n, kTagMetro}, key0, key1);
                     b = a + 1 + (int)__umulhi(x.x, (uint32_t)(q - 1));
                     if (b >= q) b -= q;
-                    if (sizeof(T) == 8) {
+                    if constexpr (kFP64) {
                         u = unit53(x.y, x.z);
                         nlu = -logf((float)u);
                     } else {
                         nlu = -logf(unit24(x.y));
                     }
-                    d = h[(size_t)a * Lpad + k] - h[(size_t)b * Lpad + k];
+                    const T dd = h[(size_t)a * Lpad + k] - h[(size_t)b * Lpad + k];
+                    base = (double)dd;
+                    d32 = (float)dd;
                 }
+                const int cbuf = g & 1;
+                int* ck = lk + cbuf * kSiteBlock;
+                int* cab = lab + cbuf * kSiteBlock;
+                int nf = 0;
                 bool mine = false;
-                for (int j = 0; j < nv; ++j) {
-                    bool dec = false;
-                    if (lane == j) {
-                        if (sizeof(T) == 8)
-                            dec = decide64((double)d, cb64, (double)c, u, nlu, nnear);
-                        else
-                            dec = decide32((float)d, cb32, nlu);
-                        if (dec) {
-                            mine = true;
-                            dE_sum += (double)c * (double)d;
+                float dmine = 0.0f;
+                int p = 0;
+                while (p < nv) {
+                    int st = kReject;
+                    if (valid && lane >= p) {
+                        if constexpr (kFP64) st = decide_fp64_filter(d32, cb32, nlu, errd);
+                        else st = (d32 <= 0.0f || cb32 * d32 < nlu) ? kAccept : kReject;
+                    }
+                    const unsigned hit = __ballot_sync(kFull, st != kReject);
+                    if (!hit) break;
+                    const int j = __ffs(hit) - 1;
+                    bool acc = true;
+                    if constexpr (kFP64) {
+                        const int stj = __shfl_sync(kFull, st, j);
+                        if (stj == kUnsure) {
+                            bool dec = false;
+                            if (lane == j) {
+                                double d64 = base;
+                                for (int f = 0; f < nf; ++f) {
+                                    const int kf = ck[f], af = cab[f] >> 8, bf = cab[f] & 255;
+                                    const int coef = (a == bf) - (a == af) - (b == bf) + (b == af);
+                                    if (coef) d64 += (double)coef * (double)J[k - kf];
+                                }
+                                dec = decide_fp64_exact(d64, cb64, u, nnear);
+                            }
+                            acc = __shfl_sync(kFull, dec, j);
                         }
                     }
-                    if (__ballot_sync(kFull, dec)) {
+                    if (acc) {
                         const int aj = __shfl_sync(kFull, a, j);
                         const int bj = __shfl_sync(kFull, b, j);
+                        if (lane == j) {
+                            mine = true;
+                            dmine = d32;
+                            ck[nf] = k;
+                            cab[nf] = (a << 8) | b;
+                        }
                         if (lane > j && valid) {
                             const int coef = (a == bj) - (a == aj) - (b == bj) + (b == aj);
-                            if (coef) d += (T)coef * Jd[lane - j];
+                            if (coef) d32 = fmaf((float)coef, Jn[lane - j], d32);
                         }
+                        ++nf;
+                        __syncwarp();
                     }
+                    p = j + 1;
                 }
-                const unsigned mask = __ballot_sync(kFull, mine);
                 if (mine) {
-                    const int pos = __popc(mask & ((1u << lane) - 1u));
-                    fk[pos] = k;
-                    fab[pos] = (a << 8) | b;
                     s[k] = (uint8_t)b;
+                    if constexpr (!kFP64) dE_acc += (double)((float)c * dmine);
                 }
                 if (lane == 0) {
-                    *nfl = __popc(mask);
-                    nacc += (unsigned long long)__popc(mask);
+                    lcnt[cbuf] = nf;
+                    nacc += (unsigned long long)nf;
                 }
             }
-            __syncthreads();
-            const int nf = *nfl;
-            for (int f = 0; f < nf; ++f) {
-                const int kf = fk[f], af = fab[f] >> 8, bf = fab[f] & 255;
-                T* ha = h + (size_t)af * Lpad;
-                T* hb = h + (size_t)bf * Lpad;
-                const T* Jc = Jd + (L - kf);  // Jc[i] = J*((i - kf) mod L)
-                for (int i = tid; i < L; i += kSweepThreads) {
-                    const T v = Jc[i];
-                    ha[i] -= v;
-                    hb[i] += v;
-                }
-            }
-            __syncthreads();
+        } else if (npend > 0) {
+            // apply block g-1's flips everywhere except at the sites warp 0 owns
+            // now: ranges [0, k0) and [k0 + nv, L)
+            apply_flips<T>(h, J, L, Lpad, pk, pab, npend, k0, nv, tid - 32);
         }
+        __syncthreads();
     }
 
     // write back
@@ -187,53 +311,78 @@ __global__ void __launch_bounds__(kSweepThreads) sweep_kernel(const JobDev* __re
         }
         spins[w] = word;
     }
-    if (jb.h_smem) {
-        const size_t ne = (size_t)q * Lpad;
-        for (size_t e = tid; e < ne; e += kSweepThreads) hg[e] = h[e];
+    if constexpr (HS) {
+        const int n = q * Lpad;
+        for (int e = tid; e < n; e += kSweepThreads) hg[e] = hs[e];
+    }
+    if constexpr (kFP64) {
+        // E = -(c/2) sum_i h[s_i][i] from the FP64 fields (Eq. 2 through the fields)
+        double part = 0.0;
+        for (int i = tid; i < L; i += kSweepThreads) part += (double)h[(size_t)s[i] * Lpad + i];
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(kFull, part, o);
+        if (lane == 0) red[warp] = part;
     }
     if (warp == 0) {
         for (int o = 16; o > 0; o >>= 1) {
-            dE_sum += __shfl_xor_sync(kFull, dE_sum, o);
+            dE_acc += __shfl_xor_sync(kFull, dE_acc, o);
             nnear += __shfl_xor_sync(kFull, nnear, o);
         }
-        if (lane == 0) {
-            jb.E[rep] += dE_sum;
-            jb.nsweep[t] = n0 + (uint32_t)nsweeps;
-            if (nacc) atomicAdd(&jb.acc_flip[t], nacc);
-            if (nnear) atomicAdd(&jb.near[0], nnear);
-        }
     }
+    __syncthreads();
+    if (tid == 0) {
+        if constexpr (kFP64) {
+            double tot = 0.0;
+            for (int w = 0; w < kWarps; ++w) tot += red[w];
+            jp->E[rep] = -0.5 * (double)c * tot;
+        } else {
+            jp->E[rep] += dE_acc;
+        }
+        jp->nsweep[t] = n0 + (uint32_t)nsweeps;
+        if (nacc) atomicAdd(&jp->acc_flip[t], nacc);
+        if (nnear) atomicAdd(&jp->near[0], nnear);
+    }
+}
+
+template <typename T, bool HS, bool JS>
+cudaError_t launch_variant(const JobDev* jobs_dev, const int2* work, int nwork, int nsweeps, size_t smem,
+                           cudaStream_t st)
+{
+    auto k = sweep_kernel<T, HS, JS>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<nwork, kSweepThreads, smem, st>>>(jobs_dev, work, nsweeps);
+    return cudaGetLastError();
 }
 
 }  // namespace
 
 size_t sweep_smem_bytes(const JobDev& j)
 {
-    const size_t w = j.precision == 0 ? 8 : 4;
-    size_t b = 0;
-    if (j.j_smem) b += (size_t)2 * j.Lpad * w;
-    if (j.h_smem) b += (size_t)j.q * j.Lpad * w;
-    b += (size_t)j.Lpad;
-    b += 3 * kSiteBlock * sizeof(int);
-    return b;
+    if (j.precision == 0) return SweepSmem<double>::bytes(j.L, j.Lpad, j.q, j.h_smem, j.j_smem);
+    return SweepSmem<float>::bytes(j.L, j.Lpad, j.q, j.h_smem, j.j_smem);
+}
+
+size_t sweep_smem_bytes_for(int precision, int L, int Lpad, int q, int h_smem, int j_smem)
+{
+    if (precision == 0) return SweepSmem<double>::bytes(L, Lpad, q, h_smem, j_smem);
+    return SweepSmem<float>::bytes(L, Lpad, q, h_smem, j_smem);
 }
 
 cudaError_t launch_sweep(const JobDev* jobs_dev, const int2* work, int nwork, int nsweeps, int precision,
-                         size_t smem_bytes, cudaStream_t st)
+                         int h_smem, int j_smem, size_t smem, cudaStream_t st)
 {
     if (nwork <= 0 || nsweeps <= 0) return cudaSuccess;
-    if (precision == 0) {
-        cudaError_t e = cudaFuncSetAttribute(sweep_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem_bytes);
-        if (e != cudaSuccess) return e;
-        sweep_kernel<double><<<nwork, kSweepThreads, smem_bytes, st>>>(jobs_dev, work, nsweeps);
-    } else {
-        cudaError_t e = cudaFuncSetAttribute(sweep_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem_bytes);
-        if (e != cudaSuccess) return e;
-        sweep_kernel<float><<<nwork, kSweepThreads, smem_bytes, st>>>(jobs_dev, work, nsweeps);
+    const int v = (precision ? 4 : 0) | (h_smem ? 2 : 0) | (j_smem ? 1 : 0);
+    switch (v) {
+    case 0: return launch_variant<double, false, false>(jobs_dev, work, nwork, nsweeps, smem, st);
+    case 1: return launch_variant<double, false, true>(jobs_dev, work, nwork, nsweeps, smem, st);
+    case 2: return launch_variant<double, true, false>(jobs_dev, work, nwork, nsweeps, smem, st);
+    case 3: return launch_variant<double, true, true>(jobs_dev, work, nwork, nsweeps, smem, st);
+    case 4: return launch_variant<float, false, false>(jobs_dev, work, nwork, nsweeps, smem, st);
+    case 5: return launch_variant<float, false, true>(jobs_dev, work, nwork, nsweeps, smem, st);
+    case 6: return launch_variant<float, true, false>(jobs_dev, work, nwork, nsweeps, smem, st);
+    default: return launch_variant<float, true, true>(jobs_dev, work, nwork, nsweeps, smem, st);
     }
-    return cudaGetLastError();
 }
 
 }  // namespace plr

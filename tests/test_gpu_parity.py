@@ -79,6 +79,21 @@ def test_parity_shapes(plr, L, q, sigma, R, c, seed):
     np.testing.assert_allclose(g.fields(), o.fields(), rtol=0, atol=1e-12 * oracle.jtot(L, sigma))
 
 
+@pytest.mark.parametrize("L,q,sigma,R,sweeps", [
+    (4096, 8, 0.2, 2, 3),    # FP64 fields (256 KB) stay in global memory, table in shared memory
+    (9000, 16, 0.7, 1, 1),   # neither fields nor table in shared memory, ragged L
+])
+def test_parity_fields_in_global_memory(plr, L, q, sigma, R, sweeps):
+    ratios = workloads.geometric_ratios(R, 0.05, 0.5)
+    g, o = _pair(plr, L, q, sigma, ratios, 21)
+    for _ in range(sweeps):
+        g.sweep(1)
+        g.exchange()
+        o.step(mode="field")
+    _compare(g, o, "global-memory fields L=%d" % L)
+    np.testing.assert_allclose(g.fields(), o.fields(), rtol=0, atol=1e-12 * oracle.jtot(L, sigma))
+
+
 def test_parity_multi_sweep_launch(plr):
     """sweep(n) with n > 1 in one launch equals n single sweeps."""
     L, q, sigma, R = 96, 5, 0.4, 4
