@@ -94,6 +94,22 @@ struct potts_lr_batch {
 
 namespace {
 
+uint16_t to_bf16(float f)
+{
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);  // round to nearest even
+    return (uint16_t)(u >> 16);
+}
+
+double from_bf16(uint16_t b)
+{
+    const uint32_t u = (uint32_t)b << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return (double)f;
+}
+
 int check_opts(const potts_lr_opts* o)
 {
     if (o->precision != POTTS_LR_FP64 && o->precision != POTTS_LR_FP32)
@@ -109,12 +125,11 @@ int check_opts(const potts_lr_opts* o)
 // job's descriptor in device memory (its own, or its entry in a batch table).
 cudaError_t rebuild_launch(const potts_lr_t* h, const JobDev* job_dev, int cond, cudaStream_t st)
 {
-    cudaError_t e = cudaErrorNotSupported;
-    if (h->precision == POTTS_LR_FP32) e = launch_fields_tc(job_dev, h->L, h->q, h->R, cond, st);
-    if (e == cudaErrorNotSupported) {
-        (void)cudaGetLastError();
+    cudaError_t e;
+    if (h->precision == POTTS_LR_FP32)
+        e = launch_fields_tc(job_dev, h->L, h->q, h->R, h->Lpad, h->hj.tc_tab_smem, cond, st);
+    else
         e = launch_fields_direct(job_dev, h->L, h->R, 0, cond, h->direct_smem, st);
-    }
     if (e != cudaSuccess) return e;
     return launch_measure(job_dev, h->dwork, h->R, 1, cond, h->measure_smem, st);
 }
@@ -123,6 +138,19 @@ int rebuild(potts_lr_t* h)
 {
     cudaError_t e = rebuild_launch(h, h->dj, 0, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "field rebuild");
+    return POTTS_LR_OK;
+}
+
+// after a stream synchronisation: report (and clear) an expired device wait
+int check_status(potts_lr_t* h)
+{
+    int st = 0;
+    cudaError_t e = cudaMemcpy(&st, h->hj.status, 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "status read");
+    if (st) {
+        cudaMemset(h->hj.status, 0, 4);
+        return fail(POTTS_LR_ETIMEOUT, "a bounded device wait expired (tensor-core rebuild); fields are invalid");
+    }
     return POTTS_LR_OK;
 }
 
@@ -217,6 +245,17 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
         J64d[m] = J[m % L];
         J32d[m] = (float)J[m % L];
     }
+    // BF16 parts hi + mid + lo of J* for the tensor-core rebuild (FP32 mode)
+    std::vector<uint16_t> split(3 * (size_t)h->Lpad, 0);
+    for (int r = 0; r < L; ++r) {
+        const uint16_t hi = to_bf16((float)J[r]);
+        const double r1 = J[r] - from_bf16(hi);
+        const uint16_t mid = to_bf16((float)r1);
+        const double r2 = r1 - from_bf16(mid);
+        split[r] = hi;
+        split[h->Lpad + r] = mid;
+        split[2 * (size_t)h->Lpad + r] = to_bf16((float)r2);
+    }
     std::vector<double> beta(R);
     for (int t = 0; t < R; ++t) beta[t] = 1.0 / temps[t];
     std::vector<int> map(R);
@@ -242,6 +281,7 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
     const size_t o_accf = take((size_t)R * 8), o_accs = take((size_t)R * 8), o_near = take(16);
     const size_t o_mE = take((size_t)R * 8), o_mM = take((size_t)R * 8), o_err = take(8);
     const size_t o_job = take(sizeof(JobDev)), o_work = take((size_t)R * sizeof(int2));
+    const size_t o_split = take(3 * Lp * 2), o_status = take(4);
     cudaError_t e = cudaMalloc(&h->arena, off);
     if (e != cudaSuccess) {
         potts_lr_destroy(h);
@@ -282,6 +322,9 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
     j.meas_E = (double*)(base + o_mE);
     j.meas_M = (double*)(base + o_mM);
     j.err_bits = (unsigned long long*)(base + o_err);
+    j.Jsplit = (const uint16_t*)(base + o_split);
+    j.tc_tab_smem = tc_table_in_smem(h->Lpad);
+    j.status = (int*)(base + o_status);
     // residency of the sweep kernel's working set: fields and table in shared
     // memory when they fit, else fields first, else the table, else neither
     {
@@ -310,6 +353,7 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
         if ((e = cudaMemcpyAsync(j.map, map.data(), (size_t)R * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
         if ((e = cudaMemcpyAsync(h->dj, &j, sizeof(JobDev), cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
         if ((e = cudaMemcpyAsync(h->dwork, work.data(), (size_t)R * sizeof(int2), cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
+        if ((e = cudaMemcpyAsync((void*)j.Jsplit, split.data(), 3 * Lp * 2, cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
         if ((e = launch_init_spins(h->dj, 0, L, h->W, R, st)) != cudaSuccess) break;
         if ((e = launch_fields_direct(h->dj, L, R, 0, 0, h->direct_smem, st)) != cudaSuccess) break;
         if ((e = launch_measure(h->dj, h->dwork, R, 1, 0, h->measure_smem, st)) != cudaSuccess) break;
@@ -377,7 +421,7 @@ int potts_lr_measure(potts_lr_t* h, double* E, double* M)
     PLR_CUDA(cudaStreamSynchronize(h->stream));
     if (E) std::memcpy(E, h->pinned, b);
     if (M) std::memcpy(M, h->pinned + h->R, b);
-    return POTTS_LR_OK;
+    return check_status(h);
 }
 
 int potts_lr_fields_recompute(potts_lr_t* h)
@@ -396,14 +440,14 @@ int potts_lr_fields_error(potts_lr_t* h, double* max_err)
     PLR_CUDA(cudaMemcpyAsync(&bits, h->hj.err_bits, 8, cudaMemcpyDeviceToHost, h->stream));
     PLR_CUDA(cudaStreamSynchronize(h->stream));
     std::memcpy(max_err, &bits, 8);
-    return POTTS_LR_OK;
+    return check_status(h);
 }
 
 int potts_lr_sync(potts_lr_t* h)
 {
     if (!h) return fail(POTTS_LR_EINVAL, "handle is NULL");
     PLR_CUDA(cudaStreamSynchronize(h->stream));
-    return POTTS_LR_OK;
+    return check_status(h);
 }
 
 int potts_lr_counters(potts_lr_t* h, uint32_t* nsweep, uint32_t* nexch)
@@ -827,6 +871,10 @@ int potts_lr_batch_sync(potts_lr_batch_t* b)
 {
     if (!b) return fail(POTTS_LR_EINVAL, "batch is NULL");
     PLR_CUDA(cudaStreamSynchronize(b->stream));
+    for (potts_lr_t* h : b->jobs) {
+        int rc = check_status(h);
+        if (rc) return rc;
+    }
     return POTTS_LR_OK;
 }
 

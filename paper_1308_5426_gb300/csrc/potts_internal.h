@@ -37,6 +37,9 @@ struct JobDev {
     double* meas_E;       // per slot, written by the measure kernel
     double* meas_M;
     unsigned long long* err_bits;  // fields_error result (double bits, max)
+    const uint16_t* Jsplit;        // FP32 mode: BF16 parts hi, mid, lo of J*, [3][Lpad]
+    int tc_tab_smem;               // tensor-core rebuild stages the split table in shared memory
+    int* status;                   // 0 ok; 1 a bounded device wait expired
 };
 
 // ---- host-side helpers (jstar.cpp) ----
@@ -61,8 +64,10 @@ cudaError_t launch_measure(const JobDev* jobs_dev, const int2* work, int nwork, 
 cudaError_t launch_fields_direct(const JobDev* job_dev, int L, int R, int mode, int cond, size_t smem_bytes,
                                  cudaStream_t st);
 // FP32 mode: the split-BF16 tensor-core rebuild H = C . onehot(S) of job
-// jobs_dev[0]; returns cudaErrorNotSupported if the shape is outside its tiling.
-cudaError_t launch_fields_tc(const JobDev* job_dev, int L, int q, int R, int cond, cudaStream_t st);
+// job_dev[0] (any L, q, R).
+cudaError_t launch_fields_tc(const JobDev* job_dev, int L, int q, int R, int Lpad, int tab_smem, int cond,
+                             cudaStream_t st);
+int tc_table_in_smem(int Lpad);
 
 size_t sweep_smem_bytes(const JobDev& j);
 size_t sweep_smem_bytes_for(int precision, int L, int Lpad, int q, int h_smem, int j_smem);

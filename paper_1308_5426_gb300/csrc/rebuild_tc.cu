@@ -1,12 +1,267 @@
-// FP32-mode field rebuild H = C . onehot(S) on the tensor cores (written next).
+// FP32-mode field rebuild on the tensor cores:
+//   H[i][n] = sum_j C[i][j] X[j][n],   C[i][j] = J*((i - j) mod L)   (J*(0) = 0),
+//   X[j][n] = delta(x_n, s_{r_n, j}),  n = r q + x  (replica r, state x),
+// so H[i][r q + x] = h_r[x][i], the local fields of every replica at once (the
+// fields are sums over sites of the coupling to the site's state, Eq. 2).
+//
+// tcgen05.mma kind::f16 with BF16 operands and FP32 accumulation in tensor
+// memory.  X is exact in BF16 (0 or 1); C is carried as three BF16 parts
+// hi + mid + lo of the FP64 J* (representation error ~2^-25 J*), each part one
+// MMA per K-step.  One CTA computes a 128 x 64 tile of H over
+// all of K in chunks of 64 sites: the four warps build the operand tiles in
+// shared memory from the split table and the packed spins, one thread issues
+// the 12 MMAs of the chunk (4 K-steps x 3 parts) and commits them to an
+// mbarrier.  The tensor core's FP32 accumulation rounds every MMA's sum into
+// the accumulator, so the accumulation chains are kept short: the hi parts of
+// successive chunks rotate over seven accumulators, and the small mid + lo
+// parts go to an eighth of their own (their rounding is then relative to their
+// own small size).  8 accumulators x 64 columns = 512 TMEM columns; the
+// epilogue adds them in FP64 and stores FP32 fields.
+//
+// Operand layout (both K-major, no swizzle): 8-row x 16-byte core matrices;
+// core matrix (row group g, K group c) of a tile with G row groups and 64 K
+// sites at byte (c G + g) 128, so the leading (K) byte offset is 128 G and the
+// stride (row-group) byte offset is 128; K-step s (16 sites) starts at 256 G s.
+#include <cstdint>
+
 #include "potts_internal.h"
 
 namespace plr {
 
-cudaError_t launch_fields_tc(const JobDev* job_dev, int L, int q, int R, int cond, cudaStream_t st)
+namespace {
+
+constexpr int kTcThreads = 128;
+constexpr int kTileM = 128;
+constexpr int kTileN = 64;
+constexpr int kChunk = 64;           // K sites per chunk
+constexpr int kAcc = 8;              // accumulators (kAcc * kTileN = 512 TMEM columns)
+constexpr int kAccHi = kAcc - 1;     // rotating accumulators of the hi parts; the last takes mid + lo
+constexpr int kTileBytes = kTileM * kChunk * 2;  // 16 KB per 128 x 64 BF16 A tile
+constexpr int kTileBytesB = kTileN * kChunk * 2; // 8 KB per 64 x 64 BF16 B tile
+constexpr int kGA = kTileM / 8, kGB = kTileN / 8;  // row groups of the A and B tiles
+constexpr int kSplit = 3;
+constexpr uint32_t kTmemCols = kAcc * kTileN;
+constexpr long long kWaitLimit = 1ll << 26;  // bounded mbarrier wait (iterations)
+constexpr size_t kTcMinSmem = 120 * 1024;   // forces one CTA per SM (owner of all 512 columns)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
 {
-    (void)job_dev; (void)L; (void)q; (void)R; (void)cond; (void)st;
-    return cudaErrorNotSupported;
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= 1ull << 46;  // descriptor version for tcgen05; layout type 0 = no swizzle
+    return d;
+}
+
+// kind::f16 instruction descriptor: D = F32, A = B = BF16, both K-major, M x N.
+__host__ __device__ constexpr uint32_t make_idesc(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+{
+    for (long long it = 0; it < kWaitLimit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ uint16_t bf16_one() { return 0x3F80u; }
+
+__global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* __restrict__ job, int cond)
+{
+    const JobDev& jb = *job;
+    if (cond) {
+        const uint32_t n = jb.nsweep[0];
+        if (!(jb.recompute_every > 0 && n > 0 && n % (uint32_t)jb.recompute_every == 0)) return;
+    }
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int L = jb.L, q = jb.q, Lpad = jb.Lpad, W = jb.W;
+    const int N = q * jb.R;
+    const int m0 = blockIdx.x * kTileM, n0 = blockIdx.y * kTileN;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    unsigned char* tileA = smem;                               // kSplit tiles
+    unsigned char* tileB = smem + kSplit * kTileBytes;         // one tile
+    uint64_t* mbar = (uint64_t*)(smem + kSplit * kTileBytes + kTileBytesB);
+    uint32_t* tmem_slot = (uint32_t*)(mbar + 1);
+    uint16_t* tab = (uint16_t*)(smem + kSplit * kTileBytes + kTileBytesB + 64);  // split table [3][Lpad], if staged
+    const bool tab_smem = jb.tc_tab_smem != 0;
+    const uint16_t* gtab = jb.Jsplit;
+
+    if (tab_smem)
+        for (int m = tid; m < kSplit * Lpad; m += kTcThreads) tab[m] = gtab[m];
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    const uint16_t* T = tab_smem ? tab : gtab;
+
+    // this thread's place in a core matrix: row rr = lane / 4, sites 2 (lane % 4), +1
+    const int rr = lane >> 2, kp = (lane & 3) * 2;
+    const int nchunks = (L + kChunk - 1) / kChunk;
+    const uint32_t idesc = make_idesc(kTileM, kTileN);
+    bool ok = true;
+    uint32_t parity = 0;
+
+    for (int c = 0; c < nchunks; ++c) {
+        const int k0 = c * kChunk;
+        // A tiles: each warp fills whole core matrices (g, kc), one 4-byte pair per lane
+        for (int cm = warp; cm < kGA * (kChunk / 8); cm += kTcThreads / 32) {
+            const int g = cm % kGA, kc = cm / kGA;
+            const int i = m0 + 8 * g + rr;
+            const int k = k0 + 8 * kc + kp;
+            const uint32_t off = (uint32_t)((kc * kGA + g) * 128 + rr * 16 + kp * 2);
+            int r0 = (i - k) % L;
+            r0 += r0 < 0 ? L : 0;
+            int r1 = r0 - 1;
+            r1 += r1 < 0 ? L : 0;
+#pragma unroll
+            for (int sp = 0; sp < kSplit; ++sp) {
+                const uint32_t v = (uint32_t)T[sp * Lpad + r0] | ((uint32_t)T[sp * Lpad + r1] << 16);
+                *(uint32_t*)(tileA + sp * kTileBytes + off) = v;
+            }
+        }
+        // B tile: row n = (replica, state), X = 1 where the replica's spin at site k is that state
+        for (int cm = warp; cm < kGB * (kChunk / 8); cm += kTcThreads / 32) {
+            const int g = cm % kGB, kc = cm / kGB;
+            const int n = n0 + 8 * g + rr;
+            const int k = k0 + 8 * kc + kp;
+            const uint32_t off = (uint32_t)((kc * kGB + g) * 128 + rr * 16 + kp * 2);
+            uint32_t v = 0;
+            if (n < N) {
+                const int rep = n / q, x = n - rep * q;
+                const uint32_t* sp = jb.spins + (size_t)rep * W;
+                if (k < L && (int)((sp[k >> 3] >> (4 * (k & 7))) & 15u) == x) v |= bf16_one();
+                if (k + 1 < L && (int)((sp[(k + 1) >> 3] >> (4 * ((k + 1) & 7))) & 15u) == x) v |= (uint32_t)bf16_one() << 16;
+            }
+            *(uint32_t*)(tileB + off) = v;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t dhi = tmem + (uint32_t)((c % kAccHi) * kTileN);
+            const uint32_t dsmall = tmem + (uint32_t)(kAccHi * kTileN);
+#pragma unroll
+            for (int s = 0; s < kChunk / 16; ++s) {
+                const uint64_t bdesc = make_desc(smem_u32(tileB) + s * 256 * kGB, 128 * kGB, 128);
+#pragma unroll
+                for (int sp = 0; sp < kSplit; ++sp) {
+                    const uint64_t adesc =
+                        make_desc(smem_u32(tileA + sp * kTileBytes) + s * 256 * kGA, 128 * kGA, 128);
+                    const uint32_t dcol = sp == 0 ? dhi : dsmall;
+                    const bool first = s == 0 && (sp == 0 ? c < kAccHi : (c == 0 && sp == 1));
+                    const uint32_t accumulate = first ? 0u : 1u;
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\t"
+                        "setp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dcol),
+                        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+                        : "memory");
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(mbar))
+                         : "memory");
+        }
+        // all threads wait for the chunk's MMAs before the tiles are rebuilt
+        if (!mbar_wait(smem_u32(mbar), parity)) ok = false;
+        parity ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (!__syncthreads_and(ok)) {
+            ok = false;
+            break;
+        }
+    }
+
+    if (ok) {
+        // epilogue: warp w reads TMEM lanes 32w..32w+31 = rows m0 + 32w + lane
+        const int i = m0 + 32 * warp + lane;
+        const int nhi = nchunks < kAccHi ? nchunks : kAccHi;
+        float* F = (float*)jb.fields;
+        for (int cb = 0; cb < kTileN; cb += 8) {
+            double sum[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) sum[e] = 0.0;
+            for (int a = 0; a <= nhi; ++a) {
+                const int col = a < nhi ? a : kAccHi;  // the used hi accumulators, then mid + lo
+                uint32_t v[8];
+                const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(col * kTileN + cb);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                    : "r"(taddr)
+                    : "memory");
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int e = 0; e < 8; ++e) sum[e] += (double)__uint_as_float(v[e]);
+            }
+            if (i < L) {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const int n = n0 + cb + e;
+                    if (n < N) F[(size_t)n * Lpad + i] = (float)sum[e];
+                }
+            }
+        }
+    } else if (tid == 0) {
+        atomicExch(jb.status, 1);  // a bounded wait expired; the host reports ETIMEOUT
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+}
+
+}  // namespace
+
+size_t tc_smem_bytes(int Lpad, int tab_smem)
+{
+    size_t b = (size_t)kSplit * kTileBytes + kTileBytesB + 64 + (tab_smem ? (size_t)kSplit * Lpad * 2 : 0);
+    b = (b + 127) & ~(size_t)127;
+    return b < kTcMinSmem ? kTcMinSmem : b;
+}
+
+int tc_table_in_smem(int Lpad)
+{
+    return (size_t)kSplit * kTileBytes + kTileBytesB + 64 + (size_t)kSplit * Lpad * 2 <= 200 * 1024;
+}
+
+cudaError_t launch_fields_tc(const JobDev* job_dev, int L, int q, int R, int Lpad, int tab_smem, int cond,
+                             cudaStream_t st)
+{
+    const size_t smem = tc_smem_bytes(Lpad, tab_smem);
+    cudaError_t e = cudaFuncSetAttribute(fields_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((L + kTileM - 1) / kTileM, (q * R + kTileN - 1) / kTileN);
+    fields_tc_kernel<<<grid, kTcThreads, smem, st>>>(job_dev, cond);
+    return cudaGetLastError();
 }
 
 }  // namespace plr

@@ -1,0 +1,94 @@
+"""Batching: ragged jobs (different L, q, sigma, R, precision) stepped together
+in graph-captured batch steps give each job exactly the results it gets alone
+with the same call sequence (bit for bit), and FP64 jobs in a batch still
+follow the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1308_5426_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+JOBS = [  # L, q, sigma, R, seed, precision, K
+    (64, 3, 0.5, 16, 1, "fp64", 0),
+    (100, 7, 0.3, 5, 2, "fp32", 10),
+    (1000, 5, 0.4, 6, 3, "fp64", 0),
+    (300, 4, 0.8, 9, 4, "fp32", 7),
+    (4096, 8, 0.2, 3, 5, "fp32", 6),
+    (33, 16, 0.9, 1, 6, "fp64", 0),
+]
+
+
+@pytest.fixture(scope="module")
+def plr():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1308_5426_gb300
+    return paper_1308_5426_gb300
+
+
+def _make(plr, spec, stream=None):
+    L, q, sigma, R, seed, prec, K = spec
+    temps = workloads.geometric_ratios(R, 0.05, 1.0) * oracle.jtot(L, sigma)
+    return plr.Job(L, q, sigma, temps, seed, precision=prec, recompute_every=K, stream=stream)
+
+
+@pytest.mark.parametrize("steps,per_graph", [(23, 10), (7, 3)])
+def test_batch_equals_alone(plr, steps, per_graph):
+    alone = []
+    for spec in JOBS:
+        j = _make(plr, spec)
+        for _ in range(steps):
+            j.sweep(1)
+            j.exchange()
+        alone.append((j.spins(), j.running_energy(), j.fields(), j.measure(), j.stats()))
+        j.close()
+    jobs = [_make(plr, spec) for spec in JOBS]
+    b = plr.Batch(jobs)
+    b.run(steps, per_graph)
+    b.sync()
+    Eb, Mb = b.measure()
+    off = 0
+    for spec, j, (S, E, F, (Em, Mm), st) in zip(JOBS, jobs, alone):
+        np.testing.assert_array_equal(j.spins(), S, err_msg=str(spec))
+        np.testing.assert_array_equal(j.running_energy(), E, err_msg=str(spec))
+        np.testing.assert_array_equal(j.fields(), F, err_msg=str(spec))
+        np.testing.assert_array_equal(Eb[off:off + j.R], Em, err_msg=str(spec))
+        np.testing.assert_array_equal(Mb[off:off + j.R], Mm, err_msg=str(spec))
+        np.testing.assert_array_equal(j.stats()["acc_flip"], st["acc_flip"])
+        assert j.counters() == (steps, steps)
+        off += j.R
+    b.close()
+
+
+def test_batch_fp64_jobs_follow_oracle(plr):
+    specs = [s for s in JOBS if s[5] == "fp64"]
+    jobs = [_make(plr, s) for s in specs]
+    b = plr.Batch(jobs)
+    b.run(12, 5)
+    b.sync()
+    for s, j in zip(specs, jobs):
+        L, q, sigma, R, seed, _, _ = s
+        temps = workloads.geometric_ratios(R, 0.05, 1.0) * oracle.jtot(L, sigma)
+        o = oracle.Oracle(L, q, sigma, temps, seed)
+        for _ in range(12):
+            o.step()
+        assert o.stats()["near_metro"].sum() == 0
+        np.testing.assert_array_equal(j.spins(), o.spins(), err_msg=str(s))
+
+
+def test_batch_split_calls_equal_run(plr):
+    """batch.sweep + batch.exchange alternated equal batch.run."""
+    a = [_make(plr, s) for s in JOBS[:4]]
+    b = [_make(plr, s) for s in JOBS[:4]]
+    ba, bb = plr.Batch(a), plr.Batch(b)
+    ba.run(9, 4)
+    for _ in range(9):
+        bb.sweep(1)
+        bb.exchange()
+    ba.sync()
+    bb.sync()
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x.spins(), y.spins())
+        np.testing.assert_array_equal(x.fields(), y.fields())

@@ -1,0 +1,109 @@
+"""FP32 mode: fields in FP32, re-anchored every K sweeps by the split-BF16
+tensor-core rebuild H = C . onehot(S).  Checked against FP64: the rebuild
+error and the field drift stay below 1e-5 of Jtot (drift = max over slots,
+states and sites of |h32 - h64| / Jtot, h64 the FP64 direct rebuild of the
+same spins), and FP32 chains sample the same <E> and <M> as FP64 chains
+within 3 binned standard errors."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1308_5426_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+DRIFT_BOUND = 1e-5
+
+
+@pytest.fixture(scope="module")
+def plr():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1308_5426_gb300
+    return paper_1308_5426_gb300
+
+
+@pytest.mark.parametrize("L,q,R,sigma", [
+    (64, 3, 4, 0.5), (200, 5, 7, 0.3), (1000, 16, 9, 0.9), (1024, 5, 64, 0.4),
+    (4096, 8, 128, 0.2), (16384, 8, 64, 0.1), (300, 2, 3, 1.5),
+])
+def test_tensor_core_rebuild_accuracy(plr, L, q, R, sigma):
+    temps = workloads.geometric_ratios(R, 0.05, 1.0) * oracle.jtot(L, sigma)
+    j = plr.Job(L, q, sigma, temps, 3, precision="fp32", recompute_every=0)
+    j.sweep(2)
+    j.fields_recompute()
+    err = j.fields_error()
+    assert err < DRIFT_BOUND, err
+    # the rebuilt fields satisfy sum_x h[x][i] = Jtot within the per-field bound
+    h = j.fields()
+    np.testing.assert_allclose(h.sum(axis=1), oracle.jtot(L, sigma), rtol=DRIFT_BOUND)
+    # re-anchored running energy equals the measured one
+    E, _ = j.measure()
+    np.testing.assert_allclose(j.running_energy(), E, rtol=1e-12)
+
+
+def test_tensor_core_rebuild_small_matches_oracle_fields(plr):
+    """Rebuilt FP32 fields against the oracle's FP64 fields of the same spins."""
+    L, q, R, sigma = 96, 4, 3, 0.6
+    temps = workloads.geometric_ratios(R, 0.05, 1.0) * oracle.jtot(L, sigma)
+    j = plr.Job(L, q, sigma, temps, 5, precision="fp32", recompute_every=0)
+    j.sweep(3)
+    j.fields_recompute()
+    o = oracle.Oracle(L, q, sigma, temps, 5)
+    o.set_spins(j.spins())
+    np.testing.assert_allclose(j.fields(), o.fields(), rtol=0, atol=2e-6 * oracle.jtot(L, sigma))
+
+
+def test_drift_over_one_rebuild_period(plr):
+    """The precision workload's shape (L=4096, q=8, sigma=0.2, T/Jtot 0.02-0.5),
+    16 of its 128 slots spread over the grid: drift just before the K=100
+    rebuild and just after it."""
+    spec = workloads.precision_job("fp32")
+    ratios = spec.ratios[::8]
+    temps = ratios * oracle.jtot(spec.L, spec.sigma)
+    j = plr.Job(spec.L, spec.q, spec.sigma, temps, 1, precision="fp32", recompute_every=100)
+    for _ in range(99):
+        j.sweep(1)
+        j.exchange()
+    before = j.fields_error()
+    j.sweep(1)  # the 100th sweep triggers the rebuild
+    after = j.fields_error()
+    print("drift before rebuild %.3e, after %.3e" % (before, after))
+    assert before < DRIFT_BOUND, before
+    assert after < DRIFT_BOUND, after
+
+
+def _binned(x, nbins=20):
+    x = np.asarray(x)
+    b = x[: (x.size // nbins) * nbins].reshape(nbins, -1).mean(axis=1)
+    return b.mean(), b.std(ddof=1) / math.sqrt(nbins)
+
+
+def test_fp32_and_fp64_sample_the_same_observables(plr):
+    """Same seeds, same call sequence: <E>/L and <M> per temperature from an
+    FP32 chain and an FP64 chain agree within 3 binned standard errors
+    (combined), after equilibration.  L=256, q=3, sigma=0.5, R=8."""
+    L, q, sigma, R = 256, 3, 0.5, 8
+    temps = workloads.geometric_ratios(R, 0.05, 1.0) * oracle.jtot(L, sigma)
+    res = {}
+    for prec in ("fp32", "fp64"):
+        j = plr.Job(L, q, sigma, temps, 17, precision=prec, recompute_every=100)
+        for _ in range(300):
+            j.sweep(1)
+            j.exchange()
+        Es, Ms = [], []
+        for _ in range(400):
+            j.sweep(5)
+            j.exchange()
+            E, M = j.measure()
+            Es.append(E / L)
+            Ms.append(M)
+        res[prec] = (np.array(Es), np.array(Ms))
+    for k, name in ((0, "E"), (1, "M")):
+        for t in range(R):
+            m32, s32 = _binned(res["fp32"][k][:, t])
+            m64, s64 = _binned(res["fp64"][k][:, t])
+            se = math.hypot(s32, s64)
+            assert abs(m32 - m64) < 3 * se + 1e-9, (name, t, m32, m64, se)
