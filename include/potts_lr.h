@@ -195,6 +195,32 @@ int potts_lr_batch_measure_device(potts_lr_batch_t* b, double* E, double* M);
 int potts_lr_batch_sync(potts_lr_batch_t* b);
 void potts_lr_batch_destroy(potts_lr_batch_t* b);
 
+/* Allocation-free measurement (the paper has no counterpart).  Same energy
+ * (Eq. 2 via the distance counts N_r) and magnetisation (Eq. 10) as
+ * potts_lr_measure, for callers that cannot allocate device memory and so
+ * cannot create a handle: code inside a host framework that owns all device
+ * memory, or a latency-critical loop that must not pay the synchronisation a
+ * cudaMalloc/cudaFree can bring.  It calls no cudaMalloc, cudaFree or other
+ * allocating routine; its scratch (the per-configuration results the kernel
+ * writes before they are copied out) is a fixed device array inside this
+ * library, 64 KB, held on every GPU that loads the library until exit.
+ *   spins:  device array, R configurations of packed spins, [R][ceil(L/8)]
+ *           uint32 words, spin i of configuration r in bits 4(i%8)..4(i%8)+3
+ *           of word i/8 of row r (values 0..q-1)
+ *   jstar:  device array of L doubles, J*(r) for r = 0..L-1 (potts_lr_jstar)
+ *   E, M:   device arrays of R doubles (outputs); pair_factor = c (1 or 2)
+ *   cuda_stream: cudaStream_t to run on (NULL = the default stream); the call
+ *           is asynchronous on it.
+ * EINVAL for a NULL pointer, L outside [2, 65536], q outside [2, 16],
+ * pair_factor not 1 or 2, or R outside [1, 4096] (the scratch size); ECUDA for
+ * a runtime error.  The first call on a device looks up the device address of
+ * the scratch array (cudaGetSymbolAddress), so make that first call before any
+ * stream capture.  Every call writes every scratch entry it later reads, so
+ * nothing needs clearing between calls; but all calls share the one array, so
+ * calls that overlap on the GPU (different streams, or threads) race. */
+int potts_lr_measure_static(const uint32_t* spins, int L, int q, int R, const double* jstar, int pair_factor,
+                            double* E, double* M, void* cuda_stream);
+
 /* Measurement utility (the paper has no counterpart): throughput of this
  * GPU's FP64 add pipe (what = 0, adds/s), FP32 add pipe (what = 1, adds/s) or
  * shared memory (what = 2, bytes/s loaded + stored), measured with CUDA

@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libpotts_lr.so")
-SOURCES = ["api.cu", "sweep.cu", "aux_kernels.cu", "rebuild_tc.cu", "probe.cu", "jstar.cpp"]
+SOURCES = ["api.cu", "sweep.cu", "aux_kernels.cu", "rebuild_tc.cu", "probe.cu", "measure_static.cu", "jstar.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr"] + ARCH

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/potts_lr.h"
+#include "measure_body.cuh"
 #include "potts_internal.h"
 
 using namespace plr;

@@ -2,6 +2,7 @@
 // FP64 direct field rebuild of the long-range Potts chain.
 #include <cmath>
 
+#include "measure_body.cuh"
 #include "philox.cuh"
 #include "potts_internal.h"
 
@@ -28,37 +29,13 @@ __global__ void init_spins_kernel(const JobDev* __restrict__ jobs, int job)
     jb.spins[(size_t)r * jb.W + w] = word;
 }
 
-// Deterministic block sum of one double per thread (fixed tree order).
-__device__ double block_sum(double v, double* red)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    double tot = 0.0;
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tot += red[i];
-        red[0] = tot;
-    }
-    __syncthreads();
-    tot = red[0];
-    __syncthreads();
-    return tot;
-}
-
-// Energy from packed spins (Eq. 2 regrouped by distance) and magnetisation
-// (Eq. 10) of one slot per CTA.
-//   N_r = #{i : s_i = s_{(i+r) mod L}}, r = 1..L/2  (N_{L-r} = N_r)
-//   E = -(c/2) sum_{r=1}^{L-1} J*(r) N_r
-// N_r is counted 8 sites at a time: the packed word of sites 8w..8w+7 is
-// XORed with the word of sites 8w+r..8w+r+7 (a funnel shift of the doubled
-// packed string) and the zero nibbles are counted.
 __device__ __forceinline__ bool rebuild_due(const JobDev& jb)
 {
     const uint32_t n = jb.nsweep[0];
     return jb.recompute_every > 0 && n > 0 && n % (uint32_t)jb.recompute_every == 0;
 }
 
+// Energy and magnetisation of one slot per CTA (see measure_body.cuh).
 __global__ void __launch_bounds__(kAuxThreads) measure_kernel(const JobDev* __restrict__ jobs,
                                                               const int2* __restrict__ work, int anchor, int cond)
 {
@@ -67,53 +44,12 @@ __global__ void __launch_bounds__(kAuxThreads) measure_kernel(const JobDev* __re
     const JobDev& jb = jobs[wk.x];
     if (cond && !rebuild_due(jb)) return;
     const int t = wk.y;
-    const int L = jb.L, q = jb.q, W = jb.W;
     const int rep = jb.map[t];
-    const uint32_t* spins = jb.spins + (size_t)rep * W;
-    const int tid = threadIdx.x;
-
-    const int nd = 2 * W + 2;  // doubled packed string, enough words for any shift
-    uint32_t* dbl = (uint32_t*)smem;
-    uint8_t* s = (uint8_t*)(dbl + nd);
-    __shared__ int cnt[kMaxQ];
-    __shared__ double red[kAuxThreads / 32];
-
-    if (tid < kMaxQ) cnt[tid] = 0;
-    for (int i = tid; i < L; i += kAuxThreads) s[i] = (uint8_t)((spins[i >> 3] >> (4 * (i & 7))) & 15u);
-    __syncthreads();
-    for (int m = tid; m < nd; m += kAuxThreads) {
-        uint32_t word = 0;
-        for (int b = 0; b < 8; ++b) word |= (uint32_t)s[(8 * m + b) % L] << (4 * b);
-        dbl[m] = word;
-    }
-    for (int i = tid; i < L; i += kAuxThreads) atomicAdd(&cnt[s[i]], 1);
-    __syncthreads();
-
-    const int tail = L & 7;  // valid nibbles of the last word (0 = all 8)
-    const uint32_t tail_bits = tail ? (0x11111111u & ((1u << (4 * tail)) - 1u)) : 0x11111111u;
-    double part = 0.0;
-    for (int r = 1 + tid; 2 * r <= L; r += kAuxThreads) {
-        const int qo = r >> 3, sh = 4 * (r & 7);
-        int Nr = 0;
-        for (int w = 0; w < W; ++w) {
-            const uint32_t lo = dbl[w + qo], hi = dbl[w + qo + 1];
-            const uint32_t rot = __funnelshift_r(lo, hi, sh);
-            uint32_t x = dbl[w] ^ rot;
-            x |= x >> 1;
-            x |= x >> 2;
-            const uint32_t valid = (w == W - 1) ? tail_bits : 0x11111111u;
-            Nr += __popc(valid) - __popc(x & valid);
-        }
-        const double wgt = (2 * r == L) ? 1.0 : 2.0;
-        part += wgt * jb.J64d[r] * (double)Nr;
-    }
-    const double tot = block_sum(part, red);
-    if (tid == 0) {
-        int nmax = 0;
-        for (int x = 0; x < q; ++x) nmax = max(nmax, cnt[x]);
-        const double E = -0.5 * (double)jb.c * tot;
+    double E, M;
+    measure_body(jb.spins + (size_t)rep * jb.W, jb.L, jb.q, jb.W, jb.c, jb.J64d, smem, &E, &M);
+    if (threadIdx.x == 0) {
         jb.meas_E[t] = E;
-        jb.meas_M[t] = ((double)q * (double)nmax / (double)L - 1.0) / (double)(q - 1);
+        jb.meas_M[t] = M;
         if (anchor) jb.E[rep] = E;
     }
 }
@@ -219,7 +155,6 @@ __global__ void __launch_bounds__(kAuxThreads) fields_direct_kernel(const JobDev
 
 }  // namespace
 
-size_t measure_smem_bytes(int L, int W) { return (size_t)(2 * W + 2) * 4 + (size_t)((L + 15) & ~15); }
 size_t direct_smem_bytes(int L, int q) { (void)q; return (size_t)((L + 7) & ~7) * sizeof(uint16_t); }
 
 cudaError_t launch_init_spins(const JobDev* jobs_dev, int job, int L, int W, int R, cudaStream_t st)

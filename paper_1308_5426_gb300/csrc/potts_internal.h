@@ -71,7 +71,6 @@ int tc_table_in_smem(int Lpad);
 
 size_t sweep_smem_bytes(const JobDev& j);
 size_t sweep_smem_bytes_for(int precision, int L, int Lpad, int q, int h_smem, int j_smem);
-size_t measure_smem_bytes(int L, int W);
 size_t direct_smem_bytes(int L, int q);
 
 }  // namespace plr
