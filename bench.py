@@ -39,7 +39,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="chains", choices=["chains", "precision"])
+    ap.add_argument("--workload", default="chains", choices=["chains", "precision", "batching", "serving"])
+    ap.add_argument("--serve-jobs", type=int, default=32)
+    ap.add_argument("--serve-sweeps", type=int, default=100)
+    ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--precision", default=None, choices=[None, "fp64", "fp32"])
     ap.add_argument("--no-fp32-compare", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -63,13 +66,22 @@ def workload_specs(name, rank, precision):
         desc = {"workload": "8 independent PT chains, L=1024 q=5 sigma=0.4 R=64, T/Jtot geometric 0.05-1, "
                             "exchange every sweep, E/M every 10 sweeps",
                 "L": 1024, "q": 5, "sigma": 0.4, "R": 64, "chains": 8}
-    else:
+    elif name == "precision":
         s = workloads.precision_job(precision or "fp32")
         s.seed += rank
         specs = [s]
         desc = {"workload": "one PT job, L=4096 q=8 sigma=0.2 R=128, T/Jtot geometric 0.02-0.5, "
                             "exchange every sweep, E/M every 10 sweeps, FP32 rebuild every 100 sweeps",
                 "L": 4096, "q": 8, "sigma": 0.2, "R": 128, "chains": 1}
+    elif name == "batching":
+        specs = workloads.batching_jobs()
+        desc = {"workload": "256 ragged PT jobs (L 256-8192, q 2-10, sigma U[0.1,1], R 32/64/128, FP32, "
+                            "rebuild every 100 sweeps) in one graph-captured batch; step = 1 sweep + exchange",
+                "jobs": 256}
+    else:
+        specs = workloads.serving_trace()[:1]
+        desc = {"workload": "serving trace: Poisson(50/s) arrivals, q 3/5/8, sigma U[0.1,1], L 512-16384, "
+                            "R=64, FP32, continuous batching"}
     return specs, desc
 
 
@@ -287,6 +299,91 @@ def timed_e2e(plr, torch, specs, steps, warmup, dev):
             "d2h_bytes_per_step": d2h}
 
 
+def serving_run(plr, torch, dev, njobs, sweeps, fp64_sample=8, fp64_sweeps=10):
+    """The serving trace (Poisson arrivals at 50 jobs/s; q in {3,5,8}, sigma in
+    U[0.1,1], L in {512..16384}, R=64, FP32 fields, K=100) cut to its first
+    njobs requests with `sweeps` sweeps each, served with continuous batching on
+    the wall clock; then the same requests' shapes run as plain FP64 jobs, one at
+    a time, for fp64_sweeps sweeps each (the per-job FP64 path)."""
+    from paper_1308_5426_gb300 import workloads
+    from paper_1308_5426_gb300.serve import GpuEngine, Request, Server
+
+    trace = workloads.serving_trace()[:njobs]
+    reqs = []
+    for i, sp in enumerate(trace):
+        temps = sp.ratios * plr.jtot(sp.L, sp.sigma)
+        reqs.append(Request(rid=i, L=sp.L, q=sp.q, sigma=sp.sigma, temps=temps, seed=sp.seed, sweeps=sweeps,
+                            recompute_every=100, arrival=sp.arrival))
+
+    class Engine(GpuEngine):
+        max_err = 0.0
+
+        def destroy(self, job):
+            Engine.max_err = max(Engine.max_err, job.fields_error())
+            job.close()
+
+    free, _ = torch.cuda.mem_get_info(dev)
+    budget = int(0.5 * free)
+    st = torch.cuda.Stream(device=dev)
+    srv = Server(Engine(stream=st.cuda_stream), budget_bytes=budget, chunk=10)
+    t0 = time.perf_counter()
+    srv.run(reqs, idle_sleep=1e-4)
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - t0
+    summ = srv.summary(wall_seconds=wall)
+    # plain FP64 per-job path on the same shapes
+    att64, t64 = 0, 0.0
+    for r in reqs[:fp64_sample]:
+        j = plr.Job(r.L, r.q, r.sigma, r.temps, r.seed, precision="fp64")
+        j.sync()
+        a = time.perf_counter()
+        for _ in range(fp64_sweeps):
+            j.sweep(1)
+            j.exchange()
+        j.sync()
+        t64 += time.perf_counter() - a
+        att64 += r.L * r.R * fp64_sweeps
+        j.close()
+    fp64_rate = att64 / t64
+    return {"jobs": len(reqs), "sweeps_per_job": sweeps,
+            "trace": "first %d requests of the 500-request Poisson(50/s) trace, seed 5; %d sweeps each "
+                     "instead of 5000" % (len(reqs), sweeps),
+            "budget_bytes": budget, "wall_s": wall, "attempts": summ["attempts"],
+            "attempts_per_s": summ.get("attempts_per_s"), "p50_latency_s": summ.get("p50_s"),
+            "p99_latency_s": summ.get("p99_s"), "done": summ["done"],
+            "max_field_error_rel_jtot": Engine.max_err,
+            "fp64_per_job_attempts_per_s": fp64_rate,
+            "fp64_per_job_sample": "first %d requests' shapes as FP64 jobs, one at a time, %d sweeps each"
+                                   % (min(fp64_sample, len(reqs)), fp64_sweeps),
+            "served_fp32_over_fp64_per_job": (summ.get("attempts_per_s") or 0.0) / fp64_rate}
+
+
+def batching_run(plr, torch, dev, steps, warmup):
+    """The 256 ragged jobs (L in {256..8192}, q in 2..10, sigma in U[0.1,1],
+    R in {32,64,128}, FP32, K=100) created together and stepped as one
+    graph-captured batch; each step = one sweep of every slot of every job +
+    one exchange step per job (+ the rebuilds that fall due)."""
+    from paper_1308_5426_gb300 import workloads
+    specs = workloads.batching_jobs()
+    st = torch.cuda.Stream(device=dev)
+    jobs = make_jobs(plr, specs, st.cuda_stream)
+    b = plr.Batch(jobs, stream=st.cuda_stream)
+    b.run(warmup, max(1, warmup))
+    b.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    b.run(steps, min(10, steps))
+    e1.record(st)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    att = steps * sum(s.L * s.R for s in specs)
+    b.close()
+    for j in jobs:
+        j.close()
+    return {"jobs": len(specs), "slots": sum(s.R for s in specs), "steps": steps, "ms": ms,
+            "attempts_per_s": att / (ms / 1e3)}
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -311,6 +408,24 @@ def main():
     _lib.load()
 
     clocks = ClockSampler(local)
+    if args.workload in ("batching", "serving"):
+        torch.cuda.synchronize(dev)
+        clocks.start()
+        if args.workload == "batching":
+            r = batching_run(plr, torch, dev, args.steps, args.warmup)
+            value, ms_step = r["attempts_per_s"], r["ms"] / args.steps
+        else:
+            r = serving_run(plr, torch, dev, args.serve_jobs, args.serve_sweeps)
+            value, ms_step = r["attempts_per_s"], 1e3 * r["wall_s"]
+        ck = clocks.stop()
+        if rank == 0:
+            line = {"metric": "spin-flip attempts/s", "value": value, "unit": "attempts/s", "n_gpus": world,
+                    "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+                    "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                    "config": desc, "clocks": ck, "detail": r, "roofline": None, "e2e": None,
+                    "cpu_baseline": None}
+            print(json.dumps(line), flush=True)
+        return 0
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
@@ -348,6 +463,9 @@ def main():
         r32 = timed_device(plr, torch, specs32, max(3, args.steps // 3), args.warmup, dev, with_events=False)
         extra["fp32_same_workload"] = {"value": world * r32["steps"] * r32["att_step"] / (r32["step_ms"] / 1e3),
                                        "unit": "attempts/s", "acceptance": r32["acceptance"]}
+
+    if args.workload == "chains" and not args.no_serving and world == 1:
+        extra["serving"] = serving_run(plr, torch, dev, args.serve_jobs, args.serve_sweeps)
 
     e2e = timed_e2e(plr, torch, specs, max(3, args.steps // 3), 1, dev)
     if world > 1:

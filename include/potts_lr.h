@@ -31,9 +31,15 @@
  *     in FP64; every accept decision is the FP64 decision (decided in FP32
  *     where the FP32 margin is provably large enough, else in FP64).
  *   POTTS_LR_FP32 -- fields in FP32, decisions in FP32, running energy in FP64;
- *     every recompute_every sweeps the fields are rebuilt as H = C . onehot(S)
- *     on the tensor cores (C = J*(|i-j|) split into BF16 hi + lo parts, FP32
- *     accumulation) and the energy is re-anchored from the spins.
+ *     at most every recompute_every sweeps the fields are rebuilt as
+ *     H = C . onehot(S) on the tensor cores (C = J*(|i-j|) split into BF16
+ *     hi + mid + lo parts, FP32 accumulation) and the energy is re-anchored
+ *     from the spins.  Each rebuild measures the drift of the period it ends,
+ *     max |h_fp32 - h_rebuilt| / Jtot; the interval halves when that exceeds
+ *     7e-6 and doubles (up to recompute_every) when it is below 3.5e-6, so the
+ *     fields stay within 1e-5 Jtot of exact.  The first interval is
+ *     min(recompute_every, max(1, 2500 q / L)).  The schedule lives on the
+ *     device, is part of the checkpoint and is the same alone or batched.
  *
  * Errors: every int-returning call returns POTTS_LR_OK (0) or one of the codes
  * below; potts_lr_last_error() gives a message for the calling thread.  A call
@@ -69,8 +75,8 @@ typedef struct potts_lr potts_lr_t;
 
 typedef struct {
     int precision;       /* POTTS_LR_FP64 (default) or POTTS_LR_FP32 */
-    int recompute_every; /* FP32 mode: tensor-core field rebuild every K sweeps
-                            (default 100; 0 = only on explicit request) */
+    int recompute_every; /* FP32 mode: longest interval K between tensor-core field
+                            rebuilds (default 100; 0 = only on explicit request) */
     int pair_factor;     /* c in Eq. 2: 2 (default) or 1 */
     void* cuda_stream;   /* cudaStream_t to run on; NULL = a stream the handle creates */
 } potts_lr_opts;
@@ -91,8 +97,9 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
                     const potts_lr_opts* opts, potts_lr_t** out);
 
 /* n full Metropolis sweeps of every slot (L attempts per slot per sweep, Eq. 8),
- * asynchronous on the handle's stream.  In FP32 mode a tensor-core field
- * rebuild runs after every recompute_every-th sweep.  n >= 0. */
+ * asynchronous on the handle's stream.  In FP32 mode the tensor-core field
+ * rebuild runs after the sweeps at which the schedule above makes it due.
+ * n >= 0. */
 int potts_lr_sweep(potts_lr_t* h, int n);
 
 /* One exchange step (Eq. 9): stage 0 then stage 1, asynchronous. */

@@ -132,7 +132,9 @@ cudaError_t rebuild_launch(const potts_lr_t* h, const JobDev* job_dev, int cond,
     else
         e = launch_fields_direct(job_dev, h->L, h->R, 0, cond, h->direct_smem, st);
     if (e != cudaSuccess) return e;
-    return launch_measure(job_dev, h->dwork, h->R, 1, cond, h->measure_smem, st);
+    e = launch_measure(job_dev, h->dwork, h->R, 1, cond, h->measure_smem, st);
+    if (e != cudaSuccess || h->precision != POTTS_LR_FP32) return e;
+    return launch_rebuild_policy(job_dev, cond, st);
 }
 
 int rebuild(potts_lr_t* h)
@@ -259,6 +261,15 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
     }
     std::vector<double> beta(R);
     for (int t = 0; t < R; ++t) beta[t] = 1.0 / temps[t];
+    // first FP32 rebuild interval: short for long chains with few states (the
+    // drift grows with the field updates per element, ~L/q per sweep); the
+    // device doubles it while the measured drift stays small
+    int sched0[2] = {0, 0};
+    if (h->K > 0) {
+        const int k0 = (int)std::max(1.0, std::min((double)h->K, 2500.0 * q / (double)L));
+        sched0[0] = k0;
+        sched0[1] = k0;
+    }
     std::vector<int> map(R);
     std::vector<int2> work(R);
     for (int t = 0; t < R; ++t) {
@@ -282,7 +293,7 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
     const size_t o_accf = take((size_t)R * 8), o_accs = take((size_t)R * 8), o_near = take(16);
     const size_t o_mE = take((size_t)R * 8), o_mM = take((size_t)R * 8), o_err = take(8);
     const size_t o_job = take(sizeof(JobDev)), o_work = take((size_t)R * sizeof(int2));
-    const size_t o_split = take(3 * Lp * 2), o_status = take(4);
+    const size_t o_split = take(3 * Lp * 2), o_status = take(4), o_sched = take(8), o_drift = take(8);
     cudaError_t e = cudaMalloc(&h->arena, off);
     if (e != cudaSuccess) {
         potts_lr_destroy(h);
@@ -326,6 +337,8 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
     j.Jsplit = (const uint16_t*)(base + o_split);
     j.tc_tab_smem = tc_table_in_smem(h->Lpad);
     j.status = (int*)(base + o_status);
+    j.sched = (int*)(base + o_sched);
+    j.drift_bits = (unsigned long long*)(base + o_drift);
     // residency of the sweep kernel's working set: fields and table in shared
     // memory when they fit, else fields first, else the table, else neither
     {
@@ -355,6 +368,7 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
         if ((e = cudaMemcpyAsync(h->dj, &j, sizeof(JobDev), cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
         if ((e = cudaMemcpyAsync(h->dwork, work.data(), (size_t)R * sizeof(int2), cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
         if ((e = cudaMemcpyAsync((void*)j.Jsplit, split.data(), 3 * Lp * 2, cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
+        if ((e = cudaMemcpyAsync(j.sched, sched0, 8, cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
         if ((e = launch_init_spins(h->dj, 0, L, h->W, R, st)) != cudaSuccess) break;
         if ((e = launch_fields_direct(h->dj, L, R, 0, 0, h->direct_smem, st)) != cudaSuccess) break;
         if ((e = launch_measure(h->dj, h->dwork, R, 1, 0, h->measure_smem, st)) != cudaSuccess) break;
@@ -375,18 +389,23 @@ int potts_lr_sweep(potts_lr_t* h, int n)
 {
     if (!h) return fail(POTTS_LR_EINVAL, "handle is NULL");
     if (n < 0) return fail(POTTS_LR_EINVAL, "n must be >= 0");
-    while (n > 0) {
-        int chunk = n;
-        if (h->K > 0) chunk = std::min(n, h->K - (int)(h->nsweep % (uint32_t)h->K));
-        cudaError_t e = launch_sweep(h->dj, h->dwork, h->R, chunk, h->precision, h->hj.h_smem, h->hj.j_smem,
+    if (n == 0) return POTTS_LR_OK;
+    if (h->K <= 0) {
+        cudaError_t e = launch_sweep(h->dj, h->dwork, h->R, n, h->precision, h->hj.h_smem, h->hj.j_smem,
                                      h->sweep_smem, h->stream);
         if (e != cudaSuccess) return cuda_fail(e, "sweep kernel");
-        h->nsweep += (uint32_t)chunk;
-        n -= chunk;
-        if (h->K > 0 && h->nsweep % (uint32_t)h->K == 0) {
-            int rc = rebuild(h);
-            if (rc) return rc;
-        }
+        h->nsweep += (uint32_t)n;
+        return POTTS_LR_OK;
+    }
+    // FP32 mode with automatic rebuilds: the schedule lives on the device, so
+    // every sweep is followed by the conditional rebuild
+    for (int s = 0; s < n; ++s) {
+        cudaError_t e = launch_sweep(h->dj, h->dwork, h->R, 1, h->precision, h->hj.h_smem, h->hj.j_smem,
+                                     h->sweep_smem, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "sweep kernel");
+        h->nsweep += 1u;
+        e = rebuild_launch(h, h->dj, 1, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "field rebuild");
     }
     return POTTS_LR_OK;
 }
@@ -464,7 +483,7 @@ static size_t state_bytes(const potts_lr_t* h)
     const size_t R = h->R;
     return sizeof(StateHeader) + R * 4 /*map*/ + R * 8 /*E*/ + R * h->W * 4 /*spins*/ +
            R * h->q * (size_t)h->Lpad * h->wsize /*fields*/ + R * 4 /*nsweep*/ + R * 8 /*acc_flip*/ +
-           R * 8 /*acc_swap*/ + 16 /*near*/;
+           R * 8 /*acc_swap*/ + 16 /*near*/ + 8 /*sched*/ + 8 /*drift*/;
 }
 
 int potts_lr_get_state(potts_lr_t* h, void* buf, size_t* len)
@@ -479,7 +498,7 @@ int potts_lr_get_state(potts_lr_t* h, void* buf, size_t* len)
     StateHeader hd;
     std::memset(&hd, 0, sizeof(hd));
     hd.magic = kStateMagic;
-    hd.version = 1;
+    hd.version = 2;
     hd.L = h->L;
     hd.q = h->q;
     hd.R = h->R;
@@ -504,7 +523,9 @@ int potts_lr_get_state(potts_lr_t* h, void* buf, size_t* len)
                   {j.nsweep, R * 4},
                   {j.acc_flip, R * 8},
                   {j.acc_swap, R * 8},
-                  {j.near, 16}};
+                  {j.near, 16},
+                  {j.sched, 8},
+                  {j.drift_bits, 8}};
     for (const Piece& pc : pieces) {
         PLR_CUDA(cudaMemcpyAsync(p, pc.src, pc.bytes, cudaMemcpyDeviceToHost, h->stream));
         p += pc.bytes;
@@ -520,7 +541,7 @@ int potts_lr_set_state(potts_lr_t* h, const void* buf, size_t len)
     if (len != state_bytes(h)) return fail(POTTS_LR_ESTATE, "checkpoint size %zu does not match %zu", len, state_bytes(h));
     StateHeader hd;
     std::memcpy(&hd, buf, sizeof(hd));
-    if (hd.magic != kStateMagic || hd.version != 1 || hd.L != h->L || hd.q != h->q || hd.R != h->R ||
+    if (hd.magic != kStateMagic || hd.version != 2 || hd.L != h->L || hd.q != h->q || hd.R != h->R ||
         hd.precision != h->precision || hd.Lpad != h->Lpad)
         return fail(POTTS_LR_ESTATE, "checkpoint does not match this job's L, q, R or precision");
     const char* p = (const char*)buf + sizeof(hd);
@@ -544,7 +565,9 @@ int potts_lr_set_state(potts_lr_t* h, const void* buf, size_t len)
                   {j.nsweep, R * 4},
                   {j.acc_flip, R * 8},
                   {j.acc_swap, R * 8},
-                  {j.near, 16}};
+                  {j.near, 16},
+                  {j.sched, 8},
+                  {j.drift_bits, 8}};
     for (const Piece& pc : pieces) {
         PLR_CUDA(cudaMemcpyAsync(pc.dst, p, pc.bytes, cudaMemcpyHostToDevice, h->stream));
         p += pc.bytes;

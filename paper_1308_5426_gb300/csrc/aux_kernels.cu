@@ -29,12 +29,6 @@ __global__ void init_spins_kernel(const JobDev* __restrict__ jobs, int job)
     jb.spins[(size_t)r * jb.W + w] = word;
 }
 
-__device__ __forceinline__ bool rebuild_due(const JobDev& jb)
-{
-    const uint32_t n = jb.nsweep[0];
-    return jb.recompute_every > 0 && n > 0 && n % (uint32_t)jb.recompute_every == 0;
-}
-
 // Energy and magnetisation of one slot per CTA (see measure_body.cuh).
 __global__ void __launch_bounds__(kAuxThreads) measure_kernel(const JobDev* __restrict__ jobs,
                                                               const int2* __restrict__ work, int anchor, int cond)
@@ -153,7 +147,26 @@ __global__ void __launch_bounds__(kAuxThreads) fields_direct_kernel(const JobDev
     }
 }
 
+__global__ void rebuild_policy_kernel(const JobDev* __restrict__ job, int cond)
+{
+    const JobDev& jb = *job;
+    if (cond && !rebuild_due(jb)) return;
+    const double d = __longlong_as_double((long long)*jb.drift_bits);
+    int k = jb.sched[0];
+    if (d > kDriftHigh) k = max(1, k / 2);
+    else if (d < kDriftLow) k = min(max(jb.recompute_every, 1), 2 * k);
+    jb.sched[0] = k;
+    jb.sched[1] = (int)(jb.nsweep[0] + (uint32_t)k);
+    *jb.drift_bits = 0ull;
+}
+
 }  // namespace
+
+cudaError_t launch_rebuild_policy(const JobDev* job_dev, int cond, cudaStream_t st)
+{
+    rebuild_policy_kernel<<<1, 1, 0, st>>>(job_dev, cond);
+    return cudaGetLastError();
+}
 
 size_t direct_smem_bytes(int L, int q) { (void)q; return (size_t)((L + 7) & ~7) * sizeof(uint16_t); }
 

@@ -40,7 +40,21 @@ struct JobDev {
     const uint16_t* Jsplit;        // FP32 mode: BF16 parts hi, mid, lo of J*, [3][Lpad]
     int tc_tab_smem;               // tensor-core rebuild stages the split table in shared memory
     int* status;                   // 0 ok; 1 a bounded device wait expired
+    int* sched;                    // FP32 rebuild schedule: [0] current interval k, [1] sweep of the next rebuild
+    unsigned long long* drift_bits;  // max |h_before - h_rebuilt| / Jtot of the last rebuild (double bits)
 };
+
+// FP32 drift control: after each rebuild the measured drift d of the period
+// halves the interval if d > kDriftHigh, doubles it (up to recompute_every)
+// if d < kDriftLow; drift grows like the square root of the interval, so the
+// field error stays below 1e-5 of Jtot.
+constexpr double kDriftHigh = 7e-6;
+constexpr double kDriftLow = 3.5e-6;
+
+__device__ __forceinline__ bool rebuild_due(const JobDev& jb)
+{
+    return jb.recompute_every > 0 && jb.nsweep[0] >= (uint32_t)jb.sched[1];
+}
 
 // ---- host-side helpers (jstar.cpp) ----
 void jstar_table(int L, double sigma, double* out);
@@ -68,6 +82,8 @@ cudaError_t launch_fields_direct(const JobDev* job_dev, int L, int R, int mode, 
 cudaError_t launch_fields_tc(const JobDev* job_dev, int L, int q, int R, int Lpad, int tab_smem, int cond,
                              cudaStream_t st);
 int tc_table_in_smem(int Lpad);
+// after a rebuild: adapt the FP32 rebuild interval to the measured drift (one thread)
+cudaError_t launch_rebuild_policy(const JobDev* job_dev, int cond, cudaStream_t st);
 
 size_t sweep_smem_bytes(const JobDev& j);
 size_t sweep_smem_bytes_for(int precision, int L, int Lpad, int q, int h_smem, int j_smem);

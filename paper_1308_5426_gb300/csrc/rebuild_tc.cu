@@ -86,10 +86,7 @@ __device__ __forceinline__ uint16_t bf16_one() { return 0x3F80u; }
 __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* __restrict__ job, int cond)
 {
     const JobDev& jb = *job;
-    if (cond) {
-        const uint32_t n = jb.nsweep[0];
-        if (!(jb.recompute_every > 0 && n > 0 && n % (uint32_t)jb.recompute_every == 0)) return;
-    }
+    if (cond && !rebuild_due(jb)) return;
     extern __shared__ __align__(1024) unsigned char smem[];
     const int L = jb.L, q = jb.q, Lpad = jb.Lpad, W = jb.W;
     const int N = q * jb.R;
@@ -129,7 +126,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* 
     bool ok = true;
     uint32_t parity = 0;
 
-    for (int c = 0; c < nchunks; ++c) {
+    // chunk order: decreasing circular distance from the chunk holding the tile's
+    // centre, so the large near-diagonal couplings are added last and the many
+    // small far-field sums accumulate while the accumulators are still small
+    const int cc = ((m0 + kTileM / 2) / kChunk) % nchunks;
+    for (int t = 0; t < nchunks; ++t) {
+        const int kk = nchunks - 1 - t;  // rank in increasing distance: 0, +1, -1, +2, -2, ...
+        const int o = kk == 0 ? 0 : ((kk & 1) ? (kk + 1) / 2 : -(kk / 2));
+        const int c = ((cc + o) % nchunks + nchunks) % nchunks;
         const int k0 = c * kChunk;
         // A tiles: each warp fills whole core matrices (g, kc), one 4-byte pair per lane
         for (int cm = warp; cm < kGA * (kChunk / 8); cm += kTcThreads / 32) {
@@ -166,7 +170,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* 
         __syncthreads();
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t dhi = tmem + (uint32_t)((c % kAccHi) * kTileN);
+            const uint32_t dhi = tmem + (uint32_t)((t % kAccHi) * kTileN);
             const uint32_t dsmall = tmem + (uint32_t)(kAccHi * kTileN);
 #pragma unroll
             for (int s = 0; s < kChunk / 16; ++s) {
@@ -176,7 +180,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* 
                     const uint64_t adesc =
                         make_desc(smem_u32(tileA + sp * kTileBytes) + s * 256 * kGA, 128 * kGA, 128);
                     const uint32_t dcol = sp == 0 ? dhi : dsmall;
-                    const bool first = s == 0 && (sp == 0 ? c < kAccHi : (c == 0 && sp == 1));
+                    const bool first = s == 0 && (sp == 0 ? t < kAccHi : (t == 0 && sp == 1));
                     const uint32_t accumulate = first ? 0u : 1u;
                     asm volatile(
                         "{\n\t.reg .pred p;\n\t"
@@ -205,6 +209,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* 
         const int i = m0 + 32 * warp + lane;
         const int nhi = nchunks < kAccHi ? nchunks : kAccHi;
         float* F = (float*)jb.fields;
+        double dmax = 0.0;
         for (int cb = 0; cb < kTileN; cb += 8) {
             double sum[8];
 #pragma unroll
@@ -226,10 +231,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* 
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
                     const int n = n0 + cb + e;
-                    if (n < N) F[(size_t)n * Lpad + i] = (float)sum[e];
+                    if (n < N) {
+                        const size_t idx = (size_t)n * Lpad + i;
+                        dmax = fmax(dmax, fabs((double)F[idx] - sum[e]));  // drift of the ending period
+                        F[idx] = (float)sum[e];
+                    }
                 }
             }
         }
+        for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+        if (lane == 0 && dmax > 0.0)
+            atomicMax(jb.drift_bits, (unsigned long long)__double_as_longlong(dmax / jb.jtot));
     } else if (tid == 0) {
         atomicExch(jb.status, 1);  // a bounded wait expired; the host reports ETIMEOUT
     }
