@@ -51,7 +51,7 @@ class Job:
     """
 
     def __init__(self, L, q, sigma, temps, seed, precision="fp64", recompute_every=100, pair_factor=2,
-                 stream=None):
+                 stream=None, sweep_variant="auto"):
         lib = _lib.load()
         self.L, self.q, self.sigma = int(L), int(q), float(sigma)
         self.temps = np.ascontiguousarray(temps, dtype=np.float64)
@@ -64,6 +64,7 @@ class Job:
         o.recompute_every = int(recompute_every)
         o.pair_factor = int(pair_factor)
         o.cuda_stream = ctypes.c_void_p(int(stream)) if stream else None
+        o.sweep_variant = {"auto": 0, "memory": 1, "registers": 2}[sweep_variant]
         h = ctypes.c_void_p()
         _lib.check(lib.potts_lr_create(self.L, self.q, self.sigma, _lib._ptr(self.temps), self.R,
                                        ctypes.c_uint64(self.seed), ctypes.byref(o), ctypes.byref(h)))

@@ -12,7 +12,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libpotts_lr.so")
-SOURCES = ["api.cu", "sweep.cu", "aux_kernels.cu", "rebuild_tc.cu", "probe.cu", "measure_static.cu", "jstar.cpp"]
+SOURCES = ["api.cu", "sweep.cu", "sweep_rf_a.cu", "sweep_rf_b.cu", "sweep_rf_c.cu", "sweep_rf_d.cu", "sweep_rf_e.cu",
+           "aux_kernels.cu", "rebuild_tc.cu", "probe.cu", "measure_static.cu", "jstar.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr"] + ARCH
@@ -45,7 +46,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         if all(os.path.getmtime(f) <= t for f in _deps()):
             return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
-    with concurrent.futures.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+    with concurrent.futures.ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 4)) as ex:
         results = list(ex.map(lambda s: _compile(s, list(extra)), SOURCES))
     if verbose:
         for _, err in results:

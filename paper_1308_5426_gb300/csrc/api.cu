@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <new>
 #include <unordered_set>
 #include <vector>
@@ -67,6 +68,8 @@ struct potts_lr {
     uint32_t nsweep, nexch;       // host mirrors of the counters
     size_t sweep_smem, measure_smem, direct_smem;
     double* pinned;               // 2R doubles of pinned host memory for measure
+    int4* dtiles;                 // FP32: tensor-core rebuild tiles of this job (job index 0)
+    int ntiles;
 };
 
 struct potts_lr_batch {
@@ -76,13 +79,20 @@ struct potts_lr_batch {
     JobDev* djobs;
     void* arena;
     struct Group {
-        int precision, h_smem, j_smem;
+        int key;  // sweep kernel variant
         int2* dwork;
         int nwork;
         size_t smem;
     };
     std::vector<Group> groups;
     std::vector<int> fp32_jobs;  // jobs that need the conditional rebuild
+    int4* dtc_tiles;             // their rebuild tiles (job index into djobs)
+    int ntc_tiles;
+    int tc_tab_Lpad;             // largest staged split table among them
+    int2* dfp_work;              // (job, slot) of their slots, for the energy re-anchor
+    int nfp_work;
+    size_t fp_meas_smem;
+    int* dfp_idx;                // their job indices, for the schedule policy
     int2* dmeas;                 // (job, slot) of every slot, job order
     int nmeas;
     size_t meas_smem;
@@ -117,6 +127,7 @@ int check_opts(const potts_lr_opts* o)
         return fail(POTTS_LR_EINVAL, "precision must be POTTS_LR_FP64 or POTTS_LR_FP32");
     if (o->pair_factor != 1 && o->pair_factor != 2) return fail(POTTS_LR_EINVAL, "pair_factor must be 1 or 2");
     if (o->recompute_every < 0) return fail(POTTS_LR_EINVAL, "recompute_every must be >= 0");
+    if (o->sweep_variant < 0 || o->sweep_variant > 2) return fail(POTTS_LR_EINVAL, "sweep_variant must be 0, 1 or 2");
     return POTTS_LR_OK;
 }
 
@@ -128,13 +139,27 @@ cudaError_t rebuild_launch(const potts_lr_t* h, const JobDev* job_dev, int cond,
 {
     cudaError_t e;
     if (h->precision == POTTS_LR_FP32)
-        e = launch_fields_tc(job_dev, h->L, h->q, h->R, h->Lpad, h->hj.tc_tab_smem, cond, st);
+        e = launch_fields_tc(job_dev, h->dtiles, h->ntiles, h->hj.tc_tab_smem ? h->Lpad : 0, cond, st);
     else
         e = launch_fields_direct(job_dev, h->L, h->R, 0, cond, h->direct_smem, st);
     if (e != cudaSuccess) return e;
     e = launch_measure(job_dev, h->dwork, h->R, 1, cond, h->measure_smem, st);
     if (e != cudaSuccess || h->precision != POTTS_LR_FP32) return e;
-    return launch_rebuild_policy(job_dev, cond, st);
+    return launch_rebuild_policy(job_dev, nullptr, 1, cond, st);
+}
+
+// the sweep kernel variant of a job: register-resident (per configuration and
+// q) or memory-resident (per precision and shared-memory residency)
+int variant_key(const potts_lr_t* h)
+{
+    return h->hj.rf ? 100 + h->hj.rf * 32 + h->q : h->precision * 4 + h->hj.h_smem * 2 + h->hj.j_smem;
+}
+
+cudaError_t launch_variant(int key, const JobDev* jobs, const int2* work, int nwork, int nsweeps, size_t smem,
+                           cudaStream_t st)
+{
+    if (key >= 100) return launch_sweep_rf((key - 100) / 32, (key - 100) % 32, jobs, work, nwork, nsweeps, smem, st);
+    return launch_sweep(jobs, work, nwork, nsweeps, key >> 2, (key >> 1) & 1, key & 1, smem, st);
 }
 
 int rebuild(potts_lr_t* h)
@@ -170,6 +195,7 @@ int potts_lr_default_opts(potts_lr_opts* opts)
     opts->recompute_every = 100;
     opts->pair_factor = 2;
     opts->cuda_stream = nullptr;
+    opts->sweep_variant = 0;
     return POTTS_LR_OK;
 }
 
@@ -294,6 +320,9 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
     const size_t o_mE = take((size_t)R * 8), o_mM = take((size_t)R * 8), o_err = take(8);
     const size_t o_job = take(sizeof(JobDev)), o_work = take((size_t)R * sizeof(int2));
     const size_t o_split = take(3 * Lp * 2), o_status = take(4), o_sched = take(8), o_drift = take(8);
+    std::vector<int4> tiles;
+    if (h->precision == POTTS_LR_FP32) tc_tiles(0, L, q, R, tiles);
+    const size_t o_tiles = take(tiles.size() * sizeof(int4) + 16);
     cudaError_t e = cudaMalloc(&h->arena, off);
     if (e != cudaSuccess) {
         potts_lr_destroy(h);
@@ -338,6 +367,8 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
     j.tc_tab_smem = tc_table_in_smem(h->Lpad);
     j.status = (int*)(base + o_status);
     j.sched = (int*)(base + o_sched);
+    h->dtiles = (int4*)(base + o_tiles);
+    h->ntiles = (int)tiles.size();
     j.drift_bits = (unsigned long long*)(base + o_drift);
     // residency of the sweep kernel's working set: fields and table in shared
     // memory when they fit, else fields first, else the table, else neither
@@ -351,9 +382,14 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
             }
         }
     }
+    j.rf = (h->precision == POTTS_LR_FP32 && o.sweep_variant != 1) ? rf_config(L, q) : 0;
+    if (o.sweep_variant == 2 && !j.rf) {
+        potts_lr_destroy(h);
+        return fail(POTTS_LR_EINVAL, "register-resident sweep needs FP32 and L <= 1120, or L <= 4320 with q <= 8");
+    }
     h->dj = (JobDev*)(base + o_job);
     h->dwork = (int2*)(base + o_work);
-    h->sweep_smem = sweep_smem_bytes(j);
+    h->sweep_smem = j.rf ? rf_smem_bytes(j.rf, q, L, h->Lpad) : sweep_smem_bytes(j);
     h->measure_smem = measure_smem_bytes(L, h->W);
     h->direct_smem = direct_smem_bytes(L, q);
 
@@ -369,6 +405,10 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
         if ((e = cudaMemcpyAsync(h->dwork, work.data(), (size_t)R * sizeof(int2), cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
         if ((e = cudaMemcpyAsync((void*)j.Jsplit, split.data(), 3 * Lp * 2, cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
         if ((e = cudaMemcpyAsync(j.sched, sched0, 8, cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
+        if (!tiles.empty() &&
+            (e = cudaMemcpyAsync(h->dtiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice, st)) !=
+                cudaSuccess)
+            break;
         if ((e = launch_init_spins(h->dj, 0, L, h->W, R, st)) != cudaSuccess) break;
         if ((e = launch_fields_direct(h->dj, L, R, 0, 0, h->direct_smem, st)) != cudaSuccess) break;
         if ((e = launch_measure(h->dj, h->dwork, R, 1, 0, h->measure_smem, st)) != cudaSuccess) break;
@@ -390,9 +430,9 @@ int potts_lr_sweep(potts_lr_t* h, int n)
     if (!h) return fail(POTTS_LR_EINVAL, "handle is NULL");
     if (n < 0) return fail(POTTS_LR_EINVAL, "n must be >= 0");
     if (n == 0) return POTTS_LR_OK;
+    const int key = variant_key(h);
     if (h->K <= 0) {
-        cudaError_t e = launch_sweep(h->dj, h->dwork, h->R, n, h->precision, h->hj.h_smem, h->hj.j_smem,
-                                     h->sweep_smem, h->stream);
+        cudaError_t e = launch_variant(key, h->dj, h->dwork, h->R, n, h->sweep_smem, h->stream);
         if (e != cudaSuccess) return cuda_fail(e, "sweep kernel");
         h->nsweep += (uint32_t)n;
         return POTTS_LR_OK;
@@ -400,8 +440,7 @@ int potts_lr_sweep(potts_lr_t* h, int n)
     // FP32 mode with automatic rebuilds: the schedule lives on the device, so
     // every sweep is followed by the conditional rebuild
     for (int s = 0; s < n; ++s) {
-        cudaError_t e = launch_sweep(h->dj, h->dwork, h->R, 1, h->precision, h->hj.h_smem, h->hj.j_smem,
-                                     h->sweep_smem, h->stream);
+        cudaError_t e = launch_variant(key, h->dj, h->dwork, h->R, 1, h->sweep_smem, h->stream);
         if (e != cudaSuccess) return cuda_fail(e, "sweep kernel");
         h->nsweep += 1u;
         e = rebuild_launch(h, h->dj, 1, h->stream);
@@ -677,19 +716,19 @@ int potts_lr_batch_create(potts_lr_t* const* jobs, int n, void* cuda_stream, pot
         potts_lr_batch_destroy(b);
         return cuda_fail(e, "cudaEventCreate");
     }
-    // work tables per kernel variant (precision, residency), longest slots first
+    // work tables per sweep kernel variant, longest slots first
     std::vector<JobDev> hjobs(n);
-    std::vector<std::vector<int2>> works(8);
-    std::vector<size_t> smem(8, 0);
+    std::map<int, std::vector<int2>> works;
+    std::map<int, size_t> smem;
     for (int i = 0; i < n; ++i) {
         hjobs[i] = jobs[i]->hj;
-        const int v = jobs[i]->precision * 4 + jobs[i]->hj.h_smem * 2 + jobs[i]->hj.j_smem;
-        for (int t = 0; t < jobs[i]->R; ++t) works[v].push_back(make_int2(i, t));
-        smem[v] = std::max(smem[v], jobs[i]->sweep_smem);
+        const int key = variant_key(jobs[i]);
+        for (int t = 0; t < jobs[i]->R; ++t) works[key].push_back(make_int2(i, t));
+        smem[key] = std::max(smem[key], jobs[i]->sweep_smem);
         if (jobs[i]->precision == POTTS_LR_FP32 && jobs[i]->K > 0) b->fp32_jobs.push_back(i);
     }
-    for (int v = 0; v < 8; ++v)
-        std::stable_sort(works[v].begin(), works[v].end(), [&](const int2& x, const int2& y) {
+    for (auto& kv : works)
+        std::stable_sort(kv.second.begin(), kv.second.end(), [&](const int2& x, const int2& y) {
             const potts_lr_t* a = jobs[x.x];
             const potts_lr_t* c = jobs[y.x];
             return (long long)a->L * (a->q + 8) > (long long)c->L * (c->q + 8);
@@ -701,16 +740,33 @@ int potts_lr_batch_create(potts_lr_t* const* jobs, int n, void* cuda_stream, pot
         b->meas_smem = std::max(b->meas_smem, jobs[i]->measure_smem);
     }
     b->nmeas = (int)mwork.size();
+    std::vector<int4> btiles;
+    std::vector<int2> fwork;
+    for (int i : b->fp32_jobs) {
+        const potts_lr_t* h = jobs[i];
+        tc_tiles(i, h->L, h->q, h->R, btiles);
+        for (int t = 0; t < h->R; ++t) fwork.push_back(make_int2(i, t));
+        if (h->hj.tc_tab_smem) b->tc_tab_Lpad = std::max(b->tc_tab_Lpad, h->Lpad);
+        b->fp_meas_smem = std::max(b->fp_meas_smem, h->measure_smem);
+    }
+    b->ntc_tiles = (int)btiles.size();
+    b->nfp_work = (int)fwork.size();
     size_t bytes = align256(n * sizeof(JobDev));
-    size_t ow[8];
-    for (int v = 0; v < 8; ++v) {
-        ow[v] = bytes;
-        bytes += align256(works[v].size() * sizeof(int2) + 8);
+    std::map<int, size_t> ow;
+    for (auto& kv : works) {
+        ow[kv.first] = bytes;
+        bytes += align256(kv.second.size() * sizeof(int2) + 8);
     }
     const size_t o_m = bytes;
     bytes += align256(mwork.size() * sizeof(int2));
     const size_t o_mb = bytes;
     bytes += align256(2 * mwork.size() * sizeof(double));
+    const size_t o_bt = bytes;
+    bytes += align256(btiles.size() * sizeof(int4) + 16);
+    const size_t o_fw = bytes;
+    bytes += align256(fwork.size() * sizeof(int2) + 8);
+    const size_t o_fi = bytes;
+    bytes += align256(b->fp32_jobs.size() * sizeof(int) + 4);
     e = cudaMalloc(&b->arena, bytes);
     if (e != cudaSuccess) {
         potts_lr_batch_destroy(b);
@@ -719,17 +775,17 @@ int potts_lr_batch_create(potts_lr_t* const* jobs, int n, void* cuda_stream, pot
     b->djobs = (JobDev*)b->arena;
     b->dmeas = (int2*)((char*)b->arena + o_m);
     b->meas_buf = (double*)((char*)b->arena + o_mb);
-    for (int v = 0; v < 8; ++v) {
-        if (works[v].empty()) continue;
+    b->dtc_tiles = (int4*)((char*)b->arena + o_bt);
+    b->dfp_work = (int2*)((char*)b->arena + o_fw);
+    b->dfp_idx = (int*)((char*)b->arena + o_fi);
+    for (auto& kv : works) {
         potts_lr_batch_t::Group g;
-        g.precision = v >> 2;
-        g.h_smem = (v >> 1) & 1;
-        g.j_smem = v & 1;
-        g.dwork = (int2*)((char*)b->arena + ow[v]);
-        g.nwork = (int)works[v].size();
-        g.smem = smem[v];
+        g.key = kv.first;
+        g.dwork = (int2*)((char*)b->arena + ow[kv.first]);
+        g.nwork = (int)kv.second.size();
+        g.smem = smem[kv.first];
         b->groups.push_back(g);
-        e = cudaMemcpyAsync(g.dwork, works[v].data(), works[v].size() * sizeof(int2), cudaMemcpyHostToDevice,
+        e = cudaMemcpyAsync(g.dwork, kv.second.data(), kv.second.size() * sizeof(int2), cudaMemcpyHostToDevice,
                             b->stream);
         if (e != cudaSuccess) break;
     }
@@ -737,6 +793,14 @@ int potts_lr_batch_create(potts_lr_t* const* jobs, int n, void* cuda_stream, pot
         e = cudaMemcpyAsync(b->djobs, hjobs.data(), n * sizeof(JobDev), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->dmeas, mwork.data(), mwork.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && !btiles.empty())
+        e = cudaMemcpyAsync(b->dtc_tiles, btiles.data(), btiles.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                            b->stream);
+    if (e == cudaSuccess && !fwork.empty())
+        e = cudaMemcpyAsync(b->dfp_work, fwork.data(), fwork.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && !b->fp32_jobs.empty())
+        e = cudaMemcpyAsync(b->dfp_idx, b->fp32_jobs.data(), b->fp32_jobs.size() * sizeof(int), cudaMemcpyHostToDevice,
+                            b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) {
         potts_lr_batch_destroy(b);
@@ -750,12 +814,15 @@ static cudaError_t batch_enqueue_sweeps(potts_lr_batch_t* b)
 {
     cudaError_t e;
     for (const auto& g : b->groups)
-        if ((e = launch_sweep(b->djobs, g.dwork, g.nwork, 1, g.precision, g.h_smem, g.j_smem, g.smem, b->stream)) !=
-            cudaSuccess)
-            return e;
-    for (int i : b->fp32_jobs)
-        if ((e = rebuild_launch(b->jobs[i], b->djobs + i, 1, b->stream)) != cudaSuccess) return e;
-    return cudaSuccess;
+        if ((e = launch_variant(g.key, b->djobs, g.dwork, g.nwork, 1, g.smem, b->stream)) != cudaSuccess) return e;
+    if (b->fp32_jobs.empty()) return cudaSuccess;
+    // the rebuilds that fall due, for all FP32 jobs at once: tensor-core fields,
+    // energy re-anchor, schedule update
+    if ((e = launch_fields_tc(b->djobs, b->dtc_tiles, b->ntc_tiles, b->tc_tab_Lpad, 1, b->stream)) != cudaSuccess)
+        return e;
+    if ((e = launch_measure(b->djobs, b->dfp_work, b->nfp_work, 1, 1, b->fp_meas_smem, b->stream)) != cudaSuccess)
+        return e;
+    return launch_rebuild_policy(b->djobs, b->dfp_idx, (int)b->fp32_jobs.size(), 1, b->stream);
 }
 
 static cudaError_t batch_enqueue_step(potts_lr_batch_t* b)

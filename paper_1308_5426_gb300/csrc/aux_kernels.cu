@@ -147,9 +147,12 @@ __global__ void __launch_bounds__(kAuxThreads) fields_direct_kernel(const JobDev
     }
 }
 
-__global__ void rebuild_policy_kernel(const JobDev* __restrict__ job, int cond)
+__global__ void rebuild_policy_kernel(const JobDev* __restrict__ jobs, const int* __restrict__ idx, int njobs,
+                                      int cond)
 {
-    const JobDev& jb = *job;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= njobs) return;
+    const JobDev& jb = jobs[idx ? idx[i] : i];
     if (cond && !rebuild_due(jb)) return;
     const double d = __longlong_as_double((long long)*jb.drift_bits);
     int k = jb.sched[0];
@@ -162,9 +165,10 @@ __global__ void rebuild_policy_kernel(const JobDev* __restrict__ job, int cond)
 
 }  // namespace
 
-cudaError_t launch_rebuild_policy(const JobDev* job_dev, int cond, cudaStream_t st)
+cudaError_t launch_rebuild_policy(const JobDev* jobs_dev, const int* idx, int njobs, int cond, cudaStream_t st)
 {
-    rebuild_policy_kernel<<<1, 1, 0, st>>>(job_dev, cond);
+    if (njobs <= 0) return cudaSuccess;
+    rebuild_policy_kernel<<<(njobs + 127) / 128, 128, 0, st>>>(jobs_dev, idx, njobs, cond);
     return cudaGetLastError();
 }
 

@@ -2,6 +2,7 @@
 #pragma once
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -20,6 +21,7 @@ struct JobDev {
     int L, q, Lpad, W, R, c, precision;
     int recompute_every;  // FP32 mode: rebuild fields after sweeps n with (n+1) % K == 0
     int h_smem, j_smem;   // sweep kernel: fields / coupling table staged in shared memory
+    int rf;               // FP32 mode: register-resident sweep configuration (0 = none, 1..5)
     uint32_t key0, key1;  // Philox key (seed low, high)
     double jtot;          // sum_r J*(r)
     const double* J64d;   // doubled table: J64d[m] = J*(m mod L), m = 0..2L-1
@@ -77,15 +79,38 @@ cudaError_t launch_measure(const JobDev* jobs_dev, const int2* work, int nwork, 
 // with the stored fields and fold max |diff| / jtot into err_bits.
 cudaError_t launch_fields_direct(const JobDev* job_dev, int L, int R, int mode, int cond, size_t smem_bytes,
                                  cudaStream_t st);
-// FP32 mode: the split-BF16 tensor-core rebuild H = C . onehot(S) of job
-// job_dev[0] (any L, q, R).
-cudaError_t launch_fields_tc(const JobDev* job_dev, int L, int q, int R, int Lpad, int tab_smem, int cond,
+// FP32 mode: the split-BF16 tensor-core rebuild H = C . onehot(S) over a tile
+// table of (job index, first row, first column) 128 x 64 output tiles (any
+// mix of jobs); max_tab_Lpad: the largest Lpad among jobs that stage their
+// split table in shared memory (0 if none).  Persistent: one CTA per SM.
+cudaError_t launch_fields_tc(const JobDev* jobs_dev, const int4* tiles, int ntiles, int max_tab_Lpad, int cond,
                              cudaStream_t st);
+void tc_tiles(int job, int L, int q, int R, std::vector<int4>& out);
 int tc_table_in_smem(int Lpad);
-// after a rebuild: adapt the FP32 rebuild interval to the measured drift (one thread)
-cudaError_t launch_rebuild_policy(const JobDev* job_dev, int cond, cudaStream_t st);
+// after a rebuild: adapt the FP32 rebuild interval of jobs[idx[i]] to the
+// measured drift (one thread per job)
+cudaError_t launch_rebuild_policy(const JobDev* jobs_dev, const int* idx, int njobs, int cond, cudaStream_t st);
 
 size_t sweep_smem_bytes(const JobDev& j);
+
+// Register-resident FP32 sweep (sweep_rf.cuh): configuration 1..5 =
+// (E sites per update thread, update warps) = (1, 7), (2, 7), (5, 7) for
+// L <= 224, 448, 1120; (5, 15), (9, 15) with q <= 8 for L <= 2400, 4320;
+// 0 if the shape does not fit in registers.
+int rf_config(int L, int q);
+size_t rf_smem_bytes(int cfg, int q, int L, int Lpad);
+cudaError_t launch_sweep_rf(int cfg, int q, const JobDev* jobs_dev, const int2* work, int nwork, int nsweeps,
+                            size_t smem, cudaStream_t st);
+cudaError_t launch_sweep_rf_a(int q, const JobDev*, const int2*, int, int, size_t, cudaStream_t);
+cudaError_t launch_sweep_rf_b(int q, const JobDev*, const int2*, int, int, size_t, cudaStream_t);
+cudaError_t launch_sweep_rf_c(int q, const JobDev*, const int2*, int, int, size_t, cudaStream_t);
+cudaError_t launch_sweep_rf_d(int q, const JobDev*, const int2*, int, int, size_t, cudaStream_t);
+cudaError_t launch_sweep_rf_e(int q, const JobDev*, const int2*, int, int, size_t, cudaStream_t);
+size_t sweep_rf_smem_a(int q, int L, int Lpad);
+size_t sweep_rf_smem_b(int q, int L, int Lpad);
+size_t sweep_rf_smem_c(int q, int L, int Lpad);
+size_t sweep_rf_smem_d(int q, int L, int Lpad);
+size_t sweep_rf_smem_e(int q, int L, int Lpad);
 size_t sweep_smem_bytes_for(int precision, int L, int Lpad, int q, int h_smem, int j_smem);
 size_t direct_smem_bytes(int L, int q);
 

@@ -23,6 +23,7 @@
 // sites at byte (c G + g) 128, so the leading (K) byte offset is 128 G and the
 // stride (row-group) byte offset is 128; K-step s (16 sites) starts at 256 G s.
 #include <cstdint>
+#include <vector>
 
 #include "potts_internal.h"
 
@@ -83,14 +84,11 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
 
 __device__ __forceinline__ uint16_t bf16_one() { return 0x3F80u; }
 
-__global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* __restrict__ job, int cond)
+__global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* __restrict__ jobs,
+                                                                  const int4* __restrict__ tiles, int ntiles,
+                                                                  int cond)
 {
-    const JobDev& jb = *job;
-    if (cond && !rebuild_due(jb)) return;
     extern __shared__ __align__(1024) unsigned char smem[];
-    const int L = jb.L, q = jb.q, Lpad = jb.Lpad, W = jb.W;
-    const int N = q * jb.R;
-    const int m0 = blockIdx.x * kTileM, n0 = blockIdx.y * kTileN;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
     unsigned char* tileA = smem;                               // kSplit tiles
@@ -98,11 +96,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* 
     uint64_t* mbar = (uint64_t*)(smem + kSplit * kTileBytes + kTileBytesB);
     uint32_t* tmem_slot = (uint32_t*)(mbar + 1);
     uint16_t* tab = (uint16_t*)(smem + kSplit * kTileBytes + kTileBytesB + 64);  // split table [3][Lpad], if staged
-    const bool tab_smem = jb.tc_tab_smem != 0;
-    const uint16_t* gtab = jb.Jsplit;
 
-    if (tab_smem)
-        for (int m = tid; m < kSplit * Lpad; m += kTcThreads) tab[m] = gtab[m];
+    // skip the whole CTA when none of its tiles is due (no tensor memory taken)
+    bool any = false;
+    for (int ti = blockIdx.x; ti < ntiles && !any; ti += gridDim.x) any = !cond || rebuild_due(jobs[tiles[ti].x]);
+    if (!any) return;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"(kTmemCols)
@@ -117,14 +115,30 @@ __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* 
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
-    const uint16_t* T = tab_smem ? tab : gtab;
-
     // this thread's place in a core matrix: row rr = lane / 4, sites 2 (lane % 4), +1
     const int rr = lane >> 2, kp = (lane & 3) * 2;
-    const int nchunks = (L + kChunk - 1) / kChunk;
     const uint32_t idesc = make_idesc(kTileM, kTileN);
     bool ok = true;
     uint32_t parity = 0;
+    const JobDev* staged = nullptr;  // job whose split table is in shared memory
+
+    for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x) {
+    const int4 tile = tiles[ti];
+    const JobDev& jb = jobs[tile.x];
+    if (cond && !rebuild_due(jb)) continue;
+    const int L = jb.L, q = jb.q, Lpad = jb.Lpad, W = jb.W;
+    const int N = q * jb.R;
+    const int m0 = tile.y, n0 = tile.z;
+    const bool tab_smem = jb.tc_tab_smem != 0;
+    const uint16_t* gtab = jb.Jsplit;
+    if (tab_smem && staged != &jb) {
+        __syncthreads();  // previous tile done with the old table
+        for (int m = tid; m < kSplit * Lpad; m += kTcThreads) tab[m] = gtab[m];
+        __syncthreads();
+        staged = &jb;
+    }
+    const uint16_t* T = tab_smem ? tab : gtab;
+    const int nchunks = (L + kChunk - 1) / kChunk;
 
     // chunk order: decreasing circular distance from the chunk holding the tile's
     // centre, so the large near-diagonal couplings are added last and the many
@@ -242,9 +256,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* 
         for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
         if (lane == 0 && dmax > 0.0)
             atomicMax(jb.drift_bits, (unsigned long long)__double_as_longlong(dmax / jb.jtot));
+        // the tensor-memory reads above are complete before the next tile's MMAs
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     } else if (tid == 0) {
         atomicExch(jb.status, 1);  // a bounded wait expired; the host reports ETIMEOUT
     }
+    }  // tiles
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
@@ -265,15 +284,24 @@ int tc_table_in_smem(int Lpad)
     return (size_t)kSplit * kTileBytes + kTileBytesB + 64 + (size_t)kSplit * Lpad * 2 <= 200 * 1024;
 }
 
-cudaError_t launch_fields_tc(const JobDev* job_dev, int L, int q, int R, int Lpad, int tab_smem, int cond,
-                             cudaStream_t st)
+cudaError_t launch_fields_tc(const JobDev* jobs_dev, const int4* tiles, int ntiles, int any_tab_smem_Lpad,
+                             int cond, cudaStream_t st)
 {
-    const size_t smem = tc_smem_bytes(Lpad, tab_smem);
+    if (ntiles <= 0) return cudaSuccess;
+    const size_t smem = tc_smem_bytes(any_tab_smem_Lpad, any_tab_smem_Lpad > 0);
     cudaError_t e = cudaFuncSetAttribute(fields_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((L + kTileM - 1) / kTileM, (q * R + kTileN - 1) / kTileN);
-    fields_tc_kernel<<<grid, kTcThreads, smem, st>>>(job_dev, cond);
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = ntiles < sms ? ntiles : sms;  // persistent: one CTA per SM walks the tile table
+    fields_tc_kernel<<<grid, kTcThreads, smem, st>>>(jobs_dev, tiles, ntiles, cond);
     return cudaGetLastError();
+}
+
+void tc_tiles(int job, int L, int q, int R, std::vector<int4>& out)
+{
+    for (int m = 0; m < L; m += kTileM)
+        for (int n = 0; n < q * R; n += kTileN) out.push_back(make_int4(job, m, n, 0));
 }
 
 }  // namespace plr

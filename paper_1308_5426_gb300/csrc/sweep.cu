@@ -23,20 +23,17 @@
 // u < exp(-beta dE) itself.  FP32 mode decides in FP32.
 #include <cmath>
 
-#include "philox.cuh"
-#include "potts_internal.h"
+#include "sweep_common.cuh"
 
 namespace plr {
 
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
 constexpr int kWarps = kSweepThreads / 32;
-enum : int { kReject = 0, kAccept = 1, kUnsure = 2 };
 
 template <typename T>
 struct SweepSmem {
-    // carve-up of the dynamic shared memory (must match sweep_smem_bytes)
+    // carve-up of the dynamic shared memory (must match the kernel)
     static size_t bytes(int L, int Lpad, int q, bool hs, bool js)
     {
         (void)L;
@@ -45,36 +42,11 @@ struct SweepSmem {
         if (hs) b += (size_t)q * Lpad * sizeof(T);
         b += (size_t)Lpad;                       // spins
         b += 2 * 2 * kSiteBlock * sizeof(int);   // double-buffered flip lists
-        b += 32 * sizeof(float);                 // J* at distances 0..31 in FP32
+        b += kNearTable * sizeof(float);         // J* at distances 0..63 in FP32
         b += kWarps * sizeof(double) + 16;       // reduction scratch, counts
         return (b + 15) & ~(size_t)15;
     }
 };
-
-// FP64 rule, evaluated exactly: dE <= 0 or u < exp(-beta dE); near-tie count.
-__device__ __forceinline__ bool decide_fp64_exact(double d, double cb, double u, unsigned long long& near)
-{
-    if (d <= 0.0) return true;
-    const double x = cb * d;  // beta * c * d
-    const bool acc = u < exp(-x);
-    if (fabs(x + log(u)) < 1e-9) ++near;
-    return acc;
-}
-
-// FP32 filter of the FP64 rule.  d32 is within errd of the FP64 d (errd = 1.2e-5 Jtot
-// bounds the conversion and up to 32 FP32 corrections of magnitude <= 3 Jtot,
-// each rounded to 2^-24, with a factor 2 to spare); x and -ln u are within
-// 1.2e-7 relative of their FP64 values.
-__device__ __forceinline__ int decide_fp64_filter(float d, float cb, float nlu, float errd)
-{
-    if (d <= -errd) return kAccept;
-    if (d < errd) return kUnsure;
-    const float x = cb * d;
-    const float m = cb * errd + 1e-6f * (x + nlu + 1.0f);
-    if (x < nlu - m) return kAccept;
-    if (x > nlu + m) return kReject;
-    return kUnsure;
-}
 
 // Rank-1 updates of the flips (pk, pab)[0..nf), in flip order, on every
 // element except [x0, x0 + nx): h[a][i] -= J*((i-k) mod L), h[b][i] += J*((i-k) mod L).
@@ -131,7 +103,7 @@ __device__ __forceinline__ void apply_flips(T* __restrict__ h, const T* __restri
 }
 
 template <typename T, bool HS, bool JS>
-__global__ void __launch_bounds__(kSweepThreads, 4) sweep_kernel(const JobDev* __restrict__ jobs,
+__global__ void __launch_bounds__(kSweepThreads, HS ? 4 : 2) sweep_kernel(const JobDev* __restrict__ jobs,
                                                               const int2* __restrict__ work, int nsweeps)
 {
     constexpr bool kFP64 = sizeof(T) == 8;
@@ -164,8 +136,8 @@ __global__ void __launch_bounds__(kSweepThreads, 4) sweep_kernel(const JobDev* _
     off += (size_t)Lpad;
     int* lk = (int*)(smem + off);      // [2][32] flip sites
     int* lab = lk + 2 * kSiteBlock;    // [2][32] (a << 8) | b
-    float* Jn = (float*)(lab + 2 * kSiteBlock);  // J*(r), r < 32, FP32
-    double* red = (double*)(((uintptr_t)(Jn + 32) + 7) & ~(uintptr_t)7);
+    float* Jn = (float*)(lab + 2 * kSiteBlock);  // J*(r), r < 64, FP32
+    double* red = (double*)(((uintptr_t)(Jn + kNearTable) + 7) & ~(uintptr_t)7);
     int* lcnt = (int*)(red + kWarps);  // [2] flip counts
 
     if constexpr (JS)
@@ -175,7 +147,7 @@ __global__ void __launch_bounds__(kSweepThreads, 4) sweep_kernel(const JobDev* _
         for (int e = tid; e < n; e += kSweepThreads) hs[e] = hg[e];
     }
     for (int i = tid; i < L; i += kSweepThreads) s[i] = (uint8_t)((spins[i >> 3] >> (4 * (i & 7))) & 15u);
-    if (tid < 32) Jn[tid] = tid < L ? (float)jp->J64d[tid] : 0.0f;
+    if (tid < kNearTable) Jn[tid] = tid < L ? (float)jp->J64d[tid] : 0.0f;
     if (tid < 2) lcnt[tid] = 0;
     __syncthreads();
 
@@ -185,7 +157,7 @@ __global__ void __launch_bounds__(kSweepThreads, 4) sweep_kernel(const JobDev* _
     const uint32_t n0 = jp->nsweep[t];
     const double cb64 = beta * (double)c;
     const float cb32 = (float)cb64;
-    const float errd = (float)(1.2e-5 * jp->jtot);
+    const float errd = (float)(2.4e-5 * jp->jtot);
     const int nblk = (L + kSiteBlock - 1) / kSiteBlock;
     const int total = nsweeps * nblk;
 
@@ -204,7 +176,37 @@ __global__ void __launch_bounds__(kSweepThreads, 4) sweep_kernel(const JobDev* _
             if (g < total) {
                 const int k = k0 + lane;
                 const bool valid = lane < nv;
-                // bring this block's sites up to date with block g-1's flips
+                const uint32_t n = n0 + (uint32_t)(g / nblk);
+                // the block's sites do not hold block g-1's flips yet: decide with
+                // corrections, then bring them up to date
+                int a = 0, b = 0;
+                float nlu = 0.0f, d32 = 0.0f;
+                double base = 0.0;
+                uint32_t ux1 = 0, ux2 = 0;
+                if (valid) {
+                    a = s[k];
+                    draw_proposal<kFP64>(k, t, n, key0, key1, q, a, b, nlu, ux1, ux2);
+                    const T dd = h[(size_t)a * Lpad + k] - h[(size_t)b * Lpad + k];
+                    base = (double)dd;
+                    d32 = (float)dd;
+                }
+                const int cbuf = g & 1;
+                int* ck = lk + cbuf * kSiteBlock;
+                int* cab = lab + cbuf * kSiteBlock;
+                bool mine;
+                float dmine;
+                const int nf = decide_block<kFP64>(lane, nv, k, L, a, b, nlu, ux1, ux2, d32, base, pk, pab, npend,
+                                                   cb32, cb64, errd, Jn,
+                                                   kFP64 ? (const double*)(const void*)J : nullptr, ck, cab, mine,
+                                                   dmine, nnear);
+                if (mine) {
+                    s[k] = (uint8_t)b;
+                    if constexpr (!kFP64) dE_acc += (double)((float)c * dmine);
+                }
+                if (lane == 0) {
+                    lcnt[cbuf] = nf;
+                    nacc += (unsigned long long)nf;
+                }
                 if (valid) {
                     for (int f = 0; f < npend; ++f) {
                         const int kf = pk[f], af = pab[f] >> 8, bf = pab[f] & 255;
@@ -214,84 +216,6 @@ __global__ void __launch_bounds__(kSweepThreads, 4) sweep_kernel(const JobDev* _
                         h[(size_t)af * Lpad + k] -= v;
                         h[(size_t)bf * Lpad + k] += v;
                     }
-                }
-                const uint32_t n = n0 + (uint32_t)(g / nblk);
-                int a = 0, b = 0;
-                float nlu = 0.0f, d32 = 0.0f;
-                double u = 1.0, base = 0.0;
-                if (valid) {
-                    a = s[k];
-                    const U4 x = philox10(U4{(uint32_t)k, (uint32_t)t, n, kTagMetro}, key0, key1);
-                    b = a + 1 + (int)__umulhi(x.x, (uint32_t)(q - 1));
-                    if (b >= q) b -= q;
-                    if constexpr (kFP64) {
-                        u = unit53(x.y, x.z);
-                        nlu = -logf((float)u);
-                    } else {
-                        nlu = -logf(unit24(x.y));
-                    }
-                    const T dd = h[(size_t)a * Lpad + k] - h[(size_t)b * Lpad + k];
-                    base = (double)dd;
-                    d32 = (float)dd;
-                }
-                const int cbuf = g & 1;
-                int* ck = lk + cbuf * kSiteBlock;
-                int* cab = lab + cbuf * kSiteBlock;
-                int nf = 0;
-                bool mine = false;
-                float dmine = 0.0f;
-                int p = 0;
-                while (p < nv) {
-                    int st = kReject;
-                    if (valid && lane >= p) {
-                        if constexpr (kFP64) st = decide_fp64_filter(d32, cb32, nlu, errd);
-                        else st = (d32 <= 0.0f || cb32 * d32 < nlu) ? kAccept : kReject;
-                    }
-                    const unsigned hit = __ballot_sync(kFull, st != kReject);
-                    if (!hit) break;
-                    const int j = __ffs(hit) - 1;
-                    bool acc = true;
-                    if constexpr (kFP64) {
-                        const int stj = __shfl_sync(kFull, st, j);
-                        if (stj == kUnsure) {
-                            bool dec = false;
-                            if (lane == j) {
-                                double d64 = base;
-                                for (int f = 0; f < nf; ++f) {
-                                    const int kf = ck[f], af = cab[f] >> 8, bf = cab[f] & 255;
-                                    const int coef = (a == bf) - (a == af) - (b == bf) + (b == af);
-                                    if (coef) d64 += (double)coef * (double)J[k - kf];
-                                }
-                                dec = decide_fp64_exact(d64, cb64, u, nnear);
-                            }
-                            acc = __shfl_sync(kFull, dec, j);
-                        }
-                    }
-                    if (acc) {
-                        const int aj = __shfl_sync(kFull, a, j);
-                        const int bj = __shfl_sync(kFull, b, j);
-                        if (lane == j) {
-                            mine = true;
-                            dmine = d32;
-                            ck[nf] = k;
-                            cab[nf] = (a << 8) | b;
-                        }
-                        if (lane > j && valid) {
-                            const int coef = (a == bj) - (a == aj) - (b == bj) + (b == aj);
-                            if (coef) d32 = fmaf((float)coef, Jn[lane - j], d32);
-                        }
-                        ++nf;
-                        __syncwarp();
-                    }
-                    p = j + 1;
-                }
-                if (mine) {
-                    s[k] = (uint8_t)b;
-                    if constexpr (!kFP64) dE_acc += (double)((float)c * dmine);
-                }
-                if (lane == 0) {
-                    lcnt[cbuf] = nf;
-                    nacc += (unsigned long long)nf;
                 }
             }
         } else if (npend > 0) {
@@ -319,13 +243,13 @@ __global__ void __launch_bounds__(kSweepThreads, 4) sweep_kernel(const JobDev* _
         // E = -(c/2) sum_i h[s_i][i] from the FP64 fields (Eq. 2 through the fields)
         double part = 0.0;
         for (int i = tid; i < L; i += kSweepThreads) part += (double)h[(size_t)s[i] * Lpad + i];
-        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(kFull, part, o);
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(kFullMask, part, o);
         if (lane == 0) red[warp] = part;
     }
     if (warp == 0) {
         for (int o = 16; o > 0; o >>= 1) {
-            dE_acc += __shfl_xor_sync(kFull, dE_acc, o);
-            nnear += __shfl_xor_sync(kFull, nnear, o);
+            dE_acc += __shfl_xor_sync(kFullMask, dE_acc, o);
+            nnear += __shfl_xor_sync(kFullMask, nnear, o);
         }
     }
     __syncthreads();
@@ -382,6 +306,42 @@ cudaError_t launch_sweep(const JobDev* jobs_dev, const int2* work, int nwork, in
     case 5: return launch_variant<float, false, true>(jobs_dev, work, nwork, nsweeps, smem, st);
     case 6: return launch_variant<float, true, false>(jobs_dev, work, nwork, nsweeps, smem, st);
     default: return launch_variant<float, true, true>(jobs_dev, work, nwork, nsweeps, smem, st);
+    }
+}
+
+int rf_config(int L, int q)
+{
+    if (L <= 224) return 1;
+    if (L <= 448) return 2;
+    if (L <= 1120) return 3;
+    if (L <= 2400 && q <= 8) return 4;
+    if (L <= 4320 && q <= 8) return 5;
+    return 0;
+}
+
+size_t rf_smem_bytes(int cfg, int q, int L, int Lpad)
+{
+    switch (cfg) {
+    case 1: return sweep_rf_smem_a(q, L, Lpad);
+    case 2: return sweep_rf_smem_b(q, L, Lpad);
+    case 3: return sweep_rf_smem_c(q, L, Lpad);
+    case 4: return sweep_rf_smem_d(q, L, Lpad);
+    case 5: return sweep_rf_smem_e(q, L, Lpad);
+    default: return 0;
+    }
+}
+
+cudaError_t launch_sweep_rf(int cfg, int q, const JobDev* jobs_dev, const int2* work, int nwork, int nsweeps,
+                            size_t smem, cudaStream_t st)
+{
+    if (nwork <= 0 || nsweeps <= 0) return cudaSuccess;
+    switch (cfg) {
+    case 1: return launch_sweep_rf_a(q, jobs_dev, work, nwork, nsweeps, smem, st);
+    case 2: return launch_sweep_rf_b(q, jobs_dev, work, nwork, nsweeps, smem, st);
+    case 3: return launch_sweep_rf_c(q, jobs_dev, work, nwork, nsweeps, smem, st);
+    case 4: return launch_sweep_rf_d(q, jobs_dev, work, nwork, nsweeps, smem, st);
+    case 5: return launch_sweep_rf_e(q, jobs_dev, work, nwork, nsweeps, smem, st);
+    default: return cudaErrorNotSupported;
     }
 }
 

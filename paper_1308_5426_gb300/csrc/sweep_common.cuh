@@ -1,0 +1,174 @@
+// Pieces shared by the sweep kernels: the proposal draw of one site and the
+// exact in-order decision of a block of 32 sites by one warp (Eq. 8, Sec. 4.2).
+#pragma once
+#include <cmath>
+#include <cstdint>
+
+#include "philox.cuh"
+#include "potts_internal.h"
+
+namespace plr {
+
+constexpr unsigned kFullMask = 0xffffffffu;
+constexpr int kNearTable = 64;  // J* in FP32 for distances < 64 (corrections within two blocks)
+enum : int { kReject = 0, kAccept = 1, kUnsure = 2 };
+
+// FP64 rule, evaluated exactly: dE <= 0 or u < exp(-beta dE); near-tie count.
+__device__ __forceinline__ bool decide_fp64_exact(double d, double cb, double u, unsigned long long& near)
+{
+    if (d <= 0.0) return true;
+    const double x = cb * d;  // beta * c * d
+    const bool acc = u < exp(-x);
+    if (fabs(x + log(u)) < 1e-9) ++near;
+    return acc;
+}
+
+// FP32 filter of the FP64 rule.  d32 is within errd of the FP64 d: errd =
+// 2.4e-5 Jtot bounds the conversion and up to 64 FP32 corrections of
+// magnitude <= 3 Jtot, each rounded to 2^-24, with a factor 2 to spare; x and
+// -ln u are within 2.4e-7 relative of their FP64 values.
+__device__ __forceinline__ int decide_fp64_filter(float d, float cb, float nlu, float errd)
+{
+    if (d <= -errd) return kAccept;
+    if (d < errd) return kUnsure;
+    const float x = cb * d;
+    const float m = cb * errd + 1e-6f * (x + nlu + 1.0f);
+    if (x < nlu - m) return kAccept;
+    if (x > nlu + m) return kReject;
+    return kUnsure;
+}
+
+// Proposal of site k of slot t at sweep n: b uniform over the other q-1 states
+// and nlu = -ln u in FP32.  (ux1, ux2) are the words u is made of: FP64 mode's
+// u = ((ux1:ux2 >> 11) + 1) 2^-53 is formed only when the exact rule runs; its
+// FP32 value here is within 2^-23 relative.  FP32 mode: u = ((ux1 >> 8) + 1) 2^-24.
+template <bool kFP64>
+__device__ __forceinline__ void draw_proposal(int k, int t, uint32_t n, uint32_t key0, uint32_t key1, int q, int a,
+                                              int& b, float& nlu, uint32_t& ux1, uint32_t& ux2)
+{
+    const U4 x = philox10(U4{(uint32_t)k, (uint32_t)t, n, kTagMetro}, key0, key1);
+    b = a + 1 + (int)__umulhi(x.x, (uint32_t)(q - 1));
+    if (b >= q) b -= q;
+    ux1 = x.y;
+    ux2 = x.z;
+    if constexpr (kFP64) {
+        const float uf = (float)x.y * 0x1p-32f + (float)((x.z >> 11) + 1u) * 0x1p-53f;
+        nlu = -logf(uf);
+    } else {
+        nlu = -logf(unit24(x.y));
+    }
+}
+
+// Decide the nv sites of a block in site order, exactly as a sequential sweep
+// would.  Lane l holds site k = k0 + l (valid if l < nv) with spin a, proposal
+// b, nlu = -ln u, and d32 = h[a][k] - h[b][k] read from fields that do not yet
+// hold the flips (pk, pab)[0..npend) of the previous block (base64: the same
+// difference in FP64 mode).  First those flips are added as corrections; then
+// all undecided lanes evaluate the rule at once: the first lane that accepts
+// is certain to accept, every lane before it to reject.  After accepted flip j
+// every later lane corrects d32 by J*(l-j)([a=b_j]-[a=a_j]-[b=b_j]+[b=a_j]) --
+// the change flip j makes to h at site k_l -- and the scan continues after j,
+// one round per accepted flip.  Accepted flips are appended to (ck, cab) in
+// site order; returns their number.  Jn: J*(r) in FP32 for r < 64; J64: the
+// FP64 table (for the exact rule in FP64 mode).
+template <bool kFP64>
+__device__ __forceinline__ int decide_block(int lane, int nv, int k, int L, int a, int b, float nlu, uint32_t ux1,
+                                            uint32_t ux2, float d32, double base64, const int* pk, const int* pab,
+                                            int npend, float cb32, double cb64, float errd, const float* Jn,
+                                            const double* J64, int* ck, int* cab, bool& mine, float& dmine,
+                                            unsigned long long& nnear)
+{
+    const bool valid = lane < nv;
+    // corrections for the previous block's flips, four independent loads at a time
+    int f = 0;
+    for (; f + 4 <= npend; f += 4) {
+        float jv[4];
+        int cf[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int kf = pk[f + e], af = pab[f + e] >> 8, bf = pab[f + e] & 255;
+            int r = k - kf;
+            r += r < 0 ? L : 0;  // 1..63 for valid lanes
+            jv[e] = Jn[r & (kNearTable - 1)];
+            cf[e] = (a == bf) - (a == af) - (b == bf) + (b == af);
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) d32 = fmaf((float)cf[e], jv[e], d32);
+    }
+    for (; f < npend; ++f) {
+        const int kf = pk[f], af = pab[f] >> 8, bf = pab[f] & 255;
+        int r = k - kf;
+        r += r < 0 ? L : 0;
+        const int coef = (a == bf) - (a == af) - (b == bf) + (b == af);
+        d32 = fmaf((float)coef, Jn[r & (kNearTable - 1)], d32);
+    }
+    const int ab = (a << 8) | b;
+    unsigned accmask = 0;  // lanes whose flip was accepted
+    dmine = 0.0f;
+    int p = 0;
+    while (p < nv) {
+        int st = kReject;
+        if (valid && lane >= p) {
+            if constexpr (kFP64) st = decide_fp64_filter(d32, cb32, nlu, errd);
+            else st = (d32 <= 0.0f || cb32 * d32 < nlu) ? kAccept : kReject;
+        }
+        const unsigned hit = __ballot_sync(kFullMask, st != kReject);
+        if (!hit) break;
+        const int j = __ffs(hit) - 1;
+        bool acc = true;
+        if constexpr (kFP64) {
+            if (__shfl_sync(kFullMask, st, j) == kUnsure) {
+                // rare: lane j applies the FP64 rule to the FP64 difference, rebuilt
+                // from the previous block's flips and this block's accepted ones
+                const unsigned before = accmask & ((1u << j) - 1u);
+                if (accmask & (1u << lane)) {
+                    const int pos = __popc(accmask & ((1u << lane) - 1u));
+                    ck[pos] = k;
+                    cab[pos] = ab;
+                }
+                __syncwarp();
+                bool dec = false;
+                if (lane == j) {
+                    double d64 = base64;
+                    for (int g = 0; g < npend; ++g) {
+                        const int kf = pk[g], af = pab[g] >> 8, bf = pab[g] & 255;
+                        int r = k - kf;
+                        r += r < 0 ? L : 0;
+                        const int coef = (a == bf) - (a == af) - (b == bf) + (b == af);
+                        if (coef) d64 += (double)coef * J64[r];
+                    }
+                    const int nb = __popc(before);
+                    for (int g = 0; g < nb; ++g) {
+                        const int kf = ck[g], af = cab[g] >> 8, bf = cab[g] & 255;
+                        const int coef = (a == bf) - (a == af) - (b == bf) + (b == af);
+                        if (coef) d64 += (double)coef * J64[k - kf];
+                    }
+                    dec = decide_fp64_exact(d64, cb64, unit53(ux1, ux2), nnear);
+                }
+                acc = __shfl_sync(kFullMask, dec, j);
+                __syncwarp();
+            }
+        }
+        if (acc) {
+            const int abj = __shfl_sync(kFullMask, ab, j);
+            const float jd = Jn[(lane - j) & 31];
+            const int aj = abj >> 8, bj = abj & 255;
+            accmask |= 1u << j;
+            dmine = lane == j ? d32 : dmine;
+            const int coef = (lane > j && valid) ? (a == bj) - (a == aj) - (b == bj) + (b == aj) : 0;
+            d32 = fmaf((float)coef, jd, d32);
+        }
+        p = j + 1;
+    }
+    // the accepted flips, in site order
+    mine = (accmask >> lane) & 1u;
+    if (mine) {
+        const int pos = __popc(accmask & ((1u << lane) - 1u));
+        ck[pos] = k;
+        cab[pos] = ab;
+    }
+    __syncwarp();
+    return __popc(accmask);
+}
+
+}  // namespace plr

@@ -1,0 +1,307 @@
+// Register-resident FP32 Metropolis sweep (Eq. 8, Sec. 4.2 of the paper).
+//
+// One CTA per temperature slot: NU update warps hold the local fields
+// h[x][i] of their sites in registers, one decision warp holds none.  Update
+// thread u (0 <= u < 32 NU) keeps sites i = m 32 NU + u (m = 0..E-1) for all Q
+// states, so an accepted flip (a -> b at site k) costs it two warp-uniform
+// switches, h[a][i] -= J*((i-k) mod L) and h[b][i] += J*(...), and one
+// shared-memory read of J* per site; the fields never travel through shared
+// memory.  Sites are decided in blocks of 32 (block g: sites 32 g .. 32 g + 31,
+// held by update warp g mod NU in register row g / NU).  In phase g:
+//   - the decision warp reads block g's proposals and field values (published
+//     during phase g-1, not yet holding block g-1's flips), decides block g with
+//     the in-order scan of sweep_common.cuh (which adds block g-1's flips as
+//     corrections), publishes the accepted flips, then draws the proposals of
+//     block g+1;
+//   - every update warp applies block g-1's flips to its registers; the owner
+//     of block g+1 then publishes that block's field values.
+// One CTA barrier per block; deciding and updating overlap.
+//
+// The arithmetic is that of the shared-memory kernel -- the same FP32 values
+// J*, the same subtractions and additions in flip order, the same decisions
+// and the same grouping of the energy sum -- so both give identical results.
+#pragma once
+#include "sweep_common.cuh"
+
+namespace plr {
+namespace rf {
+
+template <int NU, int E, int Q>
+struct RfSmem {
+    static size_t bytes(int L, int Lpad)
+    {
+        size_t b = (size_t)(E * 32 * NU + L) * sizeof(float);  // J*(m mod L), m < E 32 NU + L
+        b += (size_t)Lpad;                                       // spins
+        b = (b + 15) & ~(size_t)15;
+        b += 2 * 2 * kSiteBlock * sizeof(int);   // double-buffered flip lists
+        b += kNearTable * sizeof(float);         // J*(r), r < 64
+        b += 32 * sizeof(double);                // per-lane energy change
+        b += 2 * kSiteBlock * sizeof(int);       // proposals (a << 8 | b), double-buffered
+        b += 2 * kSiteBlock * sizeof(float);     // -ln u, double-buffered
+        b += 2 * Q * kSiteBlock * sizeof(float); // published field values, double-buffered
+        b += 16;                                 // flip counts
+        return (b + 15) & ~(size_t)15;
+    }
+};
+
+#define PLR_RF_CASE(c, OP)                                                              \
+    case c:                                                                             \
+        if constexpr ((c) < Q) {                                                        \
+            _Pragma("unroll") for (int m = 0; m < E; ++m) h[m][c] OP v[m];              \
+        }                                                                               \
+        break;
+
+// apply flips (pk, pab)[0..nf) to all register rows of update thread u
+template <int Q, int E, int NU>
+__device__ __forceinline__ void apply_rows(float (&h)[E][Q], const float* __restrict__ J2, int u, int L,
+                                           const int* pk, const int* pab, int nf)
+{
+    for (int f = 0; f < nf; ++f) {
+        const int kf = pk[f], af = pab[f] >> 8, bf = pab[f] & 255;
+        float v[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = J2[m * 32 * NU + u - kf + L];
+        switch (af) {
+            PLR_RF_CASE(0, -=) PLR_RF_CASE(1, -=) PLR_RF_CASE(2, -=) PLR_RF_CASE(3, -=)
+            PLR_RF_CASE(4, -=) PLR_RF_CASE(5, -=) PLR_RF_CASE(6, -=) PLR_RF_CASE(7, -=)
+            PLR_RF_CASE(8, -=) PLR_RF_CASE(9, -=) PLR_RF_CASE(10, -=) PLR_RF_CASE(11, -=)
+            PLR_RF_CASE(12, -=) PLR_RF_CASE(13, -=) PLR_RF_CASE(14, -=) PLR_RF_CASE(15, -=)
+            default: break;
+        }
+        switch (bf) {
+            PLR_RF_CASE(0, +=) PLR_RF_CASE(1, +=) PLR_RF_CASE(2, +=) PLR_RF_CASE(3, +=)
+            PLR_RF_CASE(4, +=) PLR_RF_CASE(5, +=) PLR_RF_CASE(6, +=) PLR_RF_CASE(7, +=)
+            PLR_RF_CASE(8, +=) PLR_RF_CASE(9, +=) PLR_RF_CASE(10, +=) PLR_RF_CASE(11, +=)
+            PLR_RF_CASE(12, +=) PLR_RF_CASE(13, +=) PLR_RF_CASE(14, +=) PLR_RF_CASE(15, +=)
+            default: break;
+        }
+    }
+}
+
+#undef PLR_RF_CASE
+
+// publish register row M (all states) of this lane: hv[x][lane] = h[M][x]
+template <int Q, int E>
+__device__ __forceinline__ void publish_row(const float (&h)[E][Q], int M, float* hv, int lane)
+{
+#pragma unroll
+    for (int m = 0; m < E; ++m)
+        if (m == M) {
+#pragma unroll
+            for (int x = 0; x < Q; ++x) hv[x * kSiteBlock + lane] = h[m][x];
+        }
+}
+
+// CTAs per SM to aim for, holding the compiler to the matching register budget
+template <int Q, int E, int NU>
+constexpr int rf_min_blocks()
+{
+    const int threads = 32 * (NU + 1);
+    if (Q * E <= 25 && threads <= 256) return 4;  // fits 64 registers
+    const int need = threads * (Q * E + E + 48);
+    const int b = 65536 / need;
+    return b < 1 ? 1 : (b > 4 ? 4 : b);
+}
+
+template <int Q, int E, int NU>
+__global__ void __launch_bounds__(32 * (NU + 1), rf_min_blocks<Q, E, NU>())
+    sweep_rf_kernel(const JobDev* __restrict__ jobs, const int2* __restrict__ work, int nsweeps)
+{
+    constexpr int NUT = 32 * NU;  // update threads
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int2 wk = work[blockIdx.x];
+    const JobDev* jp = jobs + wk.x;
+    const int t = wk.y;
+    const int L = jp->L, q = jp->q, Lpad = jp->Lpad, W = jp->W, c = jp->c;
+    const uint32_t key0 = jp->key0, key1 = jp->key1;
+    const int rep = jp->map[t];
+    const double beta = jp->beta[t];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool decider = warp == NU;
+    float* __restrict__ hg = (float*)jp->fields + (size_t)rep * q * Lpad;
+    uint32_t* __restrict__ spins = jp->spins + (size_t)rep * W;
+
+    float* J2 = (float*)smem;
+    size_t off = (size_t)(E * NUT + L) * sizeof(float);
+    uint8_t* s = smem + off;
+    off = (off + (size_t)Lpad + 15) & ~(size_t)15;
+    int* lk = (int*)(smem + off);
+    int* lab = lk + 2 * kSiteBlock;
+    float* Jn = (float*)(lab + 2 * kSiteBlock);
+    double* dEl = (double*)(Jn + kNearTable);
+    int* pab = (int*)(dEl + 32);            // [2][32] proposals
+    float* pnlu = (float*)(pab + 2 * kSiteBlock);
+    float* hv = pnlu + 2 * kSiteBlock;      // [2][Q][32]
+    int* lcnt = (int*)(hv + 2 * Q * kSiteBlock);
+
+    for (int m = tid; m < E * NUT + L; m += blockDim.x) J2[m] = jp->J32d[m % L];
+    for (int i = tid; i < L; i += blockDim.x) s[i] = (uint8_t)((spins[i >> 3] >> (4 * (i & 7))) & 15u);
+    if (tid < kNearTable) Jn[tid] = tid < L ? (float)jp->J64d[tid] : 0.0f;
+    if (tid < 32) dEl[tid] = 0.0;
+    if (tid < 2) lcnt[tid] = 0;
+    float h[E][Q];
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+        const int i = m * NUT + tid;
+#pragma unroll
+        for (int x = 0; x < Q; ++x) h[m][x] = (!decider && i < L) ? hg[(size_t)x * Lpad + i] : 0.0f;
+    }
+    __syncthreads();
+
+    const uint32_t n0 = jp->nsweep[t];
+    const double cb64 = beta * (double)c;
+    const float cb32 = (float)cb64;
+    unsigned long long nacc = 0, nnear = 0;
+    const int nblk = (L + kSiteBlock - 1) / kSiteBlock;
+    const int total = nsweeps * nblk;
+
+    // proposals of block g into buffer g & 1 (decision warp)
+    auto draw_block = [&](int g) {
+        const int k = (g % nblk) * kSiteBlock + lane;
+        int a = 0, b = 0;
+        float nlu = 0.0f;
+        if (k < L) {
+            uint32_t ux1, ux2;
+            a = s[k];
+            draw_proposal<false>(k, t, n0 + (uint32_t)(g / nblk), key0, key1, q, a, b, nlu, ux1, ux2);
+        }
+        pab[(g & 1) * kSiteBlock + lane] = (a << 8) | b;
+        pnlu[(g & 1) * kSiteBlock + lane] = nlu;
+    };
+    // field values of block g into buffer g & 1 (its owner warp)
+    auto publish_block = [&](int g) {
+        const int gb = g % nblk;
+        if (warp == gb % NU) publish_row<Q, E>(h, gb / NU, hv + (g & 1) * Q * kSiteBlock, lane);
+    };
+
+    if (total > 0) {
+        if (decider) draw_block(0);
+        else publish_block(0);
+    }
+    __syncthreads();
+
+    for (int g = 0; g <= total; ++g) {
+        const int pb = (g + 1) & 1;  // block g-1's list
+        const int npend = g > 0 ? lcnt[pb] : 0;
+        const int* pk = lk + pb * kSiteBlock;
+        const int* pl = lab + pb * kSiteBlock;
+        if (decider) {
+            if (g < total) {
+                const int cb = g & 1;
+                const int k0 = (g % nblk) * kSiteBlock;
+                const int nv = min(kSiteBlock, L - k0);
+                const int k = k0 + lane;
+                const bool valid = lane < nv;
+                if (nblk == 1 && g > 0) {  // one block per sweep: its proposals could not be drawn early
+                    __syncwarp();
+                    draw_block(g);
+                    __syncwarp();
+                }
+                const int ab = pab[cb * kSiteBlock + lane];
+                const int a = ab >> 8, b = ab & 255;
+                const float nlu = pnlu[cb * kSiteBlock + lane];
+                float d32 = 0.0f;
+                if (valid) {
+                    const float* hvb = hv + cb * Q * kSiteBlock;
+                    d32 = hvb[a * kSiteBlock + lane] - hvb[b * kSiteBlock + lane];
+                }
+                int* ck = lk + cb * kSiteBlock;
+                int* cab = lab + cb * kSiteBlock;
+                bool mine;
+                float dmine;
+                const int nf = decide_block<false>(lane, nv, k, L, a, b, nlu, 0u, 0u, d32, 0.0, pk, pl, npend,
+                                                   cb32, cb64, 0.0f, Jn, nullptr, ck, cab, mine, dmine, nnear);
+                if (mine) {
+                    s[k] = (uint8_t)b;
+                    dEl[lane] += (double)((float)c * dmine);
+                }
+                if (lane == 0) {
+                    lcnt[cb] = nf;
+                    nacc += (unsigned long long)nf;
+                }
+                if (nblk > 1 && g + 1 < total) {
+                    __syncwarp();
+                    draw_block(g + 1);
+                }
+            }
+        } else {
+            apply_rows<Q, E, NU>(h, J2, tid, L, pk, pl, npend);
+            if (g + 1 < total) publish_block(g + 1);
+        }
+        __syncthreads();
+    }
+
+    // write back
+    for (int w = tid; w < W; w += blockDim.x) {
+        uint32_t word = 0;
+        for (int m = 0; m < 8; ++m) {
+            const int i = 8 * w + m;
+            if (i < L) word |= (uint32_t)s[i] << (4 * m);
+        }
+        spins[w] = word;
+    }
+    if (!decider) {
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const int i = m * NUT + tid;
+            if (i < L) {
+#pragma unroll
+                for (int x = 0; x < Q; ++x) hg[(size_t)x * Lpad + i] = h[m][x];
+            }
+        }
+    } else {
+        double dE = dEl[lane];
+        for (int o = 16; o > 0; o >>= 1) dE += __shfl_xor_sync(kFullMask, dE, o);
+        if (lane == 0) {
+            jp->E[rep] += dE;
+            jp->nsweep[t] = n0 + (uint32_t)nsweeps;
+            if (nacc) atomicAdd(&jp->acc_flip[t], nacc);
+        }
+    }
+}
+
+template <int Q, int E, int NU>
+cudaError_t launch_rf(const JobDev* jobs_dev, const int2* work, int nwork, int nsweeps, size_t smem,
+                      cudaStream_t st)
+{
+    auto k = sweep_rf_kernel<Q, E, NU>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<nwork, 32 * (NU + 1), smem, st>>>(jobs_dev, work, nsweeps);
+    return cudaGetLastError();
+}
+
+// dispatch over Q for one (E, NU) configuration
+template <int E, int NU, int QMAX>
+cudaError_t launch_rf_q(int q, const JobDev* jobs_dev, const int2* work, int nwork, int nsweeps, size_t smem,
+                        cudaStream_t st)
+{
+    switch (q) {
+#define PLR_RF_Q(Qv) \
+    case Qv:         \
+        if constexpr (Qv <= QMAX) return launch_rf<Qv, E, NU>(jobs_dev, work, nwork, nsweeps, smem, st); \
+        break;
+        PLR_RF_Q(2) PLR_RF_Q(3) PLR_RF_Q(4) PLR_RF_Q(5) PLR_RF_Q(6) PLR_RF_Q(7) PLR_RF_Q(8) PLR_RF_Q(9)
+        PLR_RF_Q(10) PLR_RF_Q(11) PLR_RF_Q(12) PLR_RF_Q(13) PLR_RF_Q(14) PLR_RF_Q(15) PLR_RF_Q(16)
+#undef PLR_RF_Q
+    default: break;
+    }
+    return cudaErrorNotSupported;
+}
+
+// smem bytes for one (E, NU) configuration (depends on q through the published values)
+template <int E, int NU>
+size_t rf_smem_q(int q, int L, int Lpad)
+{
+    switch (q) {
+#define PLR_RF_S(Qv) \
+    case Qv: return RfSmem<NU, E, Qv>::bytes(L, Lpad);
+        PLR_RF_S(2) PLR_RF_S(3) PLR_RF_S(4) PLR_RF_S(5) PLR_RF_S(6) PLR_RF_S(7) PLR_RF_S(8) PLR_RF_S(9)
+        PLR_RF_S(10) PLR_RF_S(11) PLR_RF_S(12) PLR_RF_S(13) PLR_RF_S(14) PLR_RF_S(15) PLR_RF_S(16)
+#undef PLR_RF_S
+    default: return 0;
+    }
+}
+
+}  // namespace rf
+}  // namespace plr

@@ -1,0 +1,15 @@
+// Register-resident FP32 sweep: E = 9 sites per update thread, 15 update warps
+// + 1 decision warp per CTA, q <= 8 (chains up to L = 4320).
+#include "sweep_rf.cuh"
+
+namespace plr {
+
+cudaError_t launch_sweep_rf_e(int q, const JobDev* jobs_dev, const int2* work, int nwork, int nsweeps,
+                               size_t smem, cudaStream_t st)
+{
+    return rf::launch_rf_q<9, 15, 8>(q, jobs_dev, work, nwork, nsweeps, smem, st);
+}
+
+size_t sweep_rf_smem_e(int q, int L, int Lpad) { return rf::rf_smem_q<9, 15>(q, L, Lpad); }
+
+}  // namespace plr

@@ -108,3 +108,33 @@ def test_fp32_and_fp64_sample_the_same_observables(plr):
             m64, s64 = _binned(res["fp64"][k][:, t])
             se = math.hypot(s32, s64)
             assert abs(m32 - m64) < 3 * se + 1e-9, (name, t, m32, m64, se)
+
+
+@pytest.mark.parametrize("L,q,sigma,R", [
+    (200, 3, 0.5, 4), (256, 16, 0.3, 3), (500, 5, 0.7, 5), (1000, 16, 0.4, 3), (1024, 5, 0.4, 8),
+    (2048, 8, 0.6, 3), (1999, 2, 0.2, 4), (4096, 8, 0.2, 3), (3000, 6, 0.9, 2),
+])
+def test_register_path_equals_memory_path(plr, L, q, sigma, R):
+    """The register-resident FP32 sweep and the shared/global-memory FP32 sweep
+    run the same arithmetic: spins, fields, energies and counters agree bit for
+    bit after sweeps, exchanges and tensor-core rebuilds."""
+    temps = workloads.geometric_ratios(R, 0.05, 1.0) * oracle.jtot(L, sigma)
+    a = plr.Job(L, q, sigma, temps, 9, precision="fp32", recompute_every=6, sweep_variant="memory")
+    b = plr.Job(L, q, sigma, temps, 9, precision="fp32", recompute_every=6, sweep_variant="registers")
+    for _ in range(15):
+        a.sweep(1)
+        a.exchange()
+        b.sweep(1)
+        b.exchange()
+    a.sweep(3)
+    b.sweep(3)
+    np.testing.assert_array_equal(a.spins(), b.spins())
+    np.testing.assert_array_equal(a.fields(), b.fields())
+    np.testing.assert_array_equal(a.running_energy(), b.running_energy())
+    np.testing.assert_array_equal(a.stats()["acc_flip"], b.stats()["acc_flip"])
+
+
+def test_register_path_rejects_large_shapes(plr):
+    temps = np.linspace(1.0, 2.0, 2)
+    with pytest.raises(plr.PottsError):
+        plr.Job(8192, 10, 0.5, temps, 1, precision="fp32", sweep_variant="registers")
