@@ -11,10 +11,10 @@
 //   - the decision warp reads block g's proposals and field values (published
 //     during phase g-1, not yet holding block g-1's flips), decides block g with
 //     the in-order scan of sweep_common.cuh (which adds block g-1's flips as
-//     corrections), publishes the accepted flips, then draws the proposals of
-//     block g+1;
+//     corrections) and publishes the accepted flips;
 //   - every update warp applies block g-1's flips to its registers; the owner
-//     of block g+1 then publishes that block's field values.
+//     of block g+1 then publishes that block's field values and draws its
+//     proposals.
 // One CTA barrier per block; deciding and updating overlap.
 //
 // The arithmetic is that of the shared-memory kernel -- the same FP32 values
@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(32 * (NU + 1), rf_min_blocks<Q, E, NU>())
     const int nblk = (L + kSiteBlock - 1) / kSiteBlock;
     const int total = nsweeps * nblk;
 
-    // proposals of block g into buffer g & 1 (decision warp)
+    // proposals of block g into buffer g & 1 (one warp)
     auto draw_block = [&](int g) {
         const int k = (g % nblk) * kSiteBlock + lane;
         int a = 0, b = 0;
@@ -168,16 +168,16 @@ __global__ void __launch_bounds__(32 * (NU + 1), rf_min_blocks<Q, E, NU>())
         pab[(g & 1) * kSiteBlock + lane] = (a << 8) | b;
         pnlu[(g & 1) * kSiteBlock + lane] = nlu;
     };
-    // field values of block g into buffer g & 1 (its owner warp)
+    // field values and proposals of block g into buffer g & 1 (its owner warp)
     auto publish_block = [&](int g) {
         const int gb = g % nblk;
-        if (warp == gb % NU) publish_row<Q, E>(h, gb / NU, hv + (g & 1) * Q * kSiteBlock, lane);
+        if (warp == gb % NU) {
+            publish_row<Q, E>(h, gb / NU, hv + (g & 1) * Q * kSiteBlock, lane);
+            if (nblk > 1 || g == 0) draw_block(g);
+        }
     };
 
-    if (total > 0) {
-        if (decider) draw_block(0);
-        else publish_block(0);
-    }
+    if (total > 0 && !decider) publish_block(0);
     __syncthreads();
 
     for (int g = 0; g <= total; ++g) {
@@ -218,10 +218,6 @@ __global__ void __launch_bounds__(32 * (NU + 1), rf_min_blocks<Q, E, NU>())
                 if (lane == 0) {
                     lcnt[cb] = nf;
                     nacc += (unsigned long long)nf;
-                }
-                if (nblk > 1 && g + 1 < total) {
-                    __syncwarp();
-                    draw_block(g + 1);
                 }
             }
         } else {
