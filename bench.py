@@ -141,6 +141,33 @@ def peaks():
     return p
 
 
+SWEEP_SOURCES = ["sweep.cu", "sweep_common.cuh", "philox.cuh", "potts_internal.h"]
+SWEEP_PROFILE = os.path.join(ROOT, "profiles", "sweep_fp64_chains_L1024_q5.md")
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the FP64 sweep kernel from its committed ncu
+    summary, or None if the kernel sources changed since the capture."""
+    import hashlib
+    try:
+        h = hashlib.sha256()
+        for f in SWEEP_SOURCES:
+            with open(os.path.join(ROOT, "paper_1308_5426_gb300", "csrc", f), "rb") as fh:
+                h.update(fh.read())
+        digest = h.hexdigest()[:16]
+        vals = {}
+        with open(SWEEP_PROFILE) as fh:
+            for line in fh:
+                parts = line.strip().split(":")
+                if len(parts) == 2 and parts[0] in ("source_sha256_16", "traffic_bytes_per_launch"):
+                    vals[parts[0]] = parts[1].strip()
+        if vals.get("source_sha256_16") == digest:
+            return int(vals["traffic_bytes_per_launch"])
+    except (OSError, ValueError, KeyError):
+        pass
+    return None
+
+
 def alu_peak(kind, sm_max_mhz):
     """ALU peaks from unit counts and the maximum SM clock: 152 SMs; FP32: 128
     lanes/clk/SM; FP64: the nominal 1.25 TFLOP/s of GB300 is 2 FMA/clk/SM at
@@ -449,10 +476,12 @@ def main():
     flops_launch = att_launch * A * 2 * L  # the rank-1 field updates: 2L adds per accepted flip
     peak_adds = alu_peak(prec, ck.get("sm_max_mhz"))
     achieved = flops_launch / sweep_avg_s
-    traffic = None
+    traffic = profiled_traffic() if (args.workload == "chains" and prec == "fp64") else None
+    measured = plr.probe("fp64_add" if prec == "fp64" else "fp32_add")
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_adds / 1e12, "unit": "TFLOP/s",
-            "frac": achieved / peak_adds, "traffic": traffic, "kernel": "sweep_kernel<%s>" %
-            ("double" if prec == "fp64" else "float"),
+            "frac": achieved / peak_adds, "traffic": traffic,
+            "peak_measured_probe": measured / 1e12, "frac_of_measured_probe": achieved / measured,
+            "kernel": "sweep_kernel<%s>" % ("double" if prec == "fp64" else "float"),
             "work": "A*2L %s adds per attempt, A=%.4f measured; %d attempts per launch" % (prec, A, att_launch),
             "peak_source": "unit counts x max SM clock (2 FP64 / 128 FP32 add lanes per SM per clock, 152 SMs)",
             "sweep_ms_avg": sweep_avg_s * 1e3}

@@ -1,0 +1,51 @@
+"""Small, self-contained GPU cases for profiling single kernels with ncu.
+
+    python -m paper_1308_5426_gb300.profile_case <case>
+
+cases:
+  chains_fp64   8 chains L=1024 q=5 R=64, FP64 fields (shared-memory sweep kernel), 4 sweeps
+  chains_fp32   the same chains in FP32 (register-resident sweep kernel), 4 sweeps
+  precision_fp32  L=4096 q=8 R=128, FP32 (register-resident sweep), 3 sweeps
+  rebuild_fp32  L=4096 q=8 R=128, FP32: 3 tensor-core field rebuilds + measurements
+Each case builds its jobs, runs, synchronises and exits 0; inputs are the
+seeded workloads of paper_1308_5426_gb300.workloads.
+"""
+import sys
+
+
+def main(argv):
+    import paper_1308_5426_gb300 as plr
+    from paper_1308_5426_gb300 import workloads
+
+    case = argv[1] if len(argv) > 1 else ""
+    if case in ("chains_fp64", "chains_fp32"):
+        specs, prec, nsw = workloads.chains_jobs(), case[-4:], 4
+    elif case == "precision_fp32":
+        specs, prec, nsw = [workloads.precision_job("fp32")], "fp32", 3
+    elif case == "rebuild_fp32":
+        s = workloads.precision_job("fp32")
+        j = plr.Job(s.L, s.q, s.sigma, s.ratios * plr.jtot(s.L, s.sigma), s.seed, precision="fp32",
+                    recompute_every=0)
+        j.sweep(1)
+        for _ in range(3):
+            j.fields_recompute()
+            j.measure()
+        j.sync()
+        print("ok", case)
+        return 0
+    else:
+        print(__doc__)
+        return 2
+    jobs = [plr.Job(s.L, s.q, s.sigma, s.ratios * plr.jtot(s.L, s.sigma), s.seed, precision=prec,
+                    recompute_every=0) for s in specs]
+    b = plr.Batch(jobs)
+    for _ in range(nsw):
+        b.sweep(1)
+        b.exchange()
+    b.sync()
+    print("ok", case)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main(sys.argv))
