@@ -70,6 +70,7 @@ struct potts_lr {
     double* pinned;               // 2R doubles of pinned host memory for measure
     int4* dtiles;                 // FP32: tensor-core rebuild tiles of this job (job index 0)
     int ntiles;
+    SweepSched sched;             // placement of the R slots on the SMs
 };
 
 struct potts_lr_batch {
@@ -83,6 +84,7 @@ struct potts_lr_batch {
         int2* dwork;
         int nwork;
         size_t smem;
+        SweepSched sched;
     };
     std::vector<Group> groups;
     std::vector<int> fp32_jobs;  // jobs that need the conditional rebuild
@@ -156,10 +158,10 @@ int variant_key(const potts_lr_t* h)
 }
 
 cudaError_t launch_variant(int key, const JobDev* jobs, const int2* work, int nwork, int nsweeps, size_t smem,
-                           cudaStream_t st)
+                           const SweepSched* sched, cudaStream_t st)
 {
     if (key >= 100) return launch_sweep_rf((key - 100) / 32, (key - 100) % 32, jobs, work, nwork, nsweeps, smem, st);
-    return launch_sweep(jobs, work, nwork, nsweeps, key >> 2, (key >> 1) & 1, key & 1, smem, st);
+    return launch_sweep(jobs, work, nwork, nsweeps, key >> 2, (key >> 1) & 1, key & 1, smem, sched, st);
 }
 
 int rebuild(potts_lr_t* h)
@@ -323,6 +325,8 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
     std::vector<int4> tiles;
     if (h->precision == POTTS_LR_FP32) tc_tiles(0, L, q, R, tiles);
     const size_t o_tiles = take(tiles.size() * sizeof(int4) + 16);
+    const int nsm = device_sm_count();
+    const size_t o_plan = take(sweep_sched_bytes(R, nsm));
     cudaError_t e = cudaMalloc(&h->arena, off);
     if (e != cudaSuccess) {
         potts_lr_destroy(h);
@@ -369,6 +373,7 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
     j.sched = (int*)(base + o_sched);
     h->dtiles = (int4*)(base + o_tiles);
     h->ntiles = (int)tiles.size();
+    sweep_sched_carve(base + o_plan, R, nsm, &h->sched);
     j.drift_bits = (unsigned long long*)(base + o_drift);
     // residency of the sweep kernel's working set: fields and table in shared
     // memory when they fit, else fields first, else the table, else neither
@@ -432,7 +437,7 @@ int potts_lr_sweep(potts_lr_t* h, int n)
     if (n == 0) return POTTS_LR_OK;
     const int key = variant_key(h);
     if (h->K <= 0) {
-        cudaError_t e = launch_variant(key, h->dj, h->dwork, h->R, n, h->sweep_smem, h->stream);
+        cudaError_t e = launch_variant(key, h->dj, h->dwork, h->R, n, h->sweep_smem, &h->sched, h->stream);
         if (e != cudaSuccess) return cuda_fail(e, "sweep kernel");
         h->nsweep += (uint32_t)n;
         return POTTS_LR_OK;
@@ -440,7 +445,7 @@ int potts_lr_sweep(potts_lr_t* h, int n)
     // FP32 mode with automatic rebuilds: the schedule lives on the device, so
     // every sweep is followed by the conditional rebuild
     for (int s = 0; s < n; ++s) {
-        cudaError_t e = launch_variant(key, h->dj, h->dwork, h->R, 1, h->sweep_smem, h->stream);
+        cudaError_t e = launch_variant(key, h->dj, h->dwork, h->R, 1, h->sweep_smem, &h->sched, h->stream);
         if (e != cudaSuccess) return cuda_fail(e, "sweep kernel");
         h->nsweep += 1u;
         e = rebuild_launch(h, h->dj, 1, h->stream);
@@ -752,10 +757,13 @@ int potts_lr_batch_create(potts_lr_t* const* jobs, int n, void* cuda_stream, pot
     b->ntc_tiles = (int)btiles.size();
     b->nfp_work = (int)fwork.size();
     size_t bytes = align256(n * sizeof(JobDev));
-    std::map<int, size_t> ow;
+    std::map<int, size_t> ow, osch;
+    const int nsm = device_sm_count();
     for (auto& kv : works) {
         ow[kv.first] = bytes;
         bytes += align256(kv.second.size() * sizeof(int2) + 8);
+        osch[kv.first] = bytes;
+        bytes += align256(sweep_sched_bytes((int)kv.second.size(), nsm));
     }
     const size_t o_m = bytes;
     bytes += align256(mwork.size() * sizeof(int2));
@@ -784,6 +792,7 @@ int potts_lr_batch_create(potts_lr_t* const* jobs, int n, void* cuda_stream, pot
         g.dwork = (int2*)((char*)b->arena + ow[kv.first]);
         g.nwork = (int)kv.second.size();
         g.smem = smem[kv.first];
+        sweep_sched_carve((char*)b->arena + osch[kv.first], g.nwork, nsm, &g.sched);
         b->groups.push_back(g);
         e = cudaMemcpyAsync(g.dwork, kv.second.data(), kv.second.size() * sizeof(int2), cudaMemcpyHostToDevice,
                             b->stream);
@@ -814,7 +823,8 @@ static cudaError_t batch_enqueue_sweeps(potts_lr_batch_t* b)
 {
     cudaError_t e;
     for (const auto& g : b->groups)
-        if ((e = launch_variant(g.key, b->djobs, g.dwork, g.nwork, 1, g.smem, b->stream)) != cudaSuccess) return e;
+        if ((e = launch_variant(g.key, b->djobs, g.dwork, g.nwork, 1, g.smem, &g.sched, b->stream)) != cudaSuccess)
+            return e;
     if (b->fp32_jobs.empty()) return cudaSuccess;
     // the rebuilds that fall due, for all FP32 jobs at once: tensor-core fields,
     // energy re-anchor, schedule update

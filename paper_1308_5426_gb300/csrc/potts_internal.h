@@ -58,6 +58,31 @@ __device__ __forceinline__ bool rebuild_due(const JobDev& jb)
     return jb.recompute_every > 0 && jb.nsweep[0] >= (uint32_t)jb.sched[1];
 }
 
+// Placement of the work items of one sweep launch on the SMs.  The field
+// updates of a slot cost about (accepted flips per sweep) x L, which varies
+// many-fold along a temperature ladder, and the CTAs resident on one SM share
+// its FP64 (or FP32) pipe; hardware placement ignores that.  A plan kernel
+// orders the items by that estimate (from the slot counters) and deals the
+// heaviest nsm * occ of them to (SM, resident CTA) places in serpentine order;
+// sweep CTAs claim their place by SM id, then take the remaining items, in
+// order, from the list (every item is claimed exactly once, wherever the
+// CTAs land, so placement changes the timing only, never the results).
+constexpr int kSchedMaxOcc = 8;    // resident sweep CTAs per SM that a plan can address
+struct SweepSched {
+    int* order;   // [n] item indices, heaviest first
+    int* bins;    // [nsm * occ] item of each (SM, resident CTA) place, -1 for none
+    int* claim;   // [n] 0 until an item is taken
+    int* ctr;     // [nsm + 2]: arrivals per SM, next list position, CTAs past their claim
+    int n, nsm, occ;
+};
+size_t sweep_sched_bytes(int n, int nsm);
+// carve a SweepSched for n items out of device memory at base (sweep_sched_bytes long)
+void sweep_sched_carve(char* base, int n, int nsm, SweepSched* s);
+// device SM count (cached per device)
+int device_sm_count();
+// the plan kernel (one CTA); weights from jobs[work[i].x] counters
+cudaError_t launch_sweep_plan(const JobDev* jobs_dev, const int2* work, const SweepSched& s, cudaStream_t st);
+
 // ---- host-side helpers (jstar.cpp) ----
 void jstar_table(int L, double sigma, double* out);
 
@@ -65,8 +90,9 @@ void jstar_table(int L, double sigma, double* out);
 // work[i] = {job index, slot}; one CTA per work item
 cudaError_t launch_init_spins(const JobDev* jobs_dev, int job, int L, int W, int R, cudaStream_t st);
 // the kernel variant (precision, fields in smem, table in smem) is uniform per launch
+// sched: placement buffers for this work list (nullptr: one CTA per item, in order)
 cudaError_t launch_sweep(const JobDev* jobs_dev, const int2* work, int nwork, int nsweeps, int precision,
-                         int h_smem, int j_smem, size_t smem_bytes, cudaStream_t st);
+                         int h_smem, int j_smem, size_t smem_bytes, const SweepSched* sched, cudaStream_t st);
 cudaError_t launch_exchange(const JobDev* jobs_dev, int njobs, cudaStream_t st);
 // "cond" arguments: when nonzero the kernel does nothing unless the job's
 // sweep counter is a positive multiple of its recompute_every (a rebuild that

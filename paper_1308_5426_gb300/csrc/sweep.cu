@@ -1,7 +1,8 @@
 // Metropolis sweep of the long-range Potts chain (Eq. 8, Sec. 4.2 of the paper)
 // with local fields h[x][i] = sum_{j != i} J*(|i-j|) delta(x, s_j).
 //
-// One CTA per temperature slot; 8 warps.  Sites are taken in blocks of 32 in
+// One CTA sweeps one temperature slot at a time (see SweepSched for which
+// CTA takes which slot); 8 warps.  Sites are taken in blocks of 32 in
 // order k = 0..L-1.  Warp 0 decides a block; warps 1..7 meanwhile apply the
 // previous block's accepted flips to the fields (the rank-1 updates
 // h[a][i] -= J*(|i-k|), h[b][i] += J*(|i-k|)), except at the 32 sites of the
@@ -24,6 +25,7 @@
 #include <cmath>
 
 #include "sweep_common.cuh"
+#include "sweep_sched.cuh"
 
 namespace plr {
 
@@ -102,13 +104,12 @@ __device__ __forceinline__ void apply_flips(T* __restrict__ h, const T* __restri
     }
 }
 
+// nsweeps sweeps of one work item wk = (job, slot) by the whole CTA
 template <typename T, bool HS, bool JS>
-__global__ void __launch_bounds__(kSweepThreads, HS ? 4 : 2) sweep_kernel(const JobDev* __restrict__ jobs,
-                                                              const int2* __restrict__ work, int nsweeps)
+__device__ __forceinline__ void sweep_item(const JobDev* __restrict__ jobs, const int2 wk, int nsweeps,
+                                           unsigned char* __restrict__ smem)
 {
     constexpr bool kFP64 = sizeof(T) == 8;
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int2 wk = work[blockIdx.x];
     const JobDev* jp = jobs + wk.x;
     const int t = wk.y;
     const int L = jp->L, q = jp->q, Lpad = jp->Lpad, W = jp->W, c = jp->c;
@@ -267,14 +268,57 @@ __global__ void __launch_bounds__(kSweepThreads, HS ? 4 : 2) sweep_kernel(const 
     }
 }
 
+// Without a plan (sc.n == 0) CTA b sweeps item b.  With one, the grid is
+// persistent: each CTA takes the item dealt to its place on its SM, then
+// further items from the ordered list until none is left.
+template <typename T, bool HS, bool JS>
+__global__ void __launch_bounds__(kSweepThreads, HS ? 4 : 2) sweep_kernel(const JobDev* __restrict__ jobs,
+                                                              const int2* __restrict__ work, int nsweeps,
+                                                              const SweepSched sc)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    if (sc.n == 0) {
+        sweep_item<T, HS, JS>(jobs, work[blockIdx.x], nsweeps, smem);
+        return;
+    }
+    __shared__ int s_item;
+    bool waited = false;  // thread 0's
+    if (threadIdx.x == 0) s_item = sched_claim_home(sc);
+    __syncthreads();
+    for (;;) {
+        const int item = s_item;
+        if (item >= 0) sweep_item<T, HS, JS>(jobs, work[item], nsweeps, smem);
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = sched_claim_next(sc, waited);
+        __syncthreads();
+        if (s_item < 0) break;
+    }
+}
+
 template <typename T, bool HS, bool JS>
 cudaError_t launch_variant(const JobDev* jobs_dev, const int2* work, int nwork, int nsweeps, size_t smem,
-                           cudaStream_t st)
+                           const SweepSched* sched, cudaStream_t st)
 {
     auto k = sweep_kernel<T, HS, JS>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k<<<nwork, kSweepThreads, smem, st>>>(jobs_dev, work, nsweeps);
+    SweepSched sc{};
+    int grid = nwork;
+    // a plan pays when there are more items than SMs (fewer: the hardware
+    // already gives each its own SM)
+    if (sched && sched->nsm > 0 && nwork > sched->nsm) {
+        int occ = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kSweepThreads, smem);
+        if (e != cudaSuccess) return e;
+        if (occ > 0) {
+            sc = *sched;
+            sc.n = nwork;
+            sc.occ = occ < kSchedMaxOcc ? occ : kSchedMaxOcc;
+            grid = sc.nsm * sc.occ;
+            if ((e = launch_sweep_plan(jobs_dev, work, sc, st)) != cudaSuccess) return e;
+        }
+    }
+    k<<<grid, kSweepThreads, smem, st>>>(jobs_dev, work, nsweeps, sc);
     return cudaGetLastError();
 }
 
@@ -293,19 +337,19 @@ size_t sweep_smem_bytes_for(int precision, int L, int Lpad, int q, int h_smem, i
 }
 
 cudaError_t launch_sweep(const JobDev* jobs_dev, const int2* work, int nwork, int nsweeps, int precision,
-                         int h_smem, int j_smem, size_t smem, cudaStream_t st)
+                         int h_smem, int j_smem, size_t smem, const SweepSched* sched, cudaStream_t st)
 {
     if (nwork <= 0 || nsweeps <= 0) return cudaSuccess;
     const int v = (precision ? 4 : 0) | (h_smem ? 2 : 0) | (j_smem ? 1 : 0);
     switch (v) {
-    case 0: return launch_variant<double, false, false>(jobs_dev, work, nwork, nsweeps, smem, st);
-    case 1: return launch_variant<double, false, true>(jobs_dev, work, nwork, nsweeps, smem, st);
-    case 2: return launch_variant<double, true, false>(jobs_dev, work, nwork, nsweeps, smem, st);
-    case 3: return launch_variant<double, true, true>(jobs_dev, work, nwork, nsweeps, smem, st);
-    case 4: return launch_variant<float, false, false>(jobs_dev, work, nwork, nsweeps, smem, st);
-    case 5: return launch_variant<float, false, true>(jobs_dev, work, nwork, nsweeps, smem, st);
-    case 6: return launch_variant<float, true, false>(jobs_dev, work, nwork, nsweeps, smem, st);
-    default: return launch_variant<float, true, true>(jobs_dev, work, nwork, nsweeps, smem, st);
+    case 0: return launch_variant<double, false, false>(jobs_dev, work, nwork, nsweeps, smem, sched, st);
+    case 1: return launch_variant<double, false, true>(jobs_dev, work, nwork, nsweeps, smem, sched, st);
+    case 2: return launch_variant<double, true, false>(jobs_dev, work, nwork, nsweeps, smem, sched, st);
+    case 3: return launch_variant<double, true, true>(jobs_dev, work, nwork, nsweeps, smem, sched, st);
+    case 4: return launch_variant<float, false, false>(jobs_dev, work, nwork, nsweeps, smem, sched, st);
+    case 5: return launch_variant<float, false, true>(jobs_dev, work, nwork, nsweeps, smem, sched, st);
+    case 6: return launch_variant<float, true, false>(jobs_dev, work, nwork, nsweeps, smem, sched, st);
+    default: return launch_variant<float, true, true>(jobs_dev, work, nwork, nsweeps, smem, sched, st);
     }
 }
 
