@@ -160,7 +160,8 @@ int variant_key(const potts_lr_t* h)
 cudaError_t launch_variant(int key, const JobDev* jobs, const int2* work, int nwork, int nsweeps, size_t smem,
                            const SweepSched* sched, cudaStream_t st)
 {
-    if (key >= 100) return launch_sweep_rf((key - 100) / 32, (key - 100) % 32, jobs, work, nwork, nsweeps, smem, st);
+    if (key >= 100)
+        return launch_sweep_rf((key - 100) / 32, (key - 100) % 32, jobs, work, nwork, nsweeps, smem, sched, st);
     return launch_sweep(jobs, work, nwork, nsweeps, key >> 2, (key >> 1) & 1, key & 1, smem, sched, st);
 }
 

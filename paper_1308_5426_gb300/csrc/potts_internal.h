@@ -126,12 +126,17 @@ size_t sweep_smem_bytes(const JobDev& j);
 int rf_config(int L, int q);
 size_t rf_smem_bytes(int cfg, int q, int L, int Lpad);
 cudaError_t launch_sweep_rf(int cfg, int q, const JobDev* jobs_dev, const int2* work, int nwork, int nsweeps,
-                            size_t smem, cudaStream_t st);
-cudaError_t launch_sweep_rf_a(int q, const JobDev*, const int2*, int, int, size_t, cudaStream_t);
-cudaError_t launch_sweep_rf_b(int q, const JobDev*, const int2*, int, int, size_t, cudaStream_t);
-cudaError_t launch_sweep_rf_c(int q, const JobDev*, const int2*, int, int, size_t, cudaStream_t);
-cudaError_t launch_sweep_rf_d(int q, const JobDev*, const int2*, int, int, size_t, cudaStream_t);
-cudaError_t launch_sweep_rf_e(int q, const JobDev*, const int2*, int, int, size_t, cudaStream_t);
+                            size_t smem, const SweepSched* sched, cudaStream_t st);
+cudaError_t launch_sweep_rf_a(int q, const JobDev*, const int2*, int, int, size_t, const SweepSched*,
+                             cudaStream_t);
+cudaError_t launch_sweep_rf_b(int q, const JobDev*, const int2*, int, int, size_t, const SweepSched*,
+                             cudaStream_t);
+cudaError_t launch_sweep_rf_c(int q, const JobDev*, const int2*, int, int, size_t, const SweepSched*,
+                             cudaStream_t);
+cudaError_t launch_sweep_rf_d(int q, const JobDev*, const int2*, int, int, size_t, const SweepSched*,
+                             cudaStream_t);
+cudaError_t launch_sweep_rf_e(int q, const JobDev*, const int2*, int, int, size_t, const SweepSched*,
+                             cudaStream_t);
 size_t sweep_rf_smem_a(int q, int L, int Lpad);
 size_t sweep_rf_smem_b(int q, int L, int Lpad);
 size_t sweep_rf_smem_c(int q, int L, int Lpad);

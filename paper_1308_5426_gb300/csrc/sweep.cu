@@ -376,15 +376,15 @@ size_t rf_smem_bytes(int cfg, int q, int L, int Lpad)
 }
 
 cudaError_t launch_sweep_rf(int cfg, int q, const JobDev* jobs_dev, const int2* work, int nwork, int nsweeps,
-                            size_t smem, cudaStream_t st)
+                            size_t smem, const SweepSched* sched, cudaStream_t st)
 {
     if (nwork <= 0 || nsweeps <= 0) return cudaSuccess;
     switch (cfg) {
-    case 1: return launch_sweep_rf_a(q, jobs_dev, work, nwork, nsweeps, smem, st);
-    case 2: return launch_sweep_rf_b(q, jobs_dev, work, nwork, nsweeps, smem, st);
-    case 3: return launch_sweep_rf_c(q, jobs_dev, work, nwork, nsweeps, smem, st);
-    case 4: return launch_sweep_rf_d(q, jobs_dev, work, nwork, nsweeps, smem, st);
-    case 5: return launch_sweep_rf_e(q, jobs_dev, work, nwork, nsweeps, smem, st);
+    case 1: return launch_sweep_rf_a(q, jobs_dev, work, nwork, nsweeps, smem, sched, st);
+    case 2: return launch_sweep_rf_b(q, jobs_dev, work, nwork, nsweeps, smem, sched, st);
+    case 3: return launch_sweep_rf_c(q, jobs_dev, work, nwork, nsweeps, smem, sched, st);
+    case 4: return launch_sweep_rf_d(q, jobs_dev, work, nwork, nsweeps, smem, sched, st);
+    case 5: return launch_sweep_rf_e(q, jobs_dev, work, nwork, nsweeps, smem, sched, st);
     default: return cudaErrorNotSupported;
     }
 }

@@ -1,6 +1,6 @@
 // Register-resident FP32 Metropolis sweep (Eq. 8, Sec. 4.2 of the paper).
 //
-// One CTA per temperature slot: NU update warps hold the local fields
+// One CTA sweeps one temperature slot at a time: NU update warps hold the local fields
 // h[x][i] of their sites in registers, one decision warp holds none.  Update
 // thread u (0 <= u < 32 NU) keeps sites i = m 32 NU + u (m = 0..E-1) for all Q
 // states, so an accepted flip (a -> b at site k) costs it two warp-uniform
@@ -22,6 +22,7 @@
 // and the same grouping of the energy sum -- so both give identical results.
 #pragma once
 #include "sweep_common.cuh"
+#include "sweep_sched.cuh"
 
 namespace plr {
 namespace rf {
@@ -103,13 +104,12 @@ constexpr int rf_min_blocks()
     return b < 1 ? 1 : (b > 4 ? 4 : b);
 }
 
+// nsweeps sweeps of one work item wk = (job, slot) by the whole CTA
 template <int Q, int E, int NU>
-__global__ void __launch_bounds__(32 * (NU + 1), rf_min_blocks<Q, E, NU>())
-    sweep_rf_kernel(const JobDev* __restrict__ jobs, const int2* __restrict__ work, int nsweeps)
+__device__ __forceinline__ void rf_item(const JobDev* __restrict__ jobs, const int2 wk, int nsweeps,
+                                        unsigned char* __restrict__ smem)
 {
     constexpr int NUT = 32 * NU;  // update threads
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int2 wk = work[blockIdx.x];
     const JobDev* jp = jobs + wk.x;
     const int t = wk.y;
     const int L = jp->L, q = jp->q, Lpad = jp->Lpad, W = jp->W, c = jp->c;
@@ -256,26 +256,64 @@ __global__ void __launch_bounds__(32 * (NU + 1), rf_min_blocks<Q, E, NU>())
     }
 }
 
+// One item per CTA (sc.n == 0), or persistent CTAs placed by a SweepSched plan.
+template <int Q, int E, int NU>
+__global__ void __launch_bounds__(32 * (NU + 1), rf_min_blocks<Q, E, NU>())
+    sweep_rf_kernel(const JobDev* __restrict__ jobs, const int2* __restrict__ work, int nsweeps, const SweepSched sc)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    if (sc.n == 0) {
+        rf_item<Q, E, NU>(jobs, work[blockIdx.x], nsweeps, smem);
+        return;
+    }
+    __shared__ int s_item;
+    bool waited = false;  // thread 0's
+    if (threadIdx.x == 0) s_item = sched_claim_home(sc);
+    __syncthreads();
+    for (;;) {
+        const int item = s_item;
+        if (item >= 0) rf_item<Q, E, NU>(jobs, work[item], nsweeps, smem);
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = sched_claim_next(sc, waited);
+        __syncthreads();
+        if (s_item < 0) break;
+    }
+}
+
 template <int Q, int E, int NU>
 cudaError_t launch_rf(const JobDev* jobs_dev, const int2* work, int nwork, int nsweeps, size_t smem,
-                      cudaStream_t st)
+                      const SweepSched* sched, cudaStream_t st)
 {
     auto k = sweep_rf_kernel<Q, E, NU>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k<<<nwork, 32 * (NU + 1), smem, st>>>(jobs_dev, work, nsweeps);
+    SweepSched sc{};
+    int grid = nwork;
+    if (sched && sched->nsm > 0 && nwork > sched->nsm) {
+        int occ = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, 32 * (NU + 1), smem);
+        if (e != cudaSuccess) return e;
+        if (occ > 0) {
+            sc = *sched;
+            sc.n = nwork;
+            sc.occ = occ < kSchedMaxOcc ? occ : kSchedMaxOcc;
+            grid = sc.nsm * sc.occ;
+            if ((e = launch_sweep_plan(jobs_dev, work, sc, st)) != cudaSuccess) return e;
+        }
+    }
+    k<<<grid, 32 * (NU + 1), smem, st>>>(jobs_dev, work, nsweeps, sc);
     return cudaGetLastError();
 }
 
 // dispatch over Q for one (E, NU) configuration
 template <int E, int NU, int QMAX>
 cudaError_t launch_rf_q(int q, const JobDev* jobs_dev, const int2* work, int nwork, int nsweeps, size_t smem,
-                        cudaStream_t st)
+                        const SweepSched* sched, cudaStream_t st)
 {
     switch (q) {
 #define PLR_RF_Q(Qv) \
     case Qv:         \
-        if constexpr (Qv <= QMAX) return launch_rf<Qv, E, NU>(jobs_dev, work, nwork, nsweeps, smem, st); \
+        if constexpr (Qv <= QMAX) return launch_rf<Qv, E, NU>(jobs_dev, work, nwork, nsweeps, smem, sched, st); \
         break;
         PLR_RF_Q(2) PLR_RF_Q(3) PLR_RF_Q(4) PLR_RF_Q(5) PLR_RF_Q(6) PLR_RF_Q(7) PLR_RF_Q(8) PLR_RF_Q(9)
         PLR_RF_Q(10) PLR_RF_Q(11) PLR_RF_Q(12) PLR_RF_Q(13) PLR_RF_Q(14) PLR_RF_Q(15) PLR_RF_Q(16)

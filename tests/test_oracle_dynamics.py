@@ -145,3 +145,77 @@ def test_exchange_acceptance_rate():
     frac = st["acc_swap"][0] / st["att_swap"][0]
     expect = 2 * p / (1 + p)
     assert abs(frac - expect) < 4 * math.sqrt(expect * (1 - expect) / n) + 1e-3, (frac, expect)
+
+
+def _one_sweep_kernel(L, q, J, c, beta, rule):
+    """Transition matrix of one sequential sweep (sites 0..L-1) over all q^L
+    states, by brute force.  rule "metropolis" (Eq. 8): propose one of the
+    other q-1 states uniformly, accept with min(1, exp(-beta dE)); rule
+    "heatbath": draw the new state of the site from exp(-beta E) over all q."""
+    import itertools
+    states = list(itertools.product(range(q), repeat=L))
+    index = {s: n for n, s in enumerate(states)}
+
+    def energy(s):
+        return -0.5 * c * sum(J[abs(i - j) % L] for i in range(L) for j in range(L) if i != j and s[i] == s[j])
+
+    E = np.array([energy(s) for s in states])
+    T = np.eye(len(states))
+    for k in range(L):
+        P = np.zeros_like(T)
+        for n, s in enumerate(states):
+            nbr = [index[s[:k] + (x,) + s[k + 1:]] for x in range(q)]
+            if rule == "metropolis":
+                for x in range(q):
+                    if x == s[k]:
+                        continue
+                    p = min(1.0, math.exp(-beta * (E[nbr[x]] - E[n]))) / (q - 1)
+                    P[n, nbr[x]] += p
+                    P[n, n] += 1.0 / (q - 1) - p
+            else:
+                w = np.exp(-beta * (E[nbr] - E[nbr].min()))
+                P[n, nbr] += w / w.sum()
+        T = T @ P
+    return T, index, E
+
+
+def test_one_sweep_transition_law():
+    """The oracle's sweep is the Metropolis chain of Eq. 8 with sequential sites
+    and a uniform proposal: from a fixed start, the end states of many
+    independent sweeps follow the brute-force one-sweep transition row (chi
+    square), the Boltzmann weight is stationary under that matrix, and the same
+    samples reject the heat-bath row (which has the same stationary law)."""
+    from scipy.stats import chi2
+    L, q, sigma, c = 4, 3, 0.5, 2
+    J = jstar(L, sigma)
+    ratios = np.array([0.15, 0.4, 1.0])
+    temps = ratios * jtot(L, sigma)
+    s0 = np.array([0, 1, 1, 2], dtype=np.uint8)
+    o = Oracle(L, q, sigma, temps, seed=4242, c=c)
+    nsamp = 20000
+    counts = np.zeros((o.R, q ** L))
+    for _ in range(nsamp):
+        o.set_spins(np.tile(s0, (o.R, 1)))
+        o.sweep(1, mode="direct")
+        s = o.spins()
+        for t in range(o.R):
+            counts[t, int(sum(int(v) * q ** (L - 1 - i) for i, v in enumerate(s[t])))] += 1
+    for t in range(o.R):
+        beta = 1.0 / temps[t]
+        T, index, E = _one_sweep_kernel(L, q, J, c, beta, "metropolis")
+        pi = np.exp(-beta * (E - E.min()))
+        pi /= pi.sum()
+        np.testing.assert_allclose(pi @ T, pi, atol=1e-13)     # global balance of one sweep
+        row = T[index[tuple(int(v) for v in s0)]]
+
+        def stat(p):
+            m = p * nsamp > 5
+            x2 = ((counts[t][m] - nsamp * p[m]) ** 2 / (nsamp * p[m])).sum()
+            return x2, int(m.sum()) - 1
+
+        x2, dof = stat(row)
+        assert chi2.sf(x2, dof) > 1e-4, (t, x2, dof)
+        Th, _, _ = _one_sweep_kernel(L, q, J, c, beta, "heatbath")
+        np.testing.assert_allclose(pi @ Th, pi, atol=1e-13)
+        x2h, dofh = stat(Th[index[tuple(int(v) for v in s0)]])
+        assert chi2.sf(x2h, dofh) < 1e-6, (t, x2h, dofh)
