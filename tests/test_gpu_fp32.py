@@ -111,8 +111,9 @@ def test_fp32_and_fp64_sample_the_same_observables(plr):
 
 
 @pytest.mark.parametrize("L,q,sigma,R", [
-    (200, 3, 0.5, 4), (256, 16, 0.3, 3), (500, 5, 0.7, 5), (1000, 16, 0.4, 3), (1024, 5, 0.4, 8),
-    (2048, 8, 0.6, 3), (1999, 2, 0.2, 4), (4096, 8, 0.2, 3), (3000, 6, 0.9, 2),
+    (65, 4, 0.5, 4), (96, 3, 0.6, 3), (200, 3, 0.5, 4), (256, 16, 0.3, 3), (500, 5, 0.7, 5), (500, 11, 0.7, 3),
+    (1000, 16, 0.4, 3), (1024, 5, 0.4, 8), (1536, 7, 0.5, 3), (2048, 8, 0.6, 3), (1999, 2, 0.2, 4),
+    (4096, 8, 0.2, 3), (4224, 3, 0.3, 2), (3000, 6, 0.9, 2),
 ])
 def test_register_path_equals_memory_path(plr, L, q, sigma, R):
     """The register-resident FP32 sweep and the shared/global-memory FP32 sweep
@@ -134,7 +135,8 @@ def test_register_path_equals_memory_path(plr, L, q, sigma, R):
     np.testing.assert_array_equal(a.stats()["acc_flip"], b.stats()["acc_flip"])
 
 
-def test_register_path_rejects_large_shapes(plr):
+@pytest.mark.parametrize("L,q", [(8192, 10), (4400, 3), (2048, 9)])
+def test_register_path_rejects_unsupported_shapes(plr, L, q):
     temps = np.linspace(1.0, 2.0, 2)
     with pytest.raises(plr.PottsError):
-        plr.Job(8192, 10, 0.5, temps, 1, precision="fp32", sweep_variant="registers")
+        plr.Job(L, q, 0.5, temps, 1, precision="fp32", sweep_variant="registers")
