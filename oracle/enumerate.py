@@ -31,16 +31,17 @@ def magnetisations(states: np.ndarray, q: int) -> np.ndarray:
 
 
 def exact_averages(L: int, q: int, J: np.ndarray, c: int, betas) -> dict:
-    """<E>, <E^2>, <M>, <M^2>, <M^4> at each beta, exactly."""
+    """<E>, <E^2>, <E^4>, <M>, <M^2>, <M^4> at each beta, exactly."""
     S = all_states(L, q)
     E = energies(S, J, c)
     M = magnetisations(S, q)
-    out = {k: [] for k in ("E", "E2", "M", "M2", "M4")}
+    out = {k: [] for k in ("E", "E2", "E4", "M", "M2", "M4")}
     for beta in betas:
         w = np.exp(-beta * (E - E.min()))  # shift for range; cancels in ratios
         Z = w.sum()
         out["E"].append((w * E).sum() / Z)
         out["E2"].append((w * E * E).sum() / Z)
+        out["E4"].append((w * E ** 4).sum() / Z)
         out["M"].append((w * M).sum() / Z)
         out["M2"].append((w * M ** 2).sum() / Z)
         out["M4"].append((w * M ** 4).sum() / Z)

@@ -67,6 +67,12 @@ class Result:
     def latency(self) -> Optional[float]:
         return None if self.finished is None else self.finished - self.arrival
 
+    def observables(self, L: int, nblocks: int = 20, skip: int = 0):
+        """<E>/L, <M>, U_E (Eq. 11) and V_M (Eq. 12) per slot with jackknife
+        errors, from the measurements after the first `skip` ones."""
+        from .analysis import observables
+        return observables(np.array(self.E[skip:]), np.array(self.M[skip:]), L, nblocks)
+
 
 class GpuEngine:
     """The library's C ABI as the service's engine."""
