@@ -39,7 +39,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="chains", choices=["chains", "precision", "batching", "serving"])
+    ap.add_argument("--workload", default="chains", choices=["chains", "precision", "batching", "serving", "paper"])
     ap.add_argument("--serve-jobs", type=int, default=32)
     ap.add_argument("--serve-sweeps", type=int, default=100)
     ap.add_argument("--no-serving", action="store_true")
@@ -78,6 +78,12 @@ def workload_specs(name, rank, precision):
         desc = {"workload": "256 ragged PT jobs (L 256-8192, q 2-10, sigma U[0.1,1], R 32/64/128, FP32, "
                             "rebuild every 100 sweeps) in one graph-captured batch; step = 1 sweep + exchange",
                 "jobs": 256}
+    elif name == "paper":
+        specs = workloads.paper_benchmark_jobs()
+        desc = {"workload": "the paper's benchmark protocol (Sec. 5.2): q=3, sigma=0.2, 400 replicas on a "
+                            "uniform temperature grid, L=512..10240, production sweeps 1e4 (L=512) down to 50 "
+                            "(L=10240) + 20% thermalisation, from random spins; plus the replica scan of Fig. 5 "
+                            "(L=1024)"}
     else:
         specs = workloads.serving_trace()[:1]
         desc = {"workload": "serving trace: Poisson(50/s) arrivals, q 3/5/8, sigma U[0.1,1], L 512-16384, "
@@ -423,6 +429,69 @@ def batching_run(plr, torch, dev, steps, warmup):
             "attempts_per_s": att / (ms / 1e3)}
 
 
+def paper_run(plr, torch, dev, seconds_per_case=2.0):
+    """The paper's benchmark (Sec. 5.2, Fig. 4) and replica scan (Fig. 5) on
+    this GPU, FP32 and FP64, against the oracle on one host core.  Each GPU
+    case runs the protocol's sweeps from random spins (cut to about
+    seconds_per_case); the oracle runs 8 of the 400 temperatures (every 50th)
+    from random spins for as many sweeps as fit in about seconds_per_case."""
+    import oracle
+    from paper_1308_5426_gb300 import workloads
+
+    def gpu_rate(s, R, precision, sweeps):
+        temps = workloads.uniform_ratios(R, 0.1, 1.0) * plr.jtot(s.L, s.sigma)
+        st = torch.cuda.Stream(device=dev)
+        j = plr.Job(s.L, s.q, s.sigma, temps, s.seed, precision=precision, stream=st.cuda_stream)
+        j.sync()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        j.sweep(1)
+        j.exchange()
+        e1.record(st)
+        e1.synchronize()
+        first = max(e0.elapsed_time(e1) / 1e3, 1e-6)
+        n = max(1, min(sweeps - 1, int(seconds_per_case / first)))
+        e0.record(st)
+        for _ in range(n):
+            j.sweep(1)
+            j.exchange()
+        e1.record(st)
+        e1.synchronize()
+        dt = e0.elapsed_time(e1) / 1e3
+        j.close()
+        return n * s.L * R / dt, n + 1
+
+    def cpu_rate(s):
+        temps = workloads.uniform_ratios(400, 0.1, 1.0)[::50] * oracle.jtot(s.L, s.sigma)
+        o = oracle.Oracle(s.L, s.q, s.sigma, temps, s.seed)
+        t0 = time.perf_counter()
+        n = 0
+        while n < s.sweeps and (n == 0 or time.perf_counter() - t0 < seconds_per_case):
+            o.step(mode="field", nthreads=1)
+            n += 1
+        dt = time.perf_counter() - t0
+        return n * s.L * len(temps) / dt, n
+
+    table = []
+    for s in workloads.paper_benchmark_jobs():
+        g32, n32 = gpu_rate(s, 400, "fp32", s.sweeps)
+        g64, n64 = gpu_rate(s, 400, "fp64", s.sweeps)
+        c1, nc = cpu_rate(s)
+        table.append({"L": s.L, "R": 400, "protocol_sweeps": s.sweeps, "gpu_fp32": g32, "gpu_fp32_sweeps": n32,
+                      "gpu_fp64": g64, "gpu_fp64_sweeps": n64, "oracle_1core": c1, "oracle_sweeps": nc,
+                      "speedup_fp32_vs_1core": g32 / c1, "speedup_fp64_vs_1core": g64 / c1})
+    s1024 = [s for s in workloads.paper_benchmark_jobs() if s.L == 1024][0]
+    c1024 = [row["oracle_1core"] for row in table if row["L"] == 1024][0]
+    scan = []
+    for R in (112, 224, 336, 448, 560):
+        g, n = gpu_rate(s1024, R, "fp32", s1024.sweeps)
+        scan.append({"L": 1024, "R": R, "gpu_fp32": g, "sweeps": n, "speedup_fp32_vs_1core": g / c1024})
+    return {"fig4_table": table, "fig5_replica_scan": scan,
+            "oracle_sample": "8 of the 400 temperatures (every 50th), one thread, FP64 local-field mode, "
+                             "from random spins"}
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -447,6 +516,21 @@ def main():
     _lib.load()
 
     clocks = ClockSampler(local)
+    if args.workload == "paper":
+        if rank != 0:
+            return 0
+        torch.cuda.synchronize(dev)
+        clocks.start()
+        r = paper_run(plr, torch, dev)
+        ck = clocks.stop()
+        tot = sum(row["gpu_fp32"] for row in r["fig4_table"]) / len(r["fig4_table"])
+        line = {"metric": "spin-flip attempts/s", "value": tot, "unit": "attempts/s", "n_gpus": 1,
+                "steps": len(r["fig4_table"]), "warmup": 0, "ms_per_step": None, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": desc,
+                "clocks": ck, "value_is": "mean over the Fig. 4 lengths of the FP32 attempts/s",
+                "detail": r, "roofline": None, "e2e": None, "cpu_baseline": None}
+        print(json.dumps(line), flush=True)
+        return 0
     if args.workload in ("batching", "serving"):
         torch.cuda.synchronize(dev)
         clocks.start()

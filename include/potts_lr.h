@@ -81,7 +81,8 @@ typedef struct {
     void* cuda_stream;   /* cudaStream_t to run on; NULL = a stream the handle creates */
     int sweep_variant;   /* FP32 mode: 0 = automatic (default), 1 = fields in shared or
                             global memory, 2 = fields in registers (EINVAL if the shape
-                            does not fit: L <= 1120, or L <= 4320 with q <= 8).  Both
+                            does not fit: L <= 1120, or L <= 4320 with q <= 8, L <= 7680
+                            with q <= 5, L <= 12480 with q <= 3, L <= 16800 with q = 2).  Both
                             variants give identical results. */
 } potts_lr_opts;
 

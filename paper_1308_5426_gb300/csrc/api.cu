@@ -391,7 +391,8 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
     j.rf = (h->precision == POTTS_LR_FP32 && o.sweep_variant != 1) ? rf_config(L, q) : 0;
     if (o.sweep_variant == 2 && !j.rf) {
         potts_lr_destroy(h);
-        return fail(POTTS_LR_EINVAL, "register-resident sweep needs FP32 and L <= 1120, or L <= 4320 with q <= 8");
+        return fail(POTTS_LR_EINVAL, "register-resident sweep needs FP32 and L <= 1120, or L <= 4320 with q <= 8 "
+                                     "(7680 with q <= 5, 12480 with q <= 3, 16800 with q = 2)");
     }
     h->dj = (JobDev*)(base + o_job);
     h->dwork = (int2*)(base + o_work);

@@ -119,10 +119,11 @@ cudaError_t launch_rebuild_policy(const JobDev* jobs_dev, const int* idx, int nj
 
 size_t sweep_smem_bytes(const JobDev& j);
 
-// Register-resident FP32 sweep (sweep_rf.cuh): configuration 1..5 =
+// Register-resident FP32 sweep (sweep_rf.cuh): configuration 1..8 =
 // (E sites per update thread, update warps) = (1, 7), (2, 7), (5, 7) for
 // L <= 224, 448, 1120; (5, 15), (9, 15) with q <= 8 for L <= 2400, 4320;
-// 0 if the shape does not fit in registers.
+// (16, 15) with q <= 5 for L <= 7680; (26, 15) with q <= 3 for L <= 12480;
+// (35, 15) with q = 2 for L <= 16800; 0 if the shape does not fit in registers.
 int rf_config(int L, int q);
 size_t rf_smem_bytes(int cfg, int q, int L, int Lpad);
 cudaError_t launch_sweep_rf(int cfg, int q, const JobDev* jobs_dev, const int2* work, int nwork, int nsweeps,
@@ -137,11 +138,20 @@ cudaError_t launch_sweep_rf_d(int q, const JobDev*, const int2*, int, int, size_
                              cudaStream_t);
 cudaError_t launch_sweep_rf_e(int q, const JobDev*, const int2*, int, int, size_t, const SweepSched*,
                              cudaStream_t);
+cudaError_t launch_sweep_rf_f(int q, const JobDev*, const int2*, int, int, size_t, const SweepSched*,
+                             cudaStream_t);
+cudaError_t launch_sweep_rf_g(int q, const JobDev*, const int2*, int, int, size_t, const SweepSched*,
+                             cudaStream_t);
+cudaError_t launch_sweep_rf_h(int q, const JobDev*, const int2*, int, int, size_t, const SweepSched*,
+                             cudaStream_t);
 size_t sweep_rf_smem_a(int q, int L, int Lpad);
 size_t sweep_rf_smem_b(int q, int L, int Lpad);
 size_t sweep_rf_smem_c(int q, int L, int Lpad);
 size_t sweep_rf_smem_d(int q, int L, int Lpad);
 size_t sweep_rf_smem_e(int q, int L, int Lpad);
+size_t sweep_rf_smem_f(int q, int L, int Lpad);
+size_t sweep_rf_smem_g(int q, int L, int Lpad);
+size_t sweep_rf_smem_h(int q, int L, int Lpad);
 size_t sweep_smem_bytes_for(int precision, int L, int Lpad, int q, int h_smem, int j_smem);
 size_t direct_smem_bytes(int L, int q);
 

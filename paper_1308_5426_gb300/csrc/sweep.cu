@@ -360,6 +360,9 @@ int rf_config(int L, int q)
     if (L <= 1120) return 3;
     if (L <= 2400 && q <= 8) return 4;
     if (L <= 4320 && q <= 8) return 5;
+    if (L <= 7680 && q <= 5) return 6;
+    if (L <= 12480 && q <= 3) return 7;
+    if (L <= 16800 && q <= 2) return 8;
     return 0;
 }
 
@@ -371,6 +374,9 @@ size_t rf_smem_bytes(int cfg, int q, int L, int Lpad)
     case 3: return sweep_rf_smem_c(q, L, Lpad);
     case 4: return sweep_rf_smem_d(q, L, Lpad);
     case 5: return sweep_rf_smem_e(q, L, Lpad);
+    case 6: return sweep_rf_smem_f(q, L, Lpad);
+    case 7: return sweep_rf_smem_g(q, L, Lpad);
+    case 8: return sweep_rf_smem_h(q, L, Lpad);
     default: return 0;
     }
 }
@@ -385,6 +391,9 @@ cudaError_t launch_sweep_rf(int cfg, int q, const JobDev* jobs_dev, const int2* 
     case 3: return launch_sweep_rf_c(q, jobs_dev, work, nwork, nsweeps, smem, sched, st);
     case 4: return launch_sweep_rf_d(q, jobs_dev, work, nwork, nsweeps, smem, sched, st);
     case 5: return launch_sweep_rf_e(q, jobs_dev, work, nwork, nsweeps, smem, sched, st);
+    case 6: return launch_sweep_rf_f(q, jobs_dev, work, nwork, nsweeps, smem, sched, st);
+    case 7: return launch_sweep_rf_g(q, jobs_dev, work, nwork, nsweeps, smem, sched, st);
+    case 8: return launch_sweep_rf_h(q, jobs_dev, work, nwork, nsweeps, smem, sched, st);
     default: return cudaErrorNotSupported;
     }
 }

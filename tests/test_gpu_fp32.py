@@ -113,7 +113,8 @@ def test_fp32_and_fp64_sample_the_same_observables(plr):
 @pytest.mark.parametrize("L,q,sigma,R", [
     (65, 4, 0.5, 4), (96, 3, 0.6, 3), (200, 3, 0.5, 4), (256, 16, 0.3, 3), (500, 5, 0.7, 5), (500, 11, 0.7, 3),
     (1000, 16, 0.4, 3), (1024, 5, 0.4, 8), (1536, 7, 0.5, 3), (2048, 8, 0.6, 3), (1999, 2, 0.2, 4),
-    (4096, 8, 0.2, 3), (4224, 3, 0.3, 2), (3000, 6, 0.9, 2),
+    (4096, 8, 0.2, 3), (4224, 3, 0.3, 2), (3000, 6, 0.9, 2), (6000, 5, 0.4, 2), (10000, 3, 0.2, 2),
+    (16000, 2, 0.6, 2),
 ])
 def test_register_path_equals_memory_path(plr, L, q, sigma, R):
     """The register-resident FP32 sweep and the shared/global-memory FP32 sweep
@@ -135,7 +136,7 @@ def test_register_path_equals_memory_path(plr, L, q, sigma, R):
     np.testing.assert_array_equal(a.stats()["acc_flip"], b.stats()["acc_flip"])
 
 
-@pytest.mark.parametrize("L,q", [(8192, 10), (4400, 3), (2048, 9)])
+@pytest.mark.parametrize("L,q", [(8192, 10), (4400, 6), (2048, 9), (8000, 4), (13000, 3), (17000, 2)])
 def test_register_path_rejects_unsupported_shapes(plr, L, q):
     temps = np.linspace(1.0, 2.0, 2)
     with pytest.raises(plr.PottsError):
