@@ -79,11 +79,12 @@ typedef struct {
                             rebuilds (default 100; 0 = only on explicit request) */
     int pair_factor;     /* c in Eq. 2: 2 (default) or 1 */
     void* cuda_stream;   /* cudaStream_t to run on; NULL = a stream the handle creates */
-    int sweep_variant;   /* FP32 mode: 0 = automatic (default), 1 = fields in shared or
+    int sweep_variant;   /* 0 = automatic (default); FP32 mode: 1 = fields in shared or
                             global memory, 2 = fields in registers (EINVAL if the shape
                             does not fit: L <= 1120, or L <= 4320 with q <= 8, L <= 7680
-                            with q <= 5, L <= 12480 with q <= 3, L <= 16800 with q = 2).  Both
-                            variants give identical results. */
+                            with q <= 5, L <= 12480 with q <= 3, L <= 16800 with q = 2);
+                            either mode: 3 = fields in global memory even where they fit
+                            in shared memory.  All variants give identical results. */
 } potts_lr_opts;
 
 /* Fill *opts with the defaults above. */

@@ -47,7 +47,9 @@ class Job:
     temps: absolute temperatures, ascending (slot order); precision "fp64" or
     "fp32"; recompute_every: FP32 tensor-core field rebuild interval K;
     pair_factor: c of Eq. 2; stream: optional cudaStream_t handle as an int
-    (e.g. torch.cuda.current_stream().cuda_stream).
+    (e.g. torch.cuda.current_stream().cuda_stream); sweep_variant: "auto",
+    "memory" or "registers" (FP32 field residency), "global" (fields in global
+    memory even where they fit in shared memory) -- all give identical results.
     """
 
     def __init__(self, L, q, sigma, temps, seed, precision="fp64", recompute_every=100, pair_factor=2,
@@ -64,7 +66,7 @@ class Job:
         o.recompute_every = int(recompute_every)
         o.pair_factor = int(pair_factor)
         o.cuda_stream = ctypes.c_void_p(int(stream)) if stream else None
-        o.sweep_variant = {"auto": 0, "memory": 1, "registers": 2}[sweep_variant]
+        o.sweep_variant = {"auto": 0, "memory": 1, "registers": 2, "global": 3}[sweep_variant]
         h = ctypes.c_void_p()
         _lib.check(lib.potts_lr_create(self.L, self.q, self.sigma, _lib._ptr(self.temps), self.R,
                                        ctypes.c_uint64(self.seed), ctypes.byref(o), ctypes.byref(h)))

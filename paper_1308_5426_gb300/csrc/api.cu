@@ -129,7 +129,8 @@ int check_opts(const potts_lr_opts* o)
         return fail(POTTS_LR_EINVAL, "precision must be POTTS_LR_FP64 or POTTS_LR_FP32");
     if (o->pair_factor != 1 && o->pair_factor != 2) return fail(POTTS_LR_EINVAL, "pair_factor must be 1 or 2");
     if (o->recompute_every < 0) return fail(POTTS_LR_EINVAL, "recompute_every must be >= 0");
-    if (o->sweep_variant < 0 || o->sweep_variant > 2) return fail(POTTS_LR_EINVAL, "sweep_variant must be 0, 1 or 2");
+    if (o->sweep_variant < 0 || o->sweep_variant > 3)
+        return fail(POTTS_LR_EINVAL, "sweep_variant must be 0, 1, 2 or 3");
     return POTTS_LR_OK;
 }
 
@@ -380,7 +381,7 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
     // memory when they fit, else fields first, else the table, else neither
     {
         const int opts_hs[4] = {1, 1, 0, 0}, opts_js[4] = {1, 0, 1, 0};
-        for (int v = 0; v < 4; ++v) {
+        for (int v = o.sweep_variant == 3 ? 2 : 0; v < 4; ++v) {  // variant 3: fields in global memory
             if (sweep_smem_bytes_for(h->precision, L, h->Lpad, q, opts_hs[v], opts_js[v]) <= kSmemBudget) {
                 j.h_smem = opts_hs[v];
                 j.j_smem = opts_js[v];
@@ -388,7 +389,7 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
             }
         }
     }
-    j.rf = (h->precision == POTTS_LR_FP32 && o.sweep_variant != 1) ? rf_config(L, q) : 0;
+    j.rf = (h->precision == POTTS_LR_FP32 && (o.sweep_variant == 0 || o.sweep_variant == 2)) ? rf_config(L, q) : 0;
     if (o.sweep_variant == 2 && !j.rf) {
         potts_lr_destroy(h);
         return fail(POTTS_LR_EINVAL, "register-resident sweep needs FP32 and L <= 1120, or L <= 4320 with q <= 8 "

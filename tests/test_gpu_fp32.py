@@ -141,3 +141,24 @@ def test_register_path_rejects_unsupported_shapes(plr, L, q):
     temps = np.linspace(1.0, 2.0, 2)
     with pytest.raises(plr.PottsError):
         plr.Job(L, q, 0.5, temps, 1, precision="fp32", sweep_variant="registers")
+
+
+@pytest.mark.parametrize("precision,L,q,sigma,R", [
+    ("fp32", 2048, 5, 0.4, 3), ("fp32", 700, 11, 0.6, 3), ("fp32", 1000, 3, 0.3, 4),
+    ("fp64", 1024, 5, 0.4, 3), ("fp64", 333, 9, 0.7, 3),
+])
+def test_shared_and_global_field_residency_agree(plr, precision, L, q, sigma, R):
+    """Fields in shared memory and in global memory (and, in FP32 mode, in
+    registers) run the same arithmetic: identical spins, fields, energies."""
+    temps = workloads.geometric_ratios(R, 0.05, 1.0) * oracle.jtot(L, sigma)
+    variants = ["memory", "global"] + (["registers"] if precision == "fp32" and q <= 8 else [])
+    jobs = [plr.Job(L, q, sigma, temps, 17, precision=precision, recompute_every=6, sweep_variant=v)
+            for v in variants]
+    for _ in range(12):
+        for j in jobs:
+            j.sweep(1)
+            j.exchange()
+    for j in jobs[1:]:
+        np.testing.assert_array_equal(jobs[0].spins(), j.spins())
+        np.testing.assert_array_equal(jobs[0].fields(), j.fields())
+        np.testing.assert_array_equal(jobs[0].running_energy(), j.running_energy())
