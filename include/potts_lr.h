@@ -84,7 +84,11 @@ typedef struct {
                             does not fit: L <= 1120, or L <= 4320 with q <= 8, L <= 7680
                             with q <= 5, L <= 12480 with q <= 3, L <= 16800 with q = 2);
                             either mode: 3 = fields in global memory even where they fit
-                            in shared memory.  All variants give identical results. */
+                            in shared memory; FP32 mode: 16 + c (c = 1..8) = register
+                            configuration c (E sites per update thread x update warps:
+                            1x7, 2x7, 5x7, 5x15, 9x15, 16x15, 26x15, 35x15; q at most
+                            16, 16, 16, 8, 8, 5, 3, 2; EINVAL if L > 32 x E x warps or q
+                            too large).  All variants give identical results. */
 } potts_lr_opts;
 
 /* Fill *opts with the defaults above. */

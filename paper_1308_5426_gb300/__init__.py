@@ -41,6 +41,19 @@ def probe(what: str) -> float:
     return v.value
 
 
+SWEEP_VARIANTS = ("auto", "memory", "registers", "global") + tuple("registers%d" % c for c in range(1, 9))
+
+
+def sweep_variant_code(name):
+    """potts_lr_opts.sweep_variant for a variant name: "auto", "memory",
+    "registers", "global" or "registers<c>" (register configuration c = 1..8)."""
+    if name in ("auto", "memory", "registers", "global"):
+        return {"auto": 0, "memory": 1, "registers": 2, "global": 3}[name]
+    if isinstance(name, str) and name.startswith("registers") and name[9:].isdigit() and 1 <= int(name[9:]) <= 8:
+        return 16 + int(name[9:])
+    raise ValueError("unknown sweep variant %r" % (name,))
+
+
 class Job:
     """One PT job on the GPU (potts_lr_create).
 
@@ -49,7 +62,8 @@ class Job:
     pair_factor: c of Eq. 2; stream: optional cudaStream_t handle as an int
     (e.g. torch.cuda.current_stream().cuda_stream); sweep_variant: "auto",
     "memory" or "registers" (FP32 field residency), "global" (fields in global
-    memory even where they fit in shared memory) -- all give identical results.
+    memory even where they fit in shared memory), "registers<c>" (register
+    configuration c) -- all give identical results (see tune.py for a tuner).
     """
 
     def __init__(self, L, q, sigma, temps, seed, precision="fp64", recompute_every=100, pair_factor=2,
@@ -66,7 +80,7 @@ class Job:
         o.recompute_every = int(recompute_every)
         o.pair_factor = int(pair_factor)
         o.cuda_stream = ctypes.c_void_p(int(stream)) if stream else None
-        o.sweep_variant = {"auto": 0, "memory": 1, "registers": 2, "global": 3}[sweep_variant]
+        o.sweep_variant = sweep_variant_code(sweep_variant)
         h = ctypes.c_void_p()
         _lib.check(lib.potts_lr_create(self.L, self.q, self.sigma, _lib._ptr(self.temps), self.R,
                                        ctypes.c_uint64(self.seed), ctypes.byref(o), ctypes.byref(h)))

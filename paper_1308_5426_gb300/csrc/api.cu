@@ -129,8 +129,8 @@ int check_opts(const potts_lr_opts* o)
         return fail(POTTS_LR_EINVAL, "precision must be POTTS_LR_FP64 or POTTS_LR_FP32");
     if (o->pair_factor != 1 && o->pair_factor != 2) return fail(POTTS_LR_EINVAL, "pair_factor must be 1 or 2");
     if (o->recompute_every < 0) return fail(POTTS_LR_EINVAL, "recompute_every must be >= 0");
-    if (o->sweep_variant < 0 || o->sweep_variant > 3)
-        return fail(POTTS_LR_EINVAL, "sweep_variant must be 0, 1, 2 or 3");
+    if (o->sweep_variant < 0 || (o->sweep_variant > 3 && (o->sweep_variant < 17 || o->sweep_variant > 24)))
+        return fail(POTTS_LR_EINVAL, "sweep_variant must be 0, 1, 2, 3 or 17..24");
     return POTTS_LR_OK;
 }
 
@@ -390,6 +390,14 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
         }
     }
     j.rf = (h->precision == POTTS_LR_FP32 && (o.sweep_variant == 0 || o.sweep_variant == 2)) ? rf_config(L, q) : 0;
+    if (o.sweep_variant >= 17) {  // one register configuration, chosen by the caller (a tuner)
+        const int cfg = o.sweep_variant - 16;
+        if (h->precision != POTTS_LR_FP32 || !rf_fits(cfg, L, q)) {
+            potts_lr_destroy(h);
+            return fail(POTTS_LR_EINVAL, "register configuration %d does not hold L = %d, q = %d in FP32", cfg, L, q);
+        }
+        j.rf = cfg;
+    }
     if (o.sweep_variant == 2 && !j.rf) {
         potts_lr_destroy(h);
         return fail(POTTS_LR_EINVAL, "register-resident sweep needs FP32 and L <= 1120, or L <= 4320 with q <= 8 "

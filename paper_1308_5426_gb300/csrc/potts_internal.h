@@ -125,6 +125,7 @@ size_t sweep_smem_bytes(const JobDev& j);
 // (16, 15) with q <= 5 for L <= 7680; (26, 15) with q <= 3 for L <= 12480;
 // (35, 15) with q = 2 for L <= 16800; 0 if the shape does not fit in registers.
 int rf_config(int L, int q);
+bool rf_fits(int cfg, int L, int q);  // configuration cfg (1..8) holds L sites of q states
 size_t rf_smem_bytes(int cfg, int q, int L, int Lpad);
 cudaError_t launch_sweep_rf(int cfg, int q, const JobDev* jobs_dev, const int2* work, int nwork, int nsweeps,
                             size_t smem, const SweepSched* sched, cudaStream_t st);

@@ -353,16 +353,18 @@ cudaError_t launch_sweep(const JobDev* jobs_dev, const int2* work, int nwork, in
     }
 }
 
+namespace {
+// capacity of each register configuration: largest L (E x 32 x update warps) and q
+constexpr int kRfMaxL[9] = {0, 224, 448, 1120, 2400, 4320, 7680, 12480, 16800};
+constexpr int kRfMaxQ[9] = {0, 16, 16, 16, 8, 8, 5, 3, 2};
+}  // namespace
+
+bool rf_fits(int cfg, int L, int q) { return cfg >= 1 && cfg <= 8 && L <= kRfMaxL[cfg] && q <= kRfMaxQ[cfg]; }
+
 int rf_config(int L, int q)
 {
-    if (L <= 224) return 1;
-    if (L <= 448) return 2;
-    if (L <= 1120) return 3;
-    if (L <= 2400 && q <= 8) return 4;
-    if (L <= 4320 && q <= 8) return 5;
-    if (L <= 7680 && q <= 5) return 6;
-    if (L <= 12480 && q <= 3) return 7;
-    if (L <= 16800 && q <= 2) return 8;
+    for (int cfg = 1; cfg <= 8; ++cfg)  // the fewest sites per thread that hold the chain
+        if (rf_fits(cfg, L, q)) return cfg;
     return 0;
 }
 

@@ -77,14 +77,18 @@ class Result:
 class GpuEngine:
     """The library's C ABI as the service's engine."""
 
-    def __init__(self, stream=None):
+    def __init__(self, stream=None, variants=None):
+        """variants: optional {(L, q, precision): sweep variant name}, e.g.
+        from tune.tune() run over the shapes a trace will bring."""
         import paper_1308_5426_gb300 as plr
         self.plr = plr
         self.stream = stream
+        self.variants = dict(variants or {})
 
     def create(self, req: Request):
+        v = self.variants.get((req.L, req.q, req.precision), "auto")
         return self.plr.Job(req.L, req.q, req.sigma, req.temps, req.seed, precision=req.precision,
-                            recompute_every=req.recompute_every, stream=self.stream)
+                            recompute_every=req.recompute_every, stream=self.stream, sweep_variant=v)
 
     def batch(self, jobs):
         return self.plr.Batch(jobs, stream=self.stream)
