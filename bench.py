@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--precision", default=None, choices=[None, "fp64", "fp32"])
     ap.add_argument("--no-fp32-compare", action="store_true")
+    ap.add_argument("--no-direct-compare", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
 
@@ -250,14 +251,14 @@ def run_reference(args, specs, desc, rank, world):
 
 
 # ----------------------------------------------------------------- GPU arm
-def make_jobs(plr, specs, stream):
+def make_jobs(plr, specs, stream, variant="auto"):
     return [plr.Job(s.L, s.q, s.sigma, s.ratios * plr.jtot(s.L, s.sigma), s.seed, precision=s.precision,
-                    stream=stream) for s in specs]
+                    stream=stream, sweep_variant=variant) for s in specs]
 
 
-def timed_device(plr, torch, specs, steps, warmup, dev, with_events=True):
+def timed_device(plr, torch, specs, steps, warmup, dev, with_events=True, variant="auto"):
     st = torch.cuda.Stream(device=dev)
-    jobs = make_jobs(plr, specs, st.cuda_stream)
+    jobs = make_jobs(plr, specs, st.cuda_stream, variant)
     batch = plr.Batch(jobs, stream=st.cuda_stream)
     nslots = batch.nslots
     Eb = torch.empty(nslots, dtype=torch.float64, device=dev)
@@ -588,6 +589,15 @@ def main():
         r32 = timed_device(plr, torch, specs32, max(3, args.steps // 3), args.warmup, dev, with_events=False)
         extra["fp32_same_workload"] = {"value": world * r32["steps"] * r32["att_step"] / (r32["step_ms"] / 1e3),
                                        "unit": "attempts/s", "acceptance": r32["acceptance"]}
+    if args.workload == "chains" and not args.no_direct_compare and prec == "fp64":
+        # the paper's scheme on the same workload: every proposal sums its O(L)
+        # interaction (no fields), FP64
+        rd = timed_device(plr, torch, specs, max(3, args.steps // 10), args.warmup, dev, with_events=False,
+                          variant="direct")
+        extra["fp64_direct_same_workload"] = {
+            "value": world * rd["steps"] * rd["att_step"] / (rd["step_ms"] / 1e3), "unit": "attempts/s",
+            "acceptance": rd["acceptance"],
+            "kernel": "sweep_direct_kernel: the paper's O(L)-per-attempt sum, no local fields (Sec. 4.2)"}
 
     if args.workload == "chains" and not args.no_serving and world == 1:
         extra["serving"] = serving_run(plr, torch, dev, args.serve_jobs, args.serve_sweeps)

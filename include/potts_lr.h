@@ -84,7 +84,10 @@ typedef struct {
                             does not fit: L <= 1120, or L <= 4320 with q <= 8, L <= 7680
                             with q <= 5, L <= 12480 with q <= 3, L <= 16800 with q = 2);
                             either mode: 3 = fields in global memory even where they fit
-                            in shared memory; FP32 mode: 16 + c (c = 1..8) = register
+                            in shared memory; FP64 mode: 4 = the direct sweep of the
+                            paper (Sec. 4.2: every proposal sums its O(L) interaction,
+                            no fields; same decisions up to rounding of the sum; L up to
+                            about 24000); FP32 mode: 16 + c (c = 1..8) = register
                             configuration c (E sites per update thread x update warps:
                             1x7, 2x7, 5x7, 5x15, 9x15, 16x15, 26x15, 35x15; q at most
                             16, 16, 16, 8, 8, 5, 3, 2; EINVAL if L > 32 x E x warps or q

@@ -41,14 +41,15 @@ def probe(what: str) -> float:
     return v.value
 
 
-SWEEP_VARIANTS = ("auto", "memory", "registers", "global") + tuple("registers%d" % c for c in range(1, 9))
+SWEEP_VARIANTS = ("auto", "memory", "registers", "global", "direct") + tuple("registers%d" % c for c in range(1, 9))
 
 
 def sweep_variant_code(name):
     """potts_lr_opts.sweep_variant for a variant name: "auto", "memory",
-    "registers", "global" or "registers<c>" (register configuration c = 1..8)."""
-    if name in ("auto", "memory", "registers", "global"):
-        return {"auto": 0, "memory": 1, "registers": 2, "global": 3}[name]
+    "registers", "global", "direct" (the paper's O(L)-per-attempt sweep, FP64)
+    or "registers<c>" (register configuration c = 1..8)."""
+    if name in ("auto", "memory", "registers", "global", "direct"):
+        return {"auto": 0, "memory": 1, "registers": 2, "global": 3, "direct": 4}[name]
     if isinstance(name, str) and name.startswith("registers") and name[9:].isdigit() and 1 <= int(name[9:]) <= 8:
         return 16 + int(name[9:])
     raise ValueError("unknown sweep variant %r" % (name,))

@@ -71,6 +71,7 @@ struct potts_lr {
     int4* dtiles;                 // FP32: tensor-core rebuild tiles of this job (job index 0)
     int ntiles;
     SweepSched sched;             // placement of the R slots on the SMs
+    bool direct;                  // sweeps by the direct O(L) sum: fields are rebuilt on demand
 };
 
 struct potts_lr_batch {
@@ -129,8 +130,10 @@ int check_opts(const potts_lr_opts* o)
         return fail(POTTS_LR_EINVAL, "precision must be POTTS_LR_FP64 or POTTS_LR_FP32");
     if (o->pair_factor != 1 && o->pair_factor != 2) return fail(POTTS_LR_EINVAL, "pair_factor must be 1 or 2");
     if (o->recompute_every < 0) return fail(POTTS_LR_EINVAL, "recompute_every must be >= 0");
-    if (o->sweep_variant < 0 || (o->sweep_variant > 3 && (o->sweep_variant < 17 || o->sweep_variant > 24)))
-        return fail(POTTS_LR_EINVAL, "sweep_variant must be 0, 1, 2, 3 or 17..24");
+    if (o->sweep_variant < 0 || (o->sweep_variant > 4 && (o->sweep_variant < 17 || o->sweep_variant > 24)))
+        return fail(POTTS_LR_EINVAL, "sweep_variant must be 0..4 or 17..24");
+    if (o->sweep_variant == 4 && o->precision != POTTS_LR_FP64)
+        return fail(POTTS_LR_EINVAL, "the direct sweep (sweep_variant 4) runs in FP64 mode only");
     return POTTS_LR_OK;
 }
 
@@ -153,8 +156,11 @@ cudaError_t rebuild_launch(const potts_lr_t* h, const JobDev* job_dev, int cond,
 
 // the sweep kernel variant of a job: register-resident (per configuration and
 // q) or memory-resident (per precision and shared-memory residency)
+constexpr int kDirectKey = 99;
+
 int variant_key(const potts_lr_t* h)
 {
+    if (h->direct) return kDirectKey;
     return h->hj.rf ? 100 + h->hj.rf * 32 + h->q : h->precision * 4 + h->hj.h_smem * 2 + h->hj.j_smem;
 }
 
@@ -163,7 +169,16 @@ cudaError_t launch_variant(int key, const JobDev* jobs, const int2* work, int nw
 {
     if (key >= 100)
         return launch_sweep_rf((key - 100) / 32, (key - 100) % 32, jobs, work, nwork, nsweeps, smem, sched, st);
+    if (key == kDirectKey) return launch_sweep_direct(jobs, work, nwork, nsweeps, smem, st);
     return launch_sweep(jobs, work, nwork, nsweeps, key >> 2, (key >> 1) & 1, key & 1, smem, sched, st);
+}
+
+// the direct sweep keeps no fields: rebuild them (FP64, exact) before they are read
+int fresh_fields(potts_lr_t* h)
+{
+    if (!h->direct) return POTTS_LR_OK;
+    cudaError_t e = launch_fields_direct(h->dj, h->L, h->R, 0, 0, h->direct_smem, h->stream);
+    return e == cudaSuccess ? POTTS_LR_OK : cuda_fail(e, "field rebuild");
 }
 
 int rebuild(potts_lr_t* h)
@@ -406,6 +421,14 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
     h->dj = (JobDev*)(base + o_job);
     h->dwork = (int2*)(base + o_work);
     h->sweep_smem = j.rf ? rf_smem_bytes(j.rf, q, L, h->Lpad) : sweep_smem_bytes(j);
+    if (o.sweep_variant == 4) {
+        h->direct = true;
+        h->sweep_smem = direct_sweep_smem_bytes(L, h->Lpad);
+        if (h->sweep_smem > kSmemBudget) {
+            potts_lr_destroy(h);
+            return fail(POTTS_LR_EINVAL, "the direct sweep keeps J* and the spins in shared memory: L too large");
+        }
+    }
     h->measure_smem = measure_smem_bytes(L, h->W);
     h->direct_smem = direct_smem_bytes(L, q);
 
@@ -508,6 +531,7 @@ int potts_lr_fields_recompute(potts_lr_t* h)
 int potts_lr_fields_error(potts_lr_t* h, double* max_err)
 {
     if (!h || !max_err) return fail(POTTS_LR_EINVAL, "NULL argument");
+    if (int rc = fresh_fields(h)) return rc;
     PLR_CUDA(cudaMemsetAsync(h->hj.err_bits, 0, 8, h->stream));
     cudaError_t e = launch_fields_direct(h->dj, h->L, h->R, 1, 0, h->direct_smem, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "fields check");
@@ -550,6 +574,7 @@ int potts_lr_get_state(potts_lr_t* h, void* buf, size_t* len)
         return POTTS_LR_OK;
     }
     if (*len < need) return fail(POTTS_LR_ESTATE, "checkpoint buffer too small (%zu < %zu)", *len, need);
+    if (int rc = fresh_fields(h)) return rc;
     StateHeader hd;
     std::memset(&hd, 0, sizeof(hd));
     hd.magic = kStateMagic;
@@ -652,6 +677,7 @@ int potts_lr_get_spins(potts_lr_t* h, uint8_t* out)
 int potts_lr_get_fields(potts_lr_t* h, double* out)
 {
     if (!h || !out) return fail(POTTS_LR_EINVAL, "NULL argument");
+    if (int rc = fresh_fields(h)) return rc;
     const size_t per = (size_t)h->q * h->Lpad;
     std::vector<char> raw((size_t)h->R * per * h->wsize);
     std::vector<int> map(h->R);

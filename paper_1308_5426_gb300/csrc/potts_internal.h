@@ -119,6 +119,12 @@ cudaError_t launch_rebuild_policy(const JobDev* jobs_dev, const int* idx, int nj
 
 size_t sweep_smem_bytes(const JobDev& j);
 
+// Direct sweep (sweep_direct.cu): the paper's O(L)-per-attempt scheme, FP64,
+// no fields; one CTA per work item.
+size_t direct_sweep_smem_bytes(int L, int Lpad);
+cudaError_t launch_sweep_direct(const JobDev* jobs_dev, const int2* work, int nwork, int nsweeps, size_t smem,
+                                cudaStream_t st);
+
 // Register-resident FP32 sweep (sweep_rf.cuh): configuration 1..8 =
 // (E sites per update thread, update warps) = (1, 7), (2, 7), (5, 7) for
 // L <= 224, 448, 1120; (5, 15), (9, 15) with q <= 8 for L <= 2400, 4320;

@@ -187,3 +187,27 @@ def test_zero_and_infinite_temperature_limits(plr):
     np.testing.assert_array_equal(cold.spins(), oc.spins())
     E, _ = cold.measure()
     np.testing.assert_allclose(E, oc.energy(), rtol=1e-10)
+
+
+@pytest.mark.parametrize("L,q,sigma,R,c,seed,steps", [
+    (64, 3, 0.5, 16, 2, 1, 300),   # the small parity job
+    (257, 4, 0.15, 6, 1, 6, 40),   # ragged tail, pair-once
+    (33, 16, 0.9, 2, 2, 5, 60),    # largest q
+    (1024, 5, 0.4, 8, 2, 3, 8),    # the chain shape
+])
+def test_parity_direct_sweep(plr, L, q, sigma, R, c, seed, steps):
+    """The direct sweep (the paper's scheme: every proposal sums its O(L)
+    interaction, no fields) follows the oracle's direct mode bit for bit;
+    fields read back from such a job are rebuilt exactly."""
+    temps = workloads.geometric_ratios(R, 0.05, 1.0) * oracle.jtot(L, sigma)
+    g = plr.Job(L, q, sigma, temps, seed, precision="fp64", pair_factor=c, sweep_variant="direct")
+    o = oracle.Oracle(L, q, sigma, temps, seed, c=c)
+    for _ in range(steps):
+        g.sweep(1)
+        g.exchange()
+        o.sweep(1, mode="direct")
+        o.exchange()
+    _compare(g, o, "direct L=%d" % L)
+    np.testing.assert_allclose(g.fields(), o.fields(), rtol=0, atol=1e-12 * oracle.jtot(L, sigma))
+    with pytest.raises(plr.PottsError):
+        plr.Job(L, q, sigma, temps, seed, precision="fp32", sweep_variant="direct")

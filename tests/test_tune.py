@@ -9,12 +9,12 @@ from paper_1308_5426_gb300.tune import candidates
 
 
 def test_variant_codes():
-    assert [sweep_variant_code(v) for v in ("auto", "memory", "registers", "global")] == [0, 1, 2, 3]
+    assert [sweep_variant_code(v) for v in ("auto", "memory", "registers", "global", "direct")] == [0, 1, 2, 3, 4]
     assert [sweep_variant_code("registers%d" % c) for c in range(1, 9)] == list(range(17, 25))
     for bad in ("registers0", "registers9", "fast", 5):
         with pytest.raises(ValueError):
             sweep_variant_code(bad)
-    assert len(SWEEP_VARIANTS) == 12
+    assert len(SWEEP_VARIANTS) == 13
 
 
 def test_candidates():
