@@ -251,14 +251,14 @@ def run_reference(args, specs, desc, rank, world):
 
 
 # ----------------------------------------------------------------- GPU arm
-def make_jobs(plr, specs, stream, variant="auto"):
+def make_jobs(plr, specs, stream, variant="auto", site_order="sequential"):
     return [plr.Job(s.L, s.q, s.sigma, s.ratios * plr.jtot(s.L, s.sigma), s.seed, precision=s.precision,
-                    stream=stream, sweep_variant=variant) for s in specs]
+                    stream=stream, sweep_variant=variant, site_order=site_order) for s in specs]
 
 
-def timed_device(plr, torch, specs, steps, warmup, dev, with_events=True, variant="auto"):
+def timed_device(plr, torch, specs, steps, warmup, dev, with_events=True, variant="auto", site_order="sequential"):
     st = torch.cuda.Stream(device=dev)
-    jobs = make_jobs(plr, specs, st.cuda_stream, variant)
+    jobs = make_jobs(plr, specs, st.cuda_stream, variant, site_order)
     batch = plr.Batch(jobs, stream=st.cuda_stream)
     nslots = batch.nslots
     Eb = torch.empty(nslots, dtype=torch.float64, device=dev)
@@ -598,6 +598,12 @@ def main():
             "value": world * rd["steps"] * rd["att_step"] / (rd["step_ms"] / 1e3), "unit": "attempts/s",
             "acceptance": rd["acceptance"],
             "kernel": "sweep_direct_kernel: the paper's O(L)-per-attempt sum, no local fields (Sec. 4.2)"}
+        rr = timed_device(plr, torch, specs, max(3, args.steps // 10), args.warmup, dev, with_events=False,
+                          site_order="random")
+        extra["fp64_random_sites_same_workload"] = {
+            "value": world * rr["steps"] * rr["att_step"] / (rr["step_ms"] / 1e3), "unit": "attempts/s",
+            "acceptance": rr["acceptance"],
+            "kernel": "sweep_direct_kernel with random site order (attempts at Philox-drawn sites)"}
 
     if args.workload == "chains" and not args.no_serving and world == 1:
         extra["serving"] = serving_run(plr, torch, dev, args.serve_jobs, args.serve_sweeps)

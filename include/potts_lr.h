@@ -92,6 +92,10 @@ typedef struct {
                             1x7, 2x7, 5x7, 5x15, 9x15, 16x15, 26x15, 35x15; q at most
                             16, 16, 16, 8, 8, 5, 3, 2; EINVAL if L > 32 x E x warps or q
                             too large).  All variants give identical results. */
+    int site_order;      /* 0 = sites 0..L-1 in order (default); 1 = random sites: attempt
+                            m of a sweep at site floor(x3 L / 2^32) of Philox counter
+                            (m, slot, sweep, 3) -- the other reading of Sec. 4.2; runs
+                            on the direct sweep (FP64, sweep_variant 0 or 4, else EINVAL) */
 } potts_lr_opts;
 
 /* Fill *opts with the defaults above. */

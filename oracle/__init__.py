@@ -47,6 +47,7 @@ def _load():
     lib.oracle_get_running_energy.argtypes = [P, P]
     lib.oracle_get_fields.argtypes = [P, P]
     lib.oracle_set_counters.argtypes = [P, ctypes.c_uint32, ctypes.c_uint32]
+    lib.oracle_set_random_sites.argtypes = [P, ctypes.c_int]
     lib.oracle_get_counters.argtypes = [P, P, P]
     lib.oracle_get_stats.argtypes = [P] * 8
     lib.oracle_philox.argtypes = [P, P, P]
@@ -71,9 +72,11 @@ class Oracle:
     c: pair factor of Eq. 2 (2 = ordered i != j double sum, 1 = each pair once).
     fields: keep incremental local fields (needed for mode="field").
     J: optional J* table (defaults to oracle.jstar(L, sigma)).
+    site_order: "sequential" (sites 0..L-1 in order) or "random" (attempt m of
+    a sweep at site floor(x3 L / 2^32) of Philox counter (m, t, n, 3)).
     """
 
-    def __init__(self, L, q, sigma, temps, seed, c=2, fields=True, J=None):
+    def __init__(self, L, q, sigma, temps, seed, c=2, fields=True, J=None, site_order="sequential"):
         lib = _load()
         self.L, self.q, self.c = int(L), int(q), int(c)
         self.sigma = float(sigma)
@@ -90,6 +93,9 @@ class Oracle:
                                     int(self._fields))
         if not self._h:
             raise ValueError("oracle_create rejected its arguments")
+        if site_order not in ("sequential", "random"):
+            raise ValueError("site_order must be 'sequential' or 'random'")
+        lib.oracle_set_random_sites(self._h, int(site_order == "random"))
 
     def __del__(self):
         h = getattr(self, "_h", None)

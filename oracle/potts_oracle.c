@@ -21,7 +21,9 @@
  *   - J*(0) = 0 (self-interaction excluded, i != j);
  *   - Metropolis (Eq. 8): sites k = 0..L-1 in order, one proposal per site,
  *     proposal uniform over the other q-1 states, accept iff dE <= 0 or
- *     u < exp(-beta dE);
+ *     u < exp(-beta dE); or, in random-site order (the other reading of
+ *     Sec. 4.2), L attempts m = 0..L-1 per sweep, attempt m at a site drawn
+ *     uniformly, k_m = floor(x3 * L / 2^32), then the same proposal and rule;
  *   - replica exchange (Eq. 9, Sec. 4.2): stage 0 pairs (t, t+1) with t even,
  *     stage 1 with t odd, accept iff D >= 0 or u < exp(D),
  *     D = (beta_t - beta_{t+1}) (E_t - E_{t+1}); configurations move between
@@ -30,6 +32,7 @@
  *     key (seed_lo, seed_hi) and counter
  *         init:       (i, t, 0, 0)
  *         Metropolis: (k, t, n, 1)   n = absolute sweep index
+ *         Metropolis, random-site order: (m, t, n, 3)
  *         exchange:   (t, stage, m, 2)   m = absolute exchange index
  *     init spin = floor(x0 * q / 2^32);
  *     proposal b = (a + 1 + floor(x0 * (q-1) / 2^32)) mod q;
@@ -49,6 +52,7 @@
 #define ORC_TAG_INIT 0u
 #define ORC_TAG_METRO 1u
 #define ORC_TAG_EXCH 2u
+#define ORC_TAG_SITE 3u
 #define ORC_NEAR_TIE 1e-9
 
 /* ---- Philox4x32-10, from the published definition (SC'11, Sec. 3) ---- */
@@ -85,6 +89,7 @@ static double orc_unit(uint32_t x1, uint32_t x2)
 
 typedef struct {
     int L, q, R, c;
+    int random_sites; /* 0: sites in order; 1: each attempt at a uniformly drawn site */
     uint32_t key[2];
     double* J;        /* J[r] = J*(r), r = 0..L-1, J[0] = 0 */
     double* beta;     /* beta[t], slot t */
@@ -204,9 +209,10 @@ static void orc_sweep_slot(oracle_t* o, int t, uint32_t n, int mode)
     uint8_t* s = o->s + (size_t)t * L;
     double* h = o->h ? o->h + (size_t)t * q * L : NULL;
     const double beta = o->beta[t];
-    for (int k = 0; k < L; ++k) {
-        uint32_t ctr[4] = {(uint32_t)k, (uint32_t)t, n, ORC_TAG_METRO}, x[4];
+    for (int m = 0; m < L; ++m) {
+        uint32_t ctr[4] = {(uint32_t)m, (uint32_t)t, n, o->random_sites ? ORC_TAG_SITE : ORC_TAG_METRO}, x[4];
         orc_philox(ctr, o->key, x);
+        const int k = o->random_sites ? (int)(((uint64_t)x[3] * (uint64_t)L) >> 32) : m;
         const int a = s[k];
         const int b = (a + 1 + (int)(((uint64_t)x[0] * (uint64_t)(q - 1)) >> 32)) % q;
         const double u = orc_unit(x[1], x[2]);
@@ -344,6 +350,7 @@ void oracle_get_fields(const oracle_t* o, double* out)
     if (o->h) memcpy(out, o->h, sizeof(double) * (size_t)o->R * o->q * o->L);
 }
 void oracle_set_counters(oracle_t* o, uint32_t nsweep, uint32_t nexch) { o->nsweep = nsweep; o->nexch = nexch; }
+void oracle_set_random_sites(oracle_t* o, int on) { o->random_sites = on ? 1 : 0; }
 void oracle_get_counters(const oracle_t* o, uint32_t* nsweep, uint32_t* nexch)
 {
     *nsweep = o->nsweep;

@@ -64,11 +64,13 @@ class Job:
     (e.g. torch.cuda.current_stream().cuda_stream); sweep_variant: "auto",
     "memory" or "registers" (FP32 field residency), "global" (fields in global
     memory even where they fit in shared memory), "registers<c>" (register
-    configuration c) -- all give identical results (see tune.py for a tuner).
+    configuration c) -- all give identical results (see tune.py for a tuner);
+    site_order: "sequential" or "random" (attempts at Philox-drawn sites; FP64,
+    direct sweep).
     """
 
     def __init__(self, L, q, sigma, temps, seed, precision="fp64", recompute_every=100, pair_factor=2,
-                 stream=None, sweep_variant="auto"):
+                 stream=None, sweep_variant="auto", site_order="sequential"):
         lib = _lib.load()
         self.L, self.q, self.sigma = int(L), int(q), float(sigma)
         self.temps = np.ascontiguousarray(temps, dtype=np.float64)
@@ -82,6 +84,7 @@ class Job:
         o.pair_factor = int(pair_factor)
         o.cuda_stream = ctypes.c_void_p(int(stream)) if stream else None
         o.sweep_variant = sweep_variant_code(sweep_variant)
+        o.site_order = {"sequential": 0, "random": 1}[site_order]
         h = ctypes.c_void_p()
         _lib.check(lib.potts_lr_create(self.L, self.q, self.sigma, _lib._ptr(self.temps), self.R,
                                        ctypes.c_uint64(self.seed), ctypes.byref(o), ctypes.byref(h)))

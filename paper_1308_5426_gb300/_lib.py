@@ -37,7 +37,8 @@ class PottsError(RuntimeError):
 
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("recompute_every", ctypes.c_int),
-                ("pair_factor", ctypes.c_int), ("cuda_stream", ctypes.c_void_p), ("sweep_variant", ctypes.c_int)]
+                ("pair_factor", ctypes.c_int), ("cuda_stream", ctypes.c_void_p), ("sweep_variant", ctypes.c_int),
+                ("site_order", ctypes.c_int)]
 
 
 _lib = None

@@ -134,6 +134,9 @@ int check_opts(const potts_lr_opts* o)
         return fail(POTTS_LR_EINVAL, "sweep_variant must be 0..4 or 17..24");
     if (o->sweep_variant == 4 && o->precision != POTTS_LR_FP64)
         return fail(POTTS_LR_EINVAL, "the direct sweep (sweep_variant 4) runs in FP64 mode only");
+    if (o->site_order != 0 && o->site_order != 1) return fail(POTTS_LR_EINVAL, "site_order must be 0 or 1");
+    if (o->site_order == 1 && (o->precision != POTTS_LR_FP64 || (o->sweep_variant != 0 && o->sweep_variant != 4)))
+        return fail(POTTS_LR_EINVAL, "random site order runs on the direct sweep: FP64, sweep_variant 0 or 4");
     return POTTS_LR_OK;
 }
 
@@ -215,6 +218,7 @@ int potts_lr_default_opts(potts_lr_opts* opts)
     opts->pair_factor = 2;
     opts->cuda_stream = nullptr;
     opts->sweep_variant = 0;
+    opts->site_order = 0;
     return POTTS_LR_OK;
 }
 
@@ -421,7 +425,8 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
     h->dj = (JobDev*)(base + o_job);
     h->dwork = (int2*)(base + o_work);
     h->sweep_smem = j.rf ? rf_smem_bytes(j.rf, q, L, h->Lpad) : sweep_smem_bytes(j);
-    if (o.sweep_variant == 4) {
+    j.random_sites = o.site_order;
+    if (o.sweep_variant == 4 || o.site_order == 1) {
         h->direct = true;
         h->sweep_smem = direct_sweep_smem_bytes(L, h->Lpad);
         if (h->sweep_smem > kSmemBudget) {

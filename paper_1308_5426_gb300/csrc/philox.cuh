@@ -8,7 +8,7 @@
 
 namespace plr {
 
-enum : uint32_t { kTagInit = 0u, kTagMetro = 1u, kTagExch = 2u };
+enum : uint32_t { kTagInit = 0u, kTagMetro = 1u, kTagExch = 2u, kTagSite = 3u };
 
 struct U4 {
     uint32_t x, y, z, w;

@@ -21,7 +21,8 @@ struct JobDev {
     int L, q, Lpad, W, R, c, precision;
     int recompute_every;  // FP32 mode: rebuild fields after sweeps n with (n+1) % K == 0
     int h_smem, j_smem;   // sweep kernel: fields / coupling table staged in shared memory
-    int rf;               // FP32 mode: register-resident sweep configuration (0 = none, 1..5)
+    int rf;               // FP32 mode: register-resident sweep configuration (0 = none, 1..8)
+    int random_sites;     // direct sweep: attempt m at a site drawn from Philox counter (m, slot, sweep, 3)
     uint32_t key0, key1;  // Philox key (seed low, high)
     double jtot;          // sum_r J*(r)
     const double* J64d;   // doubled table: J64d[m] = J*(m mod L), m = 0..2L-1

@@ -6,7 +6,9 @@
 // then a warp-shuffle and shared-memory reduction), and one thread applies
 // the FP64 rule of Eq. 8.  O(L) work and three CTA barriers per attempt.
 // Spins and J* sit in shared memory; the running energy accumulates dE in
-// FP64 in site order.
+// FP64 in attempt order.  With random sites, attempt k of a sweep goes to the
+// site floor(x3 L / 2^32) of Philox counter (k, slot, sweep, 3) (the other
+// reading of Sec. 4.2), with the proposal and u from the same block.
 #include <cmath>
 
 #include "sweep_common.cuh"
@@ -40,26 +42,39 @@ __global__ void __launch_bounds__(kDirThreads) sweep_direct_kernel(const JobDev*
     __syncthreads();
 
     const uint32_t n0 = jp->nsweep[t];
+    const bool rs = jp->random_sites != 0;
     double E = 0.0, u = 0.0;
     unsigned long long nacc = 0, nnear = 0;
     if (tid == 0) E = jp->E[rep];
     for (int sw = 0; sw < nsweeps; ++sw) {
         for (int k = 0; k < L; ++k) {
             if (tid == 0) {
-                int b;
-                float nlu;
-                uint32_t ux1, ux2;
-                const int a = s[k];
-                draw_proposal<true>(k, t, n0 + (uint32_t)sw, jp->key0, jp->key1, q, a, b, nlu, ux1, ux2);
-                u = unit53(ux1, ux2);
-                ab[0] = (a << 8) | b;
+                int b, site = k;
+                if (rs) {  // attempt k at a uniformly drawn site (the proposal and u from the same block)
+                    const U4 x = philox10(U4{(uint32_t)k, (uint32_t)t, n0 + (uint32_t)sw, kTagSite}, jp->key0,
+                                          jp->key1);
+                    site = (int)__umulhi(x.w, (uint32_t)L);
+                    const int a = s[site];
+                    b = a + 1 + (int)__umulhi(x.x, (uint32_t)(q - 1));
+                    if (b >= q) b -= q;
+                    u = unit53(x.y, x.z);
+                    ab[0] = (a << 8) | b;
+                } else {
+                    float nlu;
+                    uint32_t ux1, ux2;
+                    const int a = s[k];
+                    draw_proposal<true>(k, t, n0 + (uint32_t)sw, jp->key0, jp->key1, q, a, b, nlu, ux1, ux2);
+                    u = unit53(ux1, ux2);
+                    ab[0] = (a << 8) | b;
+                }
+                ab[1] = site;
             }
             __syncthreads();
-            const int a = ab[0] >> 8, b = ab[0] & 255;
+            const int a = ab[0] >> 8, b = ab[0] & 255, kk = ab[1];
             double part = 0.0;
             for (int j = tid; j < L; j += kDirThreads) {
-                const int w = (s[j] == a) - (s[j] == b);  // j = k adds J*(0) = 0
-                if (w) part += (double)w * J[j > k ? j - k : k - j];
+                const int w = (s[j] == a) - (s[j] == b);  // j = kk adds J*(0) = 0
+                if (w) part += (double)w * J[j > kk ? j - kk : kk - j];
             }
             for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(kFullMask, part, o);
             if (lane == 0) red[warp] = part;
@@ -68,7 +83,7 @@ __global__ void __launch_bounds__(kDirThreads) sweep_direct_kernel(const JobDev*
                 double d = 0.0;
                 for (int w = 0; w < kDirWarps; ++w) d += red[w];
                 if (decide_fp64_exact(d, cb, u, nnear)) {
-                    s[k] = (uint8_t)b;
+                    s[kk] = (uint8_t)b;
                     E += (double)c * d;
                     ++nacc;
                 }

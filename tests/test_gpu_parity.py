@@ -211,3 +211,25 @@ def test_parity_direct_sweep(plr, L, q, sigma, R, c, seed, steps):
     np.testing.assert_allclose(g.fields(), o.fields(), rtol=0, atol=1e-12 * oracle.jtot(L, sigma))
     with pytest.raises(plr.PottsError):
         plr.Job(L, q, sigma, temps, seed, precision="fp32", sweep_variant="direct")
+
+
+@pytest.mark.parametrize("L,q,sigma,R,seed,steps", [
+    (64, 3, 0.5, 16, 1, 200),
+    (257, 4, 0.15, 6, 6, 30),
+    (1000, 5, 0.4, 4, 3, 6),
+])
+def test_parity_random_site_order(plr, L, q, sigma, R, seed, steps):
+    """Random site order (attempt m of a sweep at a Philox-drawn site) on the
+    direct sweep follows the oracle's random-site chain bit for bit."""
+    temps = workloads.geometric_ratios(R, 0.05, 1.0) * oracle.jtot(L, sigma)
+    g = plr.Job(L, q, sigma, temps, seed, precision="fp64", site_order="random")
+    o = oracle.Oracle(L, q, sigma, temps, seed, site_order="random")
+    for _ in range(steps):
+        g.sweep(1)
+        g.exchange()
+        o.sweep(1, mode="direct")
+        o.exchange()
+    _compare(g, o, "random sites L=%d" % L)
+    for bad in (dict(precision="fp32"), dict(precision="fp64", sweep_variant="memory")):
+        with pytest.raises(plr.PottsError):
+            plr.Job(L, q, sigma, temps, seed, site_order="random", **bad)

@@ -219,3 +219,99 @@ def test_one_sweep_transition_law():
         np.testing.assert_allclose(pi @ Th, pi, atol=1e-13)
         x2h, dofh = stat(Th[index[tuple(int(v) for v in s0)]])
         assert chi2.sf(x2h, dofh) < 1e-6, (t, x2h, dofh)
+
+
+def test_random_site_order_follows_generator_at_infinite_temperature():
+    """Random-site order, beta -> 0: attempt m of sweep n in slot t goes to site
+    k = floor(x3 L / 2^32) of Philox counter (m, t, n, 3) and always flips it
+    to (a + 1 + floor(x0 (q-1) / 2^32)) mod q, a being the site's current
+    state (a site may be drawn twice in one sweep)."""
+    L, q, R, seed = 40, 4, 2, 31
+    o = Oracle(L, q, 1.0, np.full(R, 1e300), seed, site_order="random")
+    s = o.spins().astype(np.int64)
+    key = np.array([seed & 0xFFFFFFFF, seed >> 32], np.uint32)
+    for n in range(3):
+        for t in range(R):
+            for m in range(L):
+                x = [int(v) for v in philox4x32_10(np.array([m, t, n, 3], np.uint32), key)]
+                k = (x[3] * L) >> 32
+                s[t, k] = (s[t, k] + 1 + ((x[0] * (q - 1)) >> 32)) % q
+        o.sweep(1, mode="direct")
+        np.testing.assert_array_equal(o.spins(), s)
+
+
+def test_random_site_one_sweep_transition_law():
+    """Random-site order is the chain of the averaged single-site kernel: one
+    sweep = (1/L sum_k P_k)^L.  The oracle's end states from a fixed start
+    follow that row (chi square), and reject the sequential-order row."""
+    from scipy.stats import chi2
+    L, q, sigma, c = 4, 3, 0.5, 2
+    J = jstar(L, sigma)
+    temps = np.array([0.2, 0.6]) * jtot(L, sigma)
+    s0 = np.array([0, 1, 1, 2], dtype=np.uint8)
+    o = Oracle(L, q, sigma, temps, seed=4343, c=c, site_order="random")
+    nsamp = 20000
+    counts = np.zeros((o.R, q ** L))
+    for _ in range(nsamp):
+        o.set_spins(np.tile(s0, (o.R, 1)))
+        o.sweep(1, mode="direct")
+        s = o.spins()
+        for t in range(o.R):
+            counts[t, int(sum(int(v) * q ** (L - 1 - i) for i, v in enumerate(s[t])))] += 1
+    import itertools
+    states = list(itertools.product(range(q), repeat=L))
+    index = {st: n for n, st in enumerate(states)}
+    E = np.array([-0.5 * c * sum(J[abs(i - j) % L] for i in range(L) for j in range(L) if i != j and st[i] == st[j])
+                  for st in states])
+    for t in range(o.R):
+        beta = 1.0 / temps[t]
+        Pbar = np.zeros((len(states), len(states)))
+        for k in range(L):
+            for n, st in enumerate(states):
+                for x in range(q):
+                    if x == st[k]:
+                        continue
+                    m = index[st[:k] + (x,) + st[k + 1:]]
+                    p = min(1.0, math.exp(-beta * (E[m] - E[n]))) / (q - 1) / L
+                    Pbar[n, m] += p
+                    Pbar[n, n] += 1.0 / (q - 1) / L - p
+        T = np.linalg.matrix_power(Pbar, L)
+        pi = np.exp(-beta * (E - E.min()))
+        pi /= pi.sum()
+        np.testing.assert_allclose(pi @ T, pi, atol=1e-13)
+        Tseq, _, _ = _one_sweep_kernel(L, q, J, c, beta, "metropolis")
+        row0 = index[tuple(int(v) for v in s0)]
+
+        def stat(p):
+            msk = p * nsamp > 5
+            return ((counts[t][msk] - nsamp * p[msk]) ** 2 / (nsamp * p[msk])).sum(), int(msk.sum()) - 1
+
+        x2, dof = stat(T[row0])
+        assert chi2.sf(x2, dof) > 1e-4, (t, x2, dof)
+        x2s, dofs = stat(Tseq[row0])
+        assert chi2.sf(x2s, dofs) < 1e-6, (t, x2s, dofs)
+
+
+def test_random_site_chain_samples_boltzmann():
+    """Random-site PT at L = 8, q = 3 samples exp(-beta H): <E> and <M> per slot
+    agree with exact enumeration within 3 binned standard errors."""
+    L, q, sigma, c = 8, 3, 0.5, 2
+    ratios = (0.15, 0.3, 0.6)
+    temps = np.array(ratios) * jtot(L, sigma)
+    o = Oracle(L, q, sigma, temps, seed=777, c=c, site_order="random")
+    for _ in range(500):
+        o.step()
+    n = 40_000
+    E = np.zeros((n, o.R))
+    M = np.zeros((n, o.R))
+    for k in range(n):
+        o.step()
+        E[k] = o.running_energy()
+        M[k] = o.magnetisation()
+    ex = exact_averages(L, q, jstar(L, sigma), c, 1.0 / temps)
+    for t in range(o.R):
+        for name, series in (("E", E[:, t]), ("M", M[:, t])):
+            mean, se = _binned(series)
+            var = ex[name + "2"][t] - ex[name][t] ** 2
+            se = max(se, math.sqrt(max(var, 0.0) / n))
+            assert abs(mean - ex[name][t]) < 3.0 * se + 1e-12, (t, name, mean, ex[name][t], se)
