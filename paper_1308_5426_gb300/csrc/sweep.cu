@@ -40,7 +40,7 @@ struct SweepSmem {
     {
         (void)L;
         size_t b = 0;
-        if (js) b += (size_t)Lpad * sizeof(T);
+        if (js) b += ((size_t)Lpad + 4) * sizeof(T);  // J*(m mod L), m < Lpad + 4
         if (hs) b += (size_t)q * Lpad * sizeof(T);
         b += (size_t)Lpad;                       // spins
         b += 2 * 2 * kSiteBlock * sizeof(int);   // double-buffered flip lists
@@ -104,6 +104,52 @@ __device__ __forceinline__ void apply_flips(T* __restrict__ h, const T* __restri
     }
 }
 
+// FP32 form of apply_flips: the same updates in the same order, each thread
+// taking four consecutive sites at a time with 16-byte loads and stores of
+// the two field rows (two such groups in flight), the coupling of site i0 + e
+// read as J[r + e], r = (i0 - k) mod L, from a table that runs four entries
+// past L (J[m] = J*(m mod L)).  Groups that overlap the block being decided,
+// [x0, x0 + nx), are left to the deciding warp (its sites) or untouched
+// (padding past L).
+__device__ __forceinline__ void apply_flips_vec4(float* __restrict__ h, const float* __restrict__ J, int L, int Lpad,
+                                                 const int* pk, const int* pab, int nf, int x0, int nx, int u)
+{
+    constexpr int nw = kSweepThreads - 32;
+    const int ng = (L + 3) >> 2;                        // groups holding sites < L
+    const int g0 = x0 >> 2, g1 = (x0 + nx + 3) >> 2;    // groups of the decided block (x0 % 32 == 0)
+    const int n = ng - (g1 - g0);
+    for (int jg = u; jg < n; jg += 2 * nw) {
+        int i0[2];
+        bool ok[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int gg = jg + e * nw;
+            ok[e] = gg < n;
+            i0[e] = 4 * ((ok[e] ? gg : jg) < g0 ? (ok[e] ? gg : jg) : (ok[e] ? gg : jg) + (g1 - g0));
+        }
+        for (int f = 0; f < nf; ++f) {
+            const int kf = pk[f], af = pab[f] >> 8, bf = pab[f] & 255;
+            float4 xa[2], xb[2], v[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                int r = i0[e] - kf;
+                r += r < 0 ? L : 0;
+                v[e] = make_float4(J[r], J[r + 1], J[r + 2], J[r + 3]);
+                xa[e] = *(const float4*)(h + (size_t)af * Lpad + i0[e]);
+                xb[e] = *(const float4*)(h + (size_t)bf * Lpad + i0[e]);
+            }
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                if (!ok[e]) continue;
+                xa[e].x -= v[e].x; xa[e].y -= v[e].y; xa[e].z -= v[e].z; xa[e].w -= v[e].w;
+                xb[e].x += v[e].x; xb[e].y += v[e].y; xb[e].z += v[e].z; xb[e].w += v[e].w;
+                *(float4*)(h + (size_t)af * Lpad + i0[e]) = xa[e];
+                *(float4*)(h + (size_t)bf * Lpad + i0[e]) = xb[e];
+            }
+        }
+    }
+}
+
 // nsweeps sweeps of one work item wk = (job, slot) by the whole CTA
 template <typename T, bool HS, bool JS>
 __device__ __forceinline__ void sweep_item(const JobDev* __restrict__ jobs, const int2 wk, int nsweeps,
@@ -126,7 +172,7 @@ __device__ __forceinline__ void sweep_item(const JobDev* __restrict__ jobs, cons
     T* Js = nullptr;
     if constexpr (JS) {
         Js = (T*)(smem + off);
-        off += (size_t)Lpad * sizeof(T);
+        off += ((size_t)Lpad + 4) * sizeof(T);
     }
     T* hs = nullptr;
     if constexpr (HS) {
@@ -142,7 +188,7 @@ __device__ __forceinline__ void sweep_item(const JobDev* __restrict__ jobs, cons
     int* lcnt = (int*)(red + kWarps);  // [2] flip counts
 
     if constexpr (JS)
-        for (int m = tid; m < Lpad; m += kSweepThreads) Js[m] = m < L ? Jg[m] : (T)0;
+        for (int m = tid; m < Lpad + 4; m += kSweepThreads) Js[m] = Jg[m % L];
     if constexpr (HS) {
         const int n = q * Lpad;
         for (int e = tid; e < n; e += kSweepThreads) hs[e] = hg[e];
@@ -222,7 +268,11 @@ __device__ __forceinline__ void sweep_item(const JobDev* __restrict__ jobs, cons
         } else if (npend > 0) {
             // apply block g-1's flips everywhere except at the sites warp 0 owns
             // now: ranges [0, k0) and [k0 + nv, L)
-            apply_flips<T>(h, J, L, Lpad, pk, pab, npend, k0, nv, tid - 32);
+            // FP32 with fields or table in global memory: four sites per thread
+            // (with both in shared memory, the table reads four sites apart
+            // conflict in the banks and the one-site form is faster)
+            if constexpr (kFP64 || (HS && JS)) apply_flips<T>(h, J, L, Lpad, pk, pab, npend, k0, nv, tid - 32);
+            else apply_flips_vec4(h, J, L, Lpad, pk, pab, npend, k0, nv, tid - 32);
         }
         __syncthreads();
     }
