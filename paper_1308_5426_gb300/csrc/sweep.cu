@@ -31,7 +31,18 @@ namespace plr {
 
 namespace {
 
-constexpr int kWarps = kSweepThreads / 32;
+#ifndef PLR_GLOBAL_THREADS
+#define PLR_GLOBAL_THREADS 512
+#endif
+// threads of a sweep CTA: 256 with the fields in shared memory (several CTAs
+// per SM), more with the fields in global memory, where the update's round
+// trips to L2 want more warps in flight per slot
+template <bool HS>
+constexpr int sweep_threads()
+{
+    return HS ? kSweepThreads : PLR_GLOBAL_THREADS;
+}
+constexpr int kWarpsMax = 1024 / 32;
 
 template <typename T>
 struct SweepSmem {
@@ -45,7 +56,7 @@ struct SweepSmem {
         b += (size_t)Lpad;                       // spins
         b += 2 * 2 * kSiteBlock * sizeof(int);   // double-buffered flip lists
         b += kNearTable * sizeof(float);         // J* at distances 0..63 in FP32
-        b += kWarps * sizeof(double) + 16;       // reduction scratch, counts
+        b += kWarpsMax * sizeof(double) + 16;    // reduction scratch, counts
         return (b + 15) & ~(size_t)15;
     }
 };
@@ -53,15 +64,15 @@ struct SweepSmem {
 // Rank-1 updates of the flips (pk, pab)[0..nf), in flip order, on every
 // element except [x0, x0 + nx): h[a][i] -= J*((i-k) mod L), h[b][i] += J*((i-k) mod L).
 // The elements form one index space j = 0..L-nx-1 (i = j, or j + nx past x0);
-// worker u of nw = kSweepThreads - 32 takes j = u + nw m (stride 1 across a
+// worker u of nw = NT - 32 takes j = u + nw m (stride 1 across a
 // warp: conflict-free shared-memory access) four at a time, and applies all
 // flips to those four before moving on, so four independent read-modify-write
 // chains are in flight and the flip list is read once per four elements.
-template <typename T>
+template <typename T, int NT>
 __device__ __forceinline__ void apply_flips(T* __restrict__ h, const T* __restrict__ J, int L, int Lpad,
                                             const int* pk, const int* pab, int nf, int x0, int nx, int u)
 {
-    constexpr int nw = kSweepThreads - 32;
+    constexpr int nw = NT - 32;
     const int n = L - nx;
     int j = u;
     for (; j + 3 * nw < n; j += 4 * nw) {
@@ -111,10 +122,11 @@ __device__ __forceinline__ void apply_flips(T* __restrict__ h, const T* __restri
 // past L (J[m] = J*(m mod L)).  Groups that overlap the block being decided,
 // [x0, x0 + nx), are left to the deciding warp (its sites) or untouched
 // (padding past L).
+template <int NT>
 __device__ __forceinline__ void apply_flips_vec4(float* __restrict__ h, const float* __restrict__ J, int L, int Lpad,
                                                  const int* pk, const int* pab, int nf, int x0, int nx, int u)
 {
-    constexpr int nw = kSweepThreads - 32;
+    constexpr int nw = NT - 32;
     const int ng = (L + 3) >> 2;                        // groups holding sites < L
     const int g0 = x0 >> 2, g1 = (x0 + nx + 3) >> 2;    // groups of the decided block (x0 % 32 == 0)
     const int n = ng - (g1 - g0);
@@ -156,6 +168,7 @@ __device__ __forceinline__ void sweep_item(const JobDev* __restrict__ jobs, cons
                                            unsigned char* __restrict__ smem)
 {
     constexpr bool kFP64 = sizeof(T) == 8;
+    constexpr int NT = sweep_threads<HS>();
     const JobDev* jp = jobs + wk.x;
     const int t = wk.y;
     const int L = jp->L, q = jp->q, Lpad = jp->Lpad, W = jp->W, c = jp->c;
@@ -185,15 +198,15 @@ __device__ __forceinline__ void sweep_item(const JobDev* __restrict__ jobs, cons
     int* lab = lk + 2 * kSiteBlock;    // [2][32] (a << 8) | b
     float* Jn = (float*)(lab + 2 * kSiteBlock);  // J*(r), r < 64, FP32
     double* red = (double*)(((uintptr_t)(Jn + kNearTable) + 7) & ~(uintptr_t)7);
-    int* lcnt = (int*)(red + kWarps);  // [2] flip counts
+    int* lcnt = (int*)(red + kWarpsMax);  // [2] flip counts
 
     if constexpr (JS)
-        for (int m = tid; m < Lpad + 4; m += kSweepThreads) Js[m] = Jg[m % L];
+        for (int m = tid; m < Lpad + 4; m += NT) Js[m] = Jg[m % L];
     if constexpr (HS) {
         const int n = q * Lpad;
-        for (int e = tid; e < n; e += kSweepThreads) hs[e] = hg[e];
+        for (int e = tid; e < n; e += NT) hs[e] = hg[e];
     }
-    for (int i = tid; i < L; i += kSweepThreads) s[i] = (uint8_t)((spins[i >> 3] >> (4 * (i & 7))) & 15u);
+    for (int i = tid; i < L; i += NT) s[i] = (uint8_t)((spins[i >> 3] >> (4 * (i & 7))) & 15u);
     if (tid < kNearTable) Jn[tid] = tid < L ? (float)jp->J64d[tid] : 0.0f;
     if (tid < 2) lcnt[tid] = 0;
     __syncthreads();
@@ -271,14 +284,14 @@ __device__ __forceinline__ void sweep_item(const JobDev* __restrict__ jobs, cons
             // FP32 with fields or table in global memory: four sites per thread
             // (with both in shared memory, the table reads four sites apart
             // conflict in the banks and the one-site form is faster)
-            if constexpr (kFP64 || (HS && JS)) apply_flips<T>(h, J, L, Lpad, pk, pab, npend, k0, nv, tid - 32);
-            else apply_flips_vec4(h, J, L, Lpad, pk, pab, npend, k0, nv, tid - 32);
+            if constexpr (kFP64 || (HS && JS)) apply_flips<T, NT>(h, J, L, Lpad, pk, pab, npend, k0, nv, tid - 32);
+            else apply_flips_vec4<NT>(h, J, L, Lpad, pk, pab, npend, k0, nv, tid - 32);
         }
         __syncthreads();
     }
 
     // write back
-    for (int w = tid; w < W; w += kSweepThreads) {
+    for (int w = tid; w < W; w += NT) {
         uint32_t word = 0;
         for (int m = 0; m < 8; ++m) {
             const int i = 8 * w + m;
@@ -288,14 +301,17 @@ __device__ __forceinline__ void sweep_item(const JobDev* __restrict__ jobs, cons
     }
     if constexpr (HS) {
         const int n = q * Lpad;
-        for (int e = tid; e < n; e += kSweepThreads) hg[e] = hs[e];
+        for (int e = tid; e < n; e += NT) hg[e] = hs[e];
     }
     if constexpr (kFP64) {
-        // E = -(c/2) sum_i h[s_i][i] from the FP64 fields (Eq. 2 through the fields)
+        // E = -(c/2) sum_i h[s_i][i] from the FP64 fields (Eq. 2 through the
+        // fields), summed over 256 fixed strands whatever the CTA size, so
+        // that every kernel variant rounds the sum alike
         double part = 0.0;
-        for (int i = tid; i < L; i += kSweepThreads) part += (double)h[(size_t)s[i] * Lpad + i];
+        if (tid < kSweepThreads)
+            for (int i = tid; i < L; i += kSweepThreads) part += (double)h[(size_t)s[i] * Lpad + i];
         for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(kFullMask, part, o);
-        if (lane == 0) red[warp] = part;
+        if (lane == 0 && warp < kSweepThreads / 32) red[warp] = part;
     }
     if (warp == 0) {
         for (int o = 16; o > 0; o >>= 1) {
@@ -307,7 +323,7 @@ __device__ __forceinline__ void sweep_item(const JobDev* __restrict__ jobs, cons
     if (tid == 0) {
         if constexpr (kFP64) {
             double tot = 0.0;
-            for (int w = 0; w < kWarps; ++w) tot += red[w];
+            for (int w = 0; w < kSweepThreads / 32; ++w) tot += red[w];
             jp->E[rep] = -0.5 * (double)c * tot;
         } else {
             jp->E[rep] += dE_acc;
@@ -322,7 +338,7 @@ __device__ __forceinline__ void sweep_item(const JobDev* __restrict__ jobs, cons
 // persistent: each CTA takes the item dealt to its place on its SM, then
 // further items from the ordered list until none is left.
 template <typename T, bool HS, bool JS>
-__global__ void __launch_bounds__(kSweepThreads, HS ? 4 : 2) sweep_kernel(const JobDev* __restrict__ jobs,
+__global__ void __launch_bounds__(sweep_threads<HS>(), HS ? 4 : 1) sweep_kernel(const JobDev* __restrict__ jobs,
                                                               const int2* __restrict__ work, int nsweeps,
                                                               const SweepSched sc)
 {
@@ -358,7 +374,7 @@ cudaError_t launch_variant(const JobDev* jobs_dev, const int2* work, int nwork, 
     // already gives each its own SM)
     if (sched && sched->nsm > 0 && nwork > sched->nsm) {
         int occ = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kSweepThreads, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, sweep_threads<HS>(), smem);
         if (e != cudaSuccess) return e;
         if (occ > 0) {
             sc = *sched;
@@ -368,7 +384,7 @@ cudaError_t launch_variant(const JobDev* jobs_dev, const int2* work, int nwork, 
             if ((e = launch_sweep_plan(jobs_dev, work, sc, st)) != cudaSuccess) return e;
         }
     }
-    k<<<grid, kSweepThreads, smem, st>>>(jobs_dev, work, nsweeps, sc);
+    k<<<grid, sweep_threads<HS>(), smem, st>>>(jobs_dev, work, nsweeps, sc);
     return cudaGetLastError();
 }
 
