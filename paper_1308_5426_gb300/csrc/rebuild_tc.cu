@@ -8,20 +8,23 @@
 // memory.  X is exact in BF16 (0 or 1); C is carried as three BF16 parts
 // hi + mid + lo of the FP64 J* (representation error ~2^-25 J*), each part one
 // MMA per K-step.  One CTA computes a 128 x 64 tile of H over
-// all of K in chunks of 64 sites: the four warps build the operand tiles in
+// all of K in chunks of 64 sites: eight warps build the operand tiles in
 // shared memory from the split table and the packed spins, one thread issues
-// the 12 MMAs of the chunk (4 K-steps x 3 parts) and commits them to an
-// mbarrier.  The tensor core's FP32 accumulation rounds every MMA's sum into
+// the 12 MMAs of the chunk (4 K-steps x 3 parts) and commits them to the
+// mbarrier of the chunk's stage; two stages alternate, so chunk t + 1 is
+// built while the MMAs of chunk t run.  The tensor core's FP32 accumulation rounds every MMA's sum into
 // the accumulator, so the accumulation chains are kept short: the hi parts of
 // successive chunks rotate over seven accumulators, and the small mid + lo
 // parts go to an eighth of their own (their rounding is then relative to their
 // own small size).  8 accumulators x 64 columns = 512 TMEM columns; the
 // epilogue adds them in FP64 and stores FP32 fields.
 //
-// Operand layout (both K-major, no swizzle): 8-row x 16-byte core matrices;
-// core matrix (row group g, K group c) of a tile with G row groups and 64 K
-// sites at byte (c G + g) 128, so the leading (K) byte offset is 128 G and the
-// stride (row-group) byte offset is 128; K-step s (16 sites) starts at 256 G s.
+// Operand layout (both K-major, no swizzle): 8-row x 16-byte core matrices.
+// B: core matrix (row group g, K group c) at byte (c G + g) 128 (leading (K)
+// byte offset 128 G, stride (row-group) byte offset 128; K-step s at 256 G s).
+// A: the chunk's sites are taken in reverse order (as in B), which makes the
+// circulant tile Hankel: core matrix (g, c) = core matrix g + c of a strip of
+// 23, so both byte offsets are 128 and K-step s starts at 256 s.
 #include <cstdint>
 #include <vector>
 
@@ -31,16 +34,19 @@ namespace plr {
 
 namespace {
 
-constexpr int kTcThreads = 128;
+constexpr int kTcThreads = 256;      // 8 warps build the tiles; warps w and w + 4 share TMEM lanes 32 (w % 4) ..
 constexpr int kTileM = 128;
 constexpr int kTileN = 64;
 constexpr int kChunk = 64;           // K sites per chunk
 constexpr int kAcc = 8;              // accumulators (kAcc * kTileN = 512 TMEM columns)
 constexpr int kAccHi = kAcc - 1;     // rotating accumulators of the hi parts; the last takes mid + lo
-constexpr int kTileBytes = kTileM * kChunk * 2;  // 16 KB per 128 x 64 BF16 A tile
+constexpr int kHank = kTileM / 8 + kChunk / 8 - 1;  // distinct core matrices of an A tile (Hankel form)
+constexpr int kTileBytes = kHank * 128;            // 2944 B per A tile of one split
 constexpr int kTileBytesB = kTileN * kChunk * 2; // 8 KB per 64 x 64 BF16 B tile
-constexpr int kGA = kTileM / 8, kGB = kTileN / 8;  // row groups of the A and B tiles
+constexpr int kGB = kTileN / 8;      // row groups of the B tile
 constexpr int kSplit = 3;
+constexpr int kStageBytes = kSplit * kTileBytes + kTileBytesB;  // one stage: three A tiles + the B tile
+constexpr int kStages = 2;           // chunk t + 1 is built while the MMAs of chunk t run
 constexpr uint32_t kTmemCols = kAcc * kTileN;
 constexpr long long kWaitLimit = 1ll << 26;  // bounded mbarrier wait (iterations)
 constexpr size_t kTcMinSmem = 120 * 1024;   // forces one CTA per SM (owner of all 512 columns)
@@ -84,18 +90,27 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
 
 __device__ __forceinline__ uint16_t bf16_one() { return 0x3F80u; }
 
+// (i - k) mod L for i < L + 128 and k < L + 64 (tile and chunk padding past L
+// only meet zero operands, so any in-range index serves there)
+__device__ __forceinline__ int circ(int d, int L)
+{
+    d += d < 0 ? L : 0;
+    d -= d >= L ? L : 0;
+    return (d < 0 || d >= L) ? 0 : d;
+}
+
 __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* __restrict__ jobs,
                                                                   const int4* __restrict__ tiles, int ntiles,
                                                                   int cond)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int kWarps = kTcThreads / 32;
 
-    unsigned char* tileA = smem;                               // kSplit tiles
-    unsigned char* tileB = smem + kSplit * kTileBytes;         // one tile
-    uint64_t* mbar = (uint64_t*)(smem + kSplit * kTileBytes + kTileBytesB);
-    uint32_t* tmem_slot = (uint32_t*)(mbar + 1);
-    uint16_t* tab = (uint16_t*)(smem + kSplit * kTileBytes + kTileBytesB + 64);  // split table [3][Lpad], if staged
+    // stage b: A tiles at b * kStageBytes, then its B tile
+    uint64_t* mbar = (uint64_t*)(smem + kStages * kStageBytes);  // one per stage
+    uint32_t* tmem_slot = (uint32_t*)(mbar + kStages);
+    uint16_t* tab = (uint16_t*)(smem + kStages * kStageBytes + 64);  // split table [3][Lpad], if staged
 
     // skip the whole CTA when none of its tiles is due (no tensor memory taken)
     bool any = false;
@@ -108,7 +123,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* 
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)) : "memory");
+        for (int b = 0; b < kStages; ++b)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar + b)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -119,8 +135,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* 
     const int rr = lane >> 2, kp = (lane & 3) * 2;
     const uint32_t idesc = make_idesc(kTileM, kTileN);
     bool ok = true;
-    uint32_t parity = 0;
-    const JobDev* staged = nullptr;  // job whose split table is in shared memory
+    uint32_t parity[kStages] = {0u, 0u};  // phase of each stage's barrier that is awaited next
+    int pending[kStages] = {0, 0};        // commits on each stage's barrier not yet awaited
+    const JobDev* staged = nullptr;       // job whose split table is in shared memory
 
     for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x) {
     const int4 tile = tiles[ti];
@@ -149,39 +166,52 @@ __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* 
         const int o = kk == 0 ? 0 : ((kk & 1) ? (kk + 1) / 2 : -(kk / 2));
         const int c = ((cc + o) % nchunks + nchunks) % nchunks;
         const int k0 = c * kChunk;
-        // A tiles: each warp fills whole core matrices (g, kc), one 4-byte pair per lane
-        for (int cm = warp; cm < kGA * (kChunk / 8); cm += kTcThreads / 32) {
-            const int g = cm % kGA, kc = cm / kGA;
-            const int i = m0 + 8 * g + rr;
-            const int k = k0 + 8 * kc + kp;
-            const uint32_t off = (uint32_t)((kc * kGA + g) * 128 + rr * 16 + kp * 2);
-            int r0 = (i - k) % L;
-            r0 += r0 < 0 ? L : 0;
-            int r1 = r0 - 1;
-            r1 += r1 < 0 ? L : 0;
+        const int b = t % kStages;
+        unsigned char* tileA = smem + b * kStageBytes;
+        unsigned char* tileB = tileA + kSplit * kTileBytes;
+        // the MMAs that last read this stage (chunk t - kStages) must be done
+        if (pending[b]) {
+            if (!mbar_wait(smem_u32(mbar + b), parity[b])) ok = false;
+            parity[b] ^= 1u;
+            pending[b] = 0;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        }
+        // The chunk's K sites are taken in reverse, k = k0 + 63 - k', so A[i][k'] =
+        // J*((i - k) mod L) depends on i + k' only: core matrix (g, c) is core
+        // matrix h = g + c of a Hankel strip of 23, which the MMA reads with
+        // row-group and K-group strides both 128 bytes.  Element (rr, e) of
+        // core matrix h is J*((m0 - k0 - 63 + 8 h + rr + e) mod L).
+        for (int h = warp; h < kHank; h += kWarps) {
+            const int r0 = circ(m0 - k0 - (kChunk - 1) + 8 * h + rr + kp, L);
+            const int r1 = r0 + 1 == L ? 0 : r0 + 1;
+            const uint32_t off = (uint32_t)(h * 128 + rr * 16 + kp * 2);
 #pragma unroll
             for (int sp = 0; sp < kSplit; ++sp) {
                 const uint32_t v = (uint32_t)T[sp * Lpad + r0] | ((uint32_t)T[sp * Lpad + r1] << 16);
                 *(uint32_t*)(tileA + sp * kTileBytes + off) = v;
             }
         }
-        // B tile: row n = (replica, state), X = 1 where the replica's spin at site k is that state
-        for (int cm = warp; cm < kGB * (kChunk / 8); cm += kTcThreads / 32) {
+        // B tile: row n = (replica, state), X = 1 where the replica's spin at site
+        // k = k0 + 63 - k' is that state (K reversed as for A)
+        for (int cm = warp; cm < kGB * (kChunk / 8); cm += kWarps) {
             const int g = cm % kGB, kc = cm / kGB;
             const int n = n0 + 8 * g + rr;
-            const int k = k0 + 8 * kc + kp;
+            const int ka = k0 + (kChunk - 1) - (8 * kc + kp);  // site of k' = 8 kc + kp; k' + 1 is ka - 1
             const uint32_t off = (uint32_t)((kc * kGB + g) * 128 + rr * 16 + kp * 2);
             uint32_t v = 0;
-            if (n < N) {
+            if (n < N && ka - 1 < L) {
                 const int rep = n / q, x = n - rep * q;
-                const uint32_t* sp = jb.spins + (size_t)rep * W;
-                if (k < L && (int)((sp[k >> 3] >> (4 * (k & 7))) & 15u) == x) v |= bf16_one();
-                if (k + 1 < L && (int)((sp[(k + 1) >> 3] >> (4 * ((k + 1) & 7))) & 15u) == x) v |= (uint32_t)bf16_one() << 16;
+                const uint32_t word = jb.spins[(size_t)rep * W + ((ka - 1) >> 3)] >> (4 * ((ka - 1) & 7));
+                if (ka < L && (int)((word >> 4) & 15u) == x) v |= bf16_one();  // ka odd: same word, next nibble
+                if ((int)(word & 15u) == x) v |= (uint32_t)bf16_one() << 16;
             }
             *(uint32_t*)(tileB + off) = v;
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
+        if (!__syncthreads_and(ok)) {
+            ok = false;
+            break;
+        }
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t dhi = tmem + (uint32_t)((t % kAccHi) * kTileN);
@@ -191,8 +221,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* 
                 const uint64_t bdesc = make_desc(smem_u32(tileB) + s * 256 * kGB, 128 * kGB, 128);
 #pragma unroll
                 for (int sp = 0; sp < kSplit; ++sp) {
-                    const uint64_t adesc =
-                        make_desc(smem_u32(tileA + sp * kTileBytes) + s * 256 * kGA, 128 * kGA, 128);
+                    const uint64_t adesc = make_desc(smem_u32(tileA + sp * kTileBytes) + s * 256, 128, 128);
                     const uint32_t dcol = sp == 0 ? dhi : dsmall;
                     const bool first = s == 0 && (sp == 0 ? t < kAccHi : (t == 0 && sp == 1));
                     const uint32_t accumulate = first ? 0u : 1u;
@@ -205,33 +234,38 @@ __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* 
                 }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_u32(mbar))
+                             smem_u32(mbar + b))
                          : "memory");
         }
-        // all threads wait for the chunk's MMAs before the tiles are rebuilt
-        if (!mbar_wait(smem_u32(mbar), parity)) ok = false;
-        parity ^= 1u;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (!__syncthreads_and(ok)) {
-            ok = false;
-            break;
-        }
+        pending[b] = 1;
     }
+    // all of the tile's MMAs done before its accumulators are read
+    for (int b = 0; b < kStages; ++b)
+        if (pending[b]) {
+            if (!mbar_wait(smem_u32(mbar + b), parity[b])) ok = false;
+            parity[b] ^= 1u;
+            pending[b] = 0;
+        }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!__syncthreads_and(ok)) ok = false;
 
     if (ok) {
-        // epilogue: warp w reads TMEM lanes 32w..32w+31 = rows m0 + 32w + lane
-        const int i = m0 + 32 * warp + lane;
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 = rows m0 + 32 (w % 4) + lane,
+        // columns half (w / 4) of the tile
+        const int quad = warp & 3;
+        const int i = m0 + 32 * quad + lane;
         const int nhi = nchunks < kAccHi ? nchunks : kAccHi;
         float* F = (float*)jb.fields;
         double dmax = 0.0;
-        for (int cb = 0; cb < kTileN; cb += 8) {
+        constexpr int kCols = kTileN / (kWarps / 4);
+        for (int cb = (warp >> 2) * kCols; cb < (warp >> 2) * kCols + kCols; cb += 8) {
             double sum[8];
 #pragma unroll
             for (int e = 0; e < 8; ++e) sum[e] = 0.0;
             for (int a = 0; a <= nhi; ++a) {
                 const int col = a < nhi ? a : kAccHi;  // the used hi accumulators, then mid + lo
                 uint32_t v[8];
-                const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(col * kTileN + cb);
+                const uint32_t taddr = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(col * kTileN + cb);
                 asm volatile(
                     "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                     : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
@@ -264,6 +298,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* 
         atomicExch(jb.status, 1);  // a bounded wait expired; the host reports ETIMEOUT
     }
     }  // tiles
+    // no MMA may still write tensor memory when it is freed (after an expired
+    // wait, give the outstanding commits a bounded chance to land)
+    for (int b = 0; b < kStages; ++b)
+        if (pending[b]) mbar_wait(smem_u32(mbar + b), parity[b]);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
@@ -274,14 +312,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* 
 
 size_t tc_smem_bytes(int Lpad, int tab_smem)
 {
-    size_t b = (size_t)kSplit * kTileBytes + kTileBytesB + 64 + (tab_smem ? (size_t)kSplit * Lpad * 2 : 0);
+    size_t b = (size_t)kStages * kStageBytes + 64 + (tab_smem ? (size_t)kSplit * Lpad * 2 : 0);
     b = (b + 127) & ~(size_t)127;
     return b < kTcMinSmem ? kTcMinSmem : b;
 }
 
 int tc_table_in_smem(int Lpad)
 {
-    return (size_t)kSplit * kTileBytes + kTileBytesB + 64 + (size_t)kSplit * Lpad * 2 <= 200 * 1024;
+    return (size_t)kStages * kStageBytes + 64 + (size_t)kSplit * Lpad * 2 <= 200 * 1024;
 }
 
 cudaError_t launch_fields_tc(const JobDev* jobs_dev, const int4* tiles, int ntiles, int any_tab_smem_Lpad,
