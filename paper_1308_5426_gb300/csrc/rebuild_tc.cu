@@ -43,7 +43,7 @@ constexpr int kAccHi = kAcc - 1;     // rotating accumulators of the hi parts; t
 constexpr int kHank = kTileM / 8 + kChunk / 8 - 1;  // distinct core matrices of an A tile (Hankel form)
 constexpr int kTileBytes = kHank * 128;            // 2944 B per A tile of one split
 constexpr int kTileBytesB = kTileN * kChunk * 2; // 8 KB per 64 x 64 BF16 B tile
-constexpr int kGB = kTileN / 8;      // row groups of the B tile
+constexpr int kGB = kTileN / 8;      // row groups of the B tile (one per build warp)
 constexpr int kSplit = 3;
 constexpr int kStageBytes = kSplit * kTileBytes + kTileBytesB;  // one stage: three A tiles + the B tile
 constexpr int kStages = 2;           // chunk t + 1 is built while the MMAs of chunk t run
@@ -106,6 +106,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* 
     extern __shared__ __align__(1024) unsigned char smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int kWarps = kTcThreads / 32;
+    static_assert(kWarps == kGB, "one B row group per build warp");
 
     // stage b: A tiles at b * kStageBytes, then its B tile
     uint64_t* mbar = (uint64_t*)(smem + kStages * kStageBytes);  // one per stage
@@ -156,6 +157,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* 
     }
     const uint16_t* T = tab_smem ? tab : gtab;
     const int nchunks = (L + kChunk - 1) / kChunk;
+    // this thread's row of the B tile: n = n0 + 8 warp + rr (kGB == kWarps), fixed over the tile
+    const int nb = n0 + 8 * warp + rr;
+    const bool nvalid = nb < N;
+    const int brep = nvalid ? nb / q : 0, bx = nvalid ? nb - brep * q : 0;
+    const uint32_t* bsp = jb.spins + (size_t)brep * W;
+    const int bshift = 4 * (6 - kp);  // nibble of site k0 + 62 - 8 kc - kp within its word
 
     // chunk order: decreasing circular distance from the chunk holding the tile's
     // centre, so the large near-diagonal couplings are added last and the many
@@ -169,11 +176,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* 
         const int b = t % kStages;
         unsigned char* tileA = smem + b * kStageBytes;
         unsigned char* tileB = tileA + kSplit * kTileBytes;
-        // the MMAs that last read this stage (chunk t - kStages) must be done
+        // the MMAs that last read this stage (chunk t - kStages) must be done:
+        // warp 0 waits, the barrier tells the others
         if (pending[b]) {
-            if (!mbar_wait(smem_u32(mbar + b), parity[b])) ok = false;
+            if (warp == 0 && !mbar_wait(smem_u32(mbar + b), parity[b])) ok = false;
             parity[b] ^= 1u;
             pending[b] = 0;
+            if (!__syncthreads_and(ok)) {
+                ok = false;
+                break;
+            }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         }
         // The chunk's K sites are taken in reverse, k = k0 + 63 - k', so A[i][k'] =
@@ -193,17 +205,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* 
         }
         // B tile: row n = (replica, state), X = 1 where the replica's spin at site
         // k = k0 + 63 - k' is that state (K reversed as for A)
-        for (int cm = warp; cm < kGB * (kChunk / 8); cm += kWarps) {
-            const int g = cm % kGB, kc = cm / kGB;
-            const int n = n0 + 8 * g + rr;
+        // (warp w holds row group w: the core matrices (w, kc), kc = 0..7; spin word
+        // k0 / 8 + 7 - kc holds the sites of K group kc)
+#pragma unroll
+        for (int kc = 0; kc < kChunk / 8; ++kc) {
             const int ka = k0 + (kChunk - 1) - (8 * kc + kp);  // site of k' = 8 kc + kp; k' + 1 is ka - 1
-            const uint32_t off = (uint32_t)((kc * kGB + g) * 128 + rr * 16 + kp * 2);
+            const uint32_t off = (uint32_t)((kc * kGB + warp) * 128 + rr * 16 + kp * 2);
             uint32_t v = 0;
-            if (n < N && ka - 1 < L) {
-                const int rep = n / q, x = n - rep * q;
-                const uint32_t word = jb.spins[(size_t)rep * W + ((ka - 1) >> 3)] >> (4 * ((ka - 1) & 7));
-                if (ka < L && (int)((word >> 4) & 15u) == x) v |= bf16_one();  // ka odd: same word, next nibble
-                if ((int)(word & 15u) == x) v |= (uint32_t)bf16_one() << 16;
+            if (nvalid && ka - 1 < L) {
+                const uint32_t word = bsp[(k0 >> 3) + 7 - kc] >> bshift;
+                if (ka < L && (int)((word >> 4) & 15u) == bx) v |= bf16_one();  // ka odd: same word, next nibble
+                if ((int)(word & 15u) == bx) v |= (uint32_t)bf16_one() << 16;
             }
             *(uint32_t*)(tileB + off) = v;
         }
@@ -242,7 +254,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* 
     // all of the tile's MMAs done before its accumulators are read
     for (int b = 0; b < kStages; ++b)
         if (pending[b]) {
-            if (!mbar_wait(smem_u32(mbar + b), parity[b])) ok = false;
+            if (warp == 0 && !mbar_wait(smem_u32(mbar + b), parity[b])) ok = false;
             parity[b] ^= 1u;
             pending[b] = 0;
         }
@@ -300,8 +312,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* 
     }  // tiles
     // no MMA may still write tensor memory when it is freed (after an expired
     // wait, give the outstanding commits a bounded chance to land)
-    for (int b = 0; b < kStages; ++b)
-        if (pending[b]) mbar_wait(smem_u32(mbar + b), parity[b]);
+    if (warp == 0)
+        for (int b = 0; b < kStages; ++b)
+            if (pending[b]) mbar_wait(smem_u32(mbar + b), parity[b]);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
