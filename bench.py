@@ -175,6 +175,15 @@ def profiled_traffic():
     return None
 
 
+def rf_fits_shape(L, q):
+    """Whether the automatic FP32 sweep of an (L, q) chain keeps its fields in
+    registers (the library's register configurations)."""
+    for maxL, maxq in ((224, 16), (448, 16), (1120, 16), (2400, 8), (4320, 8), (7680, 5), (12480, 3), (16800, 2)):
+        if L <= maxL and q <= maxq:
+            return True
+    return False
+
+
 def alu_peak(kind, sm_max_mhz):
     """ALU peaks from unit counts and the maximum SM clock: 152 SMs; FP32: 128
     lanes/clk/SM; FP64: the nominal 1.25 TFLOP/s of GB300 is 2 FMA/clk/SM at
@@ -578,10 +587,17 @@ def main():
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_adds / 1e12, "unit": "TFLOP/s",
             "frac": achieved / peak_adds, "traffic": traffic,
             "peak_measured_probe": measured / 1e12, "frac_of_measured_probe": achieved / measured,
-            "kernel": "sweep_kernel<%s>" % ("double" if prec == "fp64" else "float"),
+            "kernel": ("sweep_kernel<double> (fields in shared memory)" if prec == "fp64" else
+                       "sweep_rf_kernel (FP32 fields in registers)" if rf_fits_shape(L, specs[0].q) else
+                       "sweep_kernel<float> (FP32 fields in shared or global memory)"),
             "work": "A*2L %s adds per attempt, A=%.4f measured; %d attempts per launch" % (prec, A, att_launch),
             "peak_source": "unit counts x max SM clock (2 FP64 / 128 FP32 add lanes per SM per clock, 152 SMs)",
             "sweep_ms_avg": sweep_avg_s * 1e3}
+    nsms = torch.cuda.get_device_properties(dev).multi_processor_count
+    if att_launch // L < nsms:  # fewer slots than SMs: also against the SMs the slots occupy
+        occ = (att_launch // L) / nsms
+        roof["frac_of_occupied_sms"] = achieved / (peak_adds * occ)
+        roof["occupied_sms"] = att_launch // L
 
     extra = {}
     if args.workload == "chains" and not args.no_fp32_compare and prec == "fp64":
