@@ -168,11 +168,31 @@ __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* 
     // centre, so the large near-diagonal couplings are added last and the many
     // small far-field sums accumulate while the accumulators are still small
     const int cc = ((m0 + kTileM / 2) / kChunk) % nchunks;
-    for (int t = 0; t < nchunks; ++t) {
+    auto chunk_of = [&](int t) {
         const int kk = nchunks - 1 - t;  // rank in increasing distance: 0, +1, -1, +2, -2, ...
         const int o = kk == 0 ? 0 : ((kk & 1) ? (kk + 1) / 2 : -(kk / 2));
-        const int c = ((cc + o) % nchunks + nchunks) % nchunks;
+        int c = cc + o;  // |o| <= nchunks / 2
+        c += c < 0 ? nchunks : 0;
+        c -= c >= nchunks ? nchunks : 0;
+        return c;
+    };
+    // the spin words of this thread's B row for a chunk (word 8 c + 7 - kc holds K group kc)
+    uint32_t wnext[kChunk / 8];
+    auto load_words = [&](int c) {
+#pragma unroll
+        for (int kc = 0; kc < kChunk / 8; ++kc) {
+            const int wi = 8 * c + 7 - kc;
+            wnext[kc] = (nvalid && wi < W) ? bsp[wi] : 0u;
+        }
+    };
+    load_words(chunk_of(0));
+    for (int t = 0; t < nchunks; ++t) {
+        const int c = chunk_of(t);
         const int k0 = c * kChunk;
+        uint32_t words[kChunk / 8];
+#pragma unroll
+        for (int kc = 0; kc < kChunk / 8; ++kc) words[kc] = wnext[kc];
+        if (t + 1 < nchunks) load_words(chunk_of(t + 1));  // in flight during this chunk
         const int b = t % kStages;
         unsigned char* tileA = smem + b * kStageBytes;
         unsigned char* tileB = tileA + kSplit * kTileBytes;
@@ -213,7 +233,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* 
             const uint32_t off = (uint32_t)((kc * kGB + warp) * 128 + rr * 16 + kp * 2);
             uint32_t v = 0;
             if (nvalid && ka - 1 < L) {
-                const uint32_t word = bsp[(k0 >> 3) + 7 - kc] >> bshift;
+                const uint32_t word = words[kc] >> bshift;
                 if (ka < L && (int)((word >> 4) & 15u) == bx) v |= bf16_one();  // ka odd: same word, next nibble
                 if ((int)(word & 15u) == bx) v |= (uint32_t)bf16_one() << 16;
             }
