@@ -70,6 +70,7 @@ struct potts_lr {
     double* pinned;               // 2R doubles of pinned host memory for measure
     int4* dtiles;                 // FP32: tensor-core rebuild tiles of this job (job index 0)
     int ntiles;
+    int tc_tn;                    // their width (64 or 128 columns)
     SweepSched sched;             // placement of the R slots on the SMs
     bool direct;                  // sweeps by the direct O(L) sum: fields are rebuilt on demand
 };
@@ -91,6 +92,7 @@ struct potts_lr_batch {
     std::vector<int> fp32_jobs;  // jobs that need the conditional rebuild
     int4* dtc_tiles;             // their rebuild tiles (job index into djobs)
     int ntc_tiles;
+    int tc_tn;                   // tile width (64 or 128 columns)
     int tc_tab_Lpad;             // largest staged split table among them
     int2* dfp_work;              // (job, slot) of their slots, for the energy re-anchor
     int nfp_work;
@@ -148,7 +150,7 @@ cudaError_t rebuild_launch(const potts_lr_t* h, const JobDev* job_dev, int cond,
 {
     cudaError_t e;
     if (h->precision == POTTS_LR_FP32)
-        e = launch_fields_tc(job_dev, h->dtiles, h->ntiles, h->hj.tc_tab_smem ? h->Lpad : 0, cond, st);
+        e = launch_fields_tc(job_dev, h->dtiles, h->ntiles, h->hj.tc_tab_smem ? h->Lpad : 0, cond, h->tc_tn, st);
     else
         e = launch_fields_direct(job_dev, h->L, h->R, 0, cond, h->direct_smem, st);
     if (e != cudaSuccess) return e;
@@ -344,7 +346,8 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
     const size_t o_job = take(sizeof(JobDev)), o_work = take((size_t)R * sizeof(int2));
     const size_t o_split = take(3 * Lp * 2), o_status = take(4), o_sched = take(8), o_drift = take(8);
     std::vector<int4> tiles;
-    if (h->precision == POTTS_LR_FP32) tc_tiles(0, L, q, R, tiles);
+    h->tc_tn = tc_tile_width(tc_tile_count(L, q, R, 64), tc_tile_count(L, q, R, 128), device_sm_count());
+    if (h->precision == POTTS_LR_FP32) tc_tiles(0, L, q, R, h->tc_tn, tiles);
     const size_t o_tiles = take(tiles.size() * sizeof(int4) + 16);
     const int nsm = device_sm_count();
     const size_t o_plan = take(sweep_sched_bytes(R, nsm));
@@ -789,9 +792,15 @@ int potts_lr_batch_create(potts_lr_t* const* jobs, int n, void* cuda_stream, pot
     b->nmeas = (int)mwork.size();
     std::vector<int4> btiles;
     std::vector<int2> fwork;
+    long long t64 = 0, t128 = 0;
+    for (int i : b->fp32_jobs) {
+        t64 += tc_tile_count(jobs[i]->L, jobs[i]->q, jobs[i]->R, 64);
+        t128 += tc_tile_count(jobs[i]->L, jobs[i]->q, jobs[i]->R, 128);
+    }
+    b->tc_tn = tc_tile_width(t64, t128, device_sm_count());
     for (int i : b->fp32_jobs) {
         const potts_lr_t* h = jobs[i];
-        tc_tiles(i, h->L, h->q, h->R, btiles);
+        tc_tiles(i, h->L, h->q, h->R, b->tc_tn, btiles);
         for (int t = 0; t < h->R; ++t) fwork.push_back(make_int2(i, t));
         if (h->hj.tc_tab_smem) b->tc_tab_Lpad = std::max(b->tc_tab_Lpad, h->Lpad);
         b->fp_meas_smem = std::max(b->fp_meas_smem, h->measure_smem);
@@ -870,7 +879,8 @@ static cudaError_t batch_enqueue_sweeps(potts_lr_batch_t* b)
     if (b->fp32_jobs.empty()) return cudaSuccess;
     // the rebuilds that fall due, for all FP32 jobs at once: tensor-core fields,
     // energy re-anchor, schedule update
-    if ((e = launch_fields_tc(b->djobs, b->dtc_tiles, b->ntc_tiles, b->tc_tab_Lpad, 1, b->stream)) != cudaSuccess)
+    if ((e = launch_fields_tc(b->djobs, b->dtc_tiles, b->ntc_tiles, b->tc_tab_Lpad, 1, b->tc_tn, b->stream)) !=
+        cudaSuccess)
         return e;
     if ((e = launch_measure(b->djobs, b->dfp_work, b->nfp_work, 1, 1, b->fp_meas_smem, b->stream)) != cudaSuccess)
         return e;

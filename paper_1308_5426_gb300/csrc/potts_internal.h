@@ -107,12 +107,15 @@ cudaError_t launch_measure(const JobDev* jobs_dev, const int2* work, int nwork, 
 cudaError_t launch_fields_direct(const JobDev* job_dev, int L, int R, int mode, int cond, size_t smem_bytes,
                                  cudaStream_t st);
 // FP32 mode: the split-BF16 tensor-core rebuild H = C . onehot(S) over a tile
-// table of (job index, first row, first column) 128 x 64 output tiles (any
+// table of (job index, first row, first column) 128 x tn output tiles (any
 // mix of jobs); max_tab_Lpad: the largest Lpad among jobs that stage their
 // split table in shared memory (0 if none).  Persistent: one CTA per SM.
+// tn: output tile width, 64 or 128 (tc_tile_width picks it from the tile counts).
 cudaError_t launch_fields_tc(const JobDev* jobs_dev, const int4* tiles, int ntiles, int max_tab_Lpad, int cond,
-                             cudaStream_t st);
-void tc_tiles(int job, int L, int q, int R, std::vector<int4>& out);
+                             int tn, cudaStream_t st);
+void tc_tiles(int job, int L, int q, int R, int tn, std::vector<int4>& out);
+long long tc_tile_count(int L, int q, int R, int tn);
+int tc_tile_width(long long tiles64, long long tiles128, int nsm);
 int tc_table_in_smem(int Lpad);
 // after a rebuild: adapt the FP32 rebuild interval of jobs[idx[i]] to the
 // measured drift (one thread per job)

@@ -7,17 +7,17 @@
 // tcgen05.mma kind::f16 with BF16 operands and FP32 accumulation in tensor
 // memory.  X is exact in BF16 (0 or 1); C is carried as three BF16 parts
 // hi + mid + lo of the FP64 J* (representation error ~2^-25 J*), each part one
-// MMA per K-step.  One CTA computes a 128 x 64 tile of H over
+// MMA per K-step.  One CTA computes a 128 x TN tile of H (TN = 64 or 128) over
 // all of K in chunks of 64 sites: eight warps build the operand tiles in
 // shared memory from the split table and the packed spins, one thread issues
 // the 12 MMAs of the chunk (4 K-steps x 3 parts) and commits them to the
 // mbarrier of the chunk's stage; two stages alternate, so chunk t + 1 is
 // built while the MMAs of chunk t run.  The tensor core's FP32 accumulation rounds every MMA's sum into
 // the accumulator, so the accumulation chains are kept short: the hi parts of
-// successive chunks rotate over seven accumulators, and the small mid + lo
-// parts go to an eighth of their own (their rounding is then relative to their
-// own small size).  8 accumulators x 64 columns = 512 TMEM columns; the
-// epilogue adds them in FP64 and stores FP32 fields.
+// successive chunks rotate over 512 / TN - 1 accumulators (seven or three),
+// and the small mid + lo parts go to one of their own (their rounding is then
+// relative to their own small size); together they fill the 512 TMEM columns.
+// The epilogue adds them in FP64 and stores FP32 fields.
 //
 // Operand layout (both K-major, no swizzle): 8-row x 16-byte core matrices.
 // B: core matrix (row group g, K group c) at byte (c G + g) 128 (leading (K)
@@ -36,18 +36,22 @@ namespace {
 
 constexpr int kTcThreads = 256;      // 8 warps build the tiles; warps w and w + 4 share TMEM lanes 32 (w % 4) ..
 constexpr int kTileM = 128;
-constexpr int kTileN = 64;
+
 constexpr int kChunk = 64;           // K sites per chunk
-constexpr int kAcc = 8;              // accumulators (kAcc * kTileN = 512 TMEM columns)
-constexpr int kAccHi = kAcc - 1;     // rotating accumulators of the hi parts; the last takes mid + lo
 constexpr int kHank = kTileM / 8 + kChunk / 8 - 1;  // distinct core matrices of an A tile (Hankel form)
 constexpr int kTileBytes = kHank * 128;            // 2944 B per A tile of one split
-constexpr int kTileBytesB = kTileN * kChunk * 2; // 8 KB per 64 x 64 BF16 B tile
-constexpr int kGB = kTileN / 8;      // row groups of the B tile (one per build warp)
 constexpr int kSplit = 3;
-constexpr int kStageBytes = kSplit * kTileBytes + kTileBytesB;  // one stage: three A tiles + the B tile
+constexpr int kTmemCols = 512;       // all of the SM's tensor memory: accumulators of TN columns each
+// per tile width TN (64 or 128 output columns): accumulators, B tile, stage
+template <int TN>
+struct TcShape {
+    static constexpr int kAcc = kTmemCols / TN;      // 8 or 4 accumulators
+    static constexpr int kAccHi = kAcc - 1;          // rotating accumulators of the hi parts; the last takes mid + lo
+    static constexpr int kTileBytesB = TN * kChunk * 2;  // TN x 64 BF16 B tile
+    static constexpr int kGB = TN / 8;               // row groups of the B tile
+    static constexpr int kStageBytes = kSplit * kTileBytes + kTileBytesB;  // three A tiles + the B tile
+};
 constexpr int kStages = 2;           // chunk t + 1 is built while the MMAs of chunk t run
-constexpr uint32_t kTmemCols = kAcc * kTileN;
 constexpr long long kWaitLimit = 1ll << 26;  // bounded mbarrier wait (iterations)
 constexpr size_t kTcMinSmem = 120 * 1024;   // forces one CTA per SM (owner of all 512 columns)
 
@@ -99,14 +103,20 @@ __device__ __forceinline__ int circ(int d, int L)
     return (d < 0 || d >= L) ? 0 : d;
 }
 
+template <int TN>
 __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* __restrict__ jobs,
                                                                   const int4* __restrict__ tiles, int ntiles,
                                                                   int cond)
 {
+    constexpr int kTileN = TN;
+    constexpr int kAcc = TcShape<TN>::kAcc, kAccHi = TcShape<TN>::kAccHi;
+    constexpr int kGB = TcShape<TN>::kGB, kStageBytes = TcShape<TN>::kStageBytes;
+    constexpr int kHB = kGB / (kTcThreads / 32);  // B row groups per build warp
+    static_assert(kAcc * TN == kTmemCols, "accumulators fill the tensor memory");
     extern __shared__ __align__(1024) unsigned char smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int kWarps = kTcThreads / 32;
-    static_assert(kWarps == kGB, "one B row group per build warp");
+    static_assert(kHB * kWarps == kGB, "whole B row groups per build warp");
 
     // stage b: A tiles at b * kStageBytes, then its B tile
     uint64_t* mbar = (uint64_t*)(smem + kStages * kStageBytes);  // one per stage
@@ -157,11 +167,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* 
     }
     const uint16_t* T = tab_smem ? tab : gtab;
     const int nchunks = (L + kChunk - 1) / kChunk;
-    // this thread's row of the B tile: n = n0 + 8 warp + rr (kGB == kWarps), fixed over the tile
-    const int nb = n0 + 8 * warp + rr;
-    const bool nvalid = nb < N;
-    const int brep = nvalid ? nb / q : 0, bx = nvalid ? nb - brep * q : 0;
-    const uint32_t* bsp = jb.spins + (size_t)brep * W;
+    // this thread's rows of the B tile: n = n0 + 8 (warp + 8 hb) + rr, hb < kHB, fixed over the tile
+    int bx[kHB];
+    bool nvalid[kHB];
+    const uint32_t* bsp[kHB];
+#pragma unroll
+    for (int hb = 0; hb < kHB; ++hb) {
+        const int nb = n0 + 8 * (warp + kWarps * hb) + rr;
+        nvalid[hb] = nb < N;
+        const int brep = nvalid[hb] ? nb / q : 0;
+        bx[hb] = nvalid[hb] ? nb - brep * q : 0;
+        bsp[hb] = jb.spins + (size_t)brep * W;
+    }
     const int bshift = 4 * (6 - kp);  // nibble of site k0 + 62 - 8 kc - kp within its word
 
     // chunk order: decreasing circular distance from the chunk holding the tile's
@@ -176,22 +193,26 @@ __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* 
         c -= c >= nchunks ? nchunks : 0;
         return c;
     };
-    // the spin words of this thread's B row for a chunk (word 8 c + 7 - kc holds K group kc)
-    uint32_t wnext[kChunk / 8];
+    // the spin words of this thread's B rows for a chunk (word 8 c + 7 - kc holds K group kc)
+    uint32_t wnext[kHB][kChunk / 8];
     auto load_words = [&](int c) {
 #pragma unroll
-        for (int kc = 0; kc < kChunk / 8; ++kc) {
-            const int wi = 8 * c + 7 - kc;
-            wnext[kc] = (nvalid && wi < W) ? bsp[wi] : 0u;
-        }
+        for (int hb = 0; hb < kHB; ++hb)
+#pragma unroll
+            for (int kc = 0; kc < kChunk / 8; ++kc) {
+                const int wi = 8 * c + 7 - kc;
+                wnext[hb][kc] = (nvalid[hb] && wi < W) ? bsp[hb][wi] : 0u;
+            }
     };
     load_words(chunk_of(0));
     for (int t = 0; t < nchunks; ++t) {
         const int c = chunk_of(t);
         const int k0 = c * kChunk;
-        uint32_t words[kChunk / 8];
+        uint32_t words[kHB][kChunk / 8];
 #pragma unroll
-        for (int kc = 0; kc < kChunk / 8; ++kc) words[kc] = wnext[kc];
+        for (int hb = 0; hb < kHB; ++hb)
+#pragma unroll
+            for (int kc = 0; kc < kChunk / 8; ++kc) words[hb][kc] = wnext[hb][kc];
         if (t + 1 < nchunks) load_words(chunk_of(t + 1));  // in flight during this chunk
         const int b = t % kStages;
         unsigned char* tileA = smem + b * kStageBytes;
@@ -225,20 +246,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* 
         }
         // B tile: row n = (replica, state), X = 1 where the replica's spin at site
         // k = k0 + 63 - k' is that state (K reversed as for A)
-        // (warp w holds row group w: the core matrices (w, kc), kc = 0..7; spin word
-        // k0 / 8 + 7 - kc holds the sites of K group kc)
+        // (warp w holds row groups w + 8 hb: the core matrices (g, kc), kc = 0..7;
+        // spin word k0 / 8 + 7 - kc holds the sites of K group kc)
 #pragma unroll
-        for (int kc = 0; kc < kChunk / 8; ++kc) {
-            const int ka = k0 + (kChunk - 1) - (8 * kc + kp);  // site of k' = 8 kc + kp; k' + 1 is ka - 1
-            const uint32_t off = (uint32_t)((kc * kGB + warp) * 128 + rr * 16 + kp * 2);
-            uint32_t v = 0;
-            if (nvalid && ka - 1 < L) {
-                const uint32_t word = words[kc] >> bshift;
-                if (ka < L && (int)((word >> 4) & 15u) == bx) v |= bf16_one();  // ka odd: same word, next nibble
-                if ((int)(word & 15u) == bx) v |= (uint32_t)bf16_one() << 16;
+        for (int hb = 0; hb < kHB; ++hb)
+#pragma unroll
+            for (int kc = 0; kc < kChunk / 8; ++kc) {
+                const int ka = k0 + (kChunk - 1) - (8 * kc + kp);  // site of k' = 8 kc + kp; k' + 1 is ka - 1
+                const uint32_t off = (uint32_t)((kc * kGB + warp + kWarps * hb) * 128 + rr * 16 + kp * 2);
+                uint32_t v = 0;
+                if (nvalid[hb] && ka - 1 < L) {
+                    const uint32_t word = words[hb][kc] >> bshift;
+                    if (ka < L && (int)((word >> 4) & 15u) == bx[hb]) v |= bf16_one();  // next nibble: site ka
+                    if ((int)(word & 15u) == bx[hb]) v |= (uint32_t)bf16_one() << 16;
+                }
+                *(uint32_t*)(tileB + off) = v;
             }
-            *(uint32_t*)(tileB + off) = v;
-        }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         if (!__syncthreads_and(ok)) {
             ok = false;
@@ -345,34 +368,51 @@ __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* 
 
 size_t tc_smem_bytes(int Lpad, int tab_smem)
 {
-    size_t b = (size_t)kStages * kStageBytes + 64 + (tab_smem ? (size_t)kSplit * Lpad * 2 : 0);
+    // sized for the wider tile, so either width fits
+    size_t b = (size_t)kStages * TcShape<128>::kStageBytes + 64 + (tab_smem ? (size_t)kSplit * Lpad * 2 : 0);
     b = (b + 127) & ~(size_t)127;
     return b < kTcMinSmem ? kTcMinSmem : b;
 }
 
 int tc_table_in_smem(int Lpad)
 {
-    return (size_t)kStages * kStageBytes + 64 + (size_t)kSplit * Lpad * 2 <= 200 * 1024;
+    return (size_t)kStages * TcShape<128>::kStageBytes + 64 + (size_t)kSplit * Lpad * 2 <= 200 * 1024;
+}
+
+int tc_tile_width(long long tiles64, long long tiles128, int nsm)
+{
+    // persistent CTAs walk the tiles; a 128-wide tile costs about 1.4 times a
+    // 64-wide one (half the MMA instructions per output), so the wider tile
+    // pays unless it leaves the SMs idler
+    if (nsm <= 0) return 64;
+    const double w64 = (double)((tiles64 + nsm - 1) / nsm), w128 = (double)((tiles128 + nsm - 1) / nsm);
+    return 1.4 * w128 < w64 ? 128 : 64;
 }
 
 cudaError_t launch_fields_tc(const JobDev* jobs_dev, const int4* tiles, int ntiles, int any_tab_smem_Lpad,
-                             int cond, cudaStream_t st)
+                             int cond, int tn, cudaStream_t st)
 {
     if (ntiles <= 0) return cudaSuccess;
     const size_t smem = tc_smem_bytes(any_tab_smem_Lpad, any_tab_smem_Lpad > 0);
-    cudaError_t e = cudaFuncSetAttribute(fields_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto k = tn == 128 ? fields_tc_kernel<128> : fields_tc_kernel<64>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 148;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int grid = ntiles < sms ? ntiles : sms;  // persistent: one CTA per SM walks the tile table
-    fields_tc_kernel<<<grid, kTcThreads, smem, st>>>(jobs_dev, tiles, ntiles, cond);
+    k<<<grid, kTcThreads, smem, st>>>(jobs_dev, tiles, ntiles, cond);
     return cudaGetLastError();
 }
 
-void tc_tiles(int job, int L, int q, int R, std::vector<int4>& out)
+void tc_tiles(int job, int L, int q, int R, int tn, std::vector<int4>& out)
 {
     for (int m = 0; m < L; m += kTileM)
-        for (int n = 0; n < q * R; n += kTileN) out.push_back(make_int4(job, m, n, 0));
+        for (int n = 0; n < q * R; n += tn) out.push_back(make_int4(job, m, n, 0));
+}
+
+long long tc_tile_count(int L, int q, int R, int tn)
+{
+    return (long long)((L + kTileM - 1) / kTileM) * ((q * R + tn - 1) / tn);
 }
 
 }  // namespace plr
