@@ -50,6 +50,32 @@ def parse():
     return ap.parse_args()
 
 
+def rank_max(x, world, device):
+    """The largest x over the ranks (the job's time is its slowest rank's)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_min(x, world, device):
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MIN)
+    return float(t.item())
+
+
+def job_rate(total_attempts, slowest_ms):
+    """Whole-job attempts/s: the attempts of all ranks over the slowest rank's time."""
+    return total_attempts / (slowest_ms / 1e3)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -565,13 +591,8 @@ def main():
     clocks.start()
     res = timed_device(plr, torch, specs, args.steps, args.warmup, dev)
     ck = clocks.stop()
-    step_ms = res["step_ms"]
-    if world > 1:
-        t = torch.tensor([step_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms = float(t.item())
-    total_att = world * args.steps * res["att_step"]
-    value = total_att / (step_ms / 1e3)
+    step_ms = rank_max(res["step_ms"], world, dev)
+    value = job_rate(world * args.steps * res["att_step"], step_ms)
 
     # roofline of the sweep kernel (the dominant kernel)
     prec = specs[0].precision
@@ -625,10 +646,8 @@ def main():
         extra["serving"] = serving_run(plr, torch, dev, args.serve_jobs, args.serve_sweeps)
 
     e2e = timed_e2e(plr, torch, specs, max(3, args.steps // 3), 1, dev)
-    if world > 1:
-        t = torch.tensor([e2e["value"]], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MIN)
-        e2e["value"] = float(t.item()) * world
+    if world > 1:  # every rank runs the same amount of work: the slowest rank's rate, times the ranks
+        e2e["value"] = rank_min(e2e["value"], world, dev) * world
 
     if rank == 0:
         cpu = cpu_baseline(specs, args.cpu_seconds) if world == 1 else None
