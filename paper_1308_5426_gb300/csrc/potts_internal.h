@@ -19,7 +19,7 @@ constexpr int kMaxL = 65536;        // largest L (16-bit positions in the direct
 // "slot" belong to a temperature.  map[slot] = replica currently at that slot.
 struct JobDev {
     int L, q, Lpad, W, R, c, precision;
-    int recompute_every;  // FP32 mode: rebuild fields after sweeps n with (n+1) % K == 0
+    int recompute_every;  // FP32 mode: longest interval K between field rebuilds (0 = on request only)
     int h_smem, j_smem;   // sweep kernel: fields / coupling table staged in shared memory
     int rf;               // FP32 mode: register-resident sweep configuration (0 = none, 1..8)
     int random_sites;     // direct sweep: attempt m at a site drawn from Philox counter (m, slot, sweep, 3)
@@ -88,7 +88,7 @@ cudaError_t launch_sweep_plan(const JobDev* jobs_dev, const int2* work, const Sw
 void jstar_table(int L, double sigma, double* out);
 
 // ---- launchers (each returns the cudaError_t of the launch) ----
-// work[i] = {job index, slot}; one CTA per work item
+// work[i] = {job index, slot}
 cudaError_t launch_init_spins(const JobDev* jobs_dev, int job, int L, int W, int R, cudaStream_t st);
 // the kernel variant (precision, fields in smem, table in smem) is uniform per launch
 // sched: placement buffers for this work list (nullptr: one CTA per item, in order)
@@ -96,8 +96,9 @@ cudaError_t launch_sweep(const JobDev* jobs_dev, const int2* work, int nwork, in
                          int h_smem, int j_smem, size_t smem_bytes, const SweepSched* sched, cudaStream_t st);
 cudaError_t launch_exchange(const JobDev* jobs_dev, int njobs, cudaStream_t st);
 // "cond" arguments: when nonzero the kernel does nothing unless the job's
-// sweep counter is a positive multiple of its recompute_every (a rebuild that
-// is due), which lets a captured CUDA graph carry the rebuild every step.
+// rebuild is due (rebuild_due: its sweep counter has reached the next rebuild
+// of its schedule), which lets a captured CUDA graph carry the rebuild every
+// step.
 // anchor: 0 = measure only, 1 = measure and re-anchor the running energy.
 cudaError_t launch_measure(const JobDev* jobs_dev, const int2* work, int nwork, int anchor, int cond,
                            size_t smem_bytes, cudaStream_t st);
