@@ -87,8 +87,11 @@ struct potts_lr_batch {
         int nwork;
         size_t smem;
         SweepSched sched;
+        cudaStream_t stream;  // its own stream when the batch has several groups
+        cudaEvent_t done;     // recorded on it after the group's sweep
     };
     std::vector<Group> groups;
+    cudaEvent_t fork;             // the batch stream's point where the groups' sweeps start
     std::vector<int> fp32_jobs;  // jobs that need the conditional rebuild
     int4* dtc_tiles;             // their rebuild tiles (job index into djobs)
     int ntc_tiles;
@@ -733,6 +736,11 @@ void potts_lr_batch_destroy(potts_lr_batch_t* b)
     if (b->stream) cudaStreamSynchronize(b->stream);
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->ev) cudaEventDestroy(b->ev);
+    if (b->fork) cudaEventDestroy(b->fork);
+    for (auto& g : b->groups) {
+        if (g.done) cudaEventDestroy(g.done);
+        if (g.stream) cudaStreamDestroy(g.stream);
+    }
     if (b->arena) cudaFree(b->arena);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;
@@ -844,10 +852,19 @@ int potts_lr_batch_create(potts_lr_t* const* jobs, int n, void* cuda_stream, pot
         g.nwork = (int)kv.second.size();
         g.smem = smem[kv.first];
         sweep_sched_carve((char*)b->arena + osch[kv.first], g.nwork, nsm, &g.sched);
+        g.stream = nullptr;
+        g.done = nullptr;
         b->groups.push_back(g);
         e = cudaMemcpyAsync(g.dwork, kv.second.data(), kv.second.size() * sizeof(int2), cudaMemcpyHostToDevice,
                             b->stream);
         if (e != cudaSuccess) break;
+    }
+    if (e == cudaSuccess && b->groups.size() > 1) {
+        e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+        for (auto& g : b->groups) {
+            if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming);
+        }
     }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->djobs, hjobs.data(), n * sizeof(JobDev), cudaMemcpyHostToDevice, b->stream);
@@ -873,9 +890,25 @@ int potts_lr_batch_create(potts_lr_t* const* jobs, int n, void* cuda_stream, pot
 static cudaError_t batch_enqueue_sweeps(potts_lr_batch_t* b)
 {
     cudaError_t e;
-    for (const auto& g : b->groups)
+    if (b->groups.size() == 1) {
+        const auto& g = b->groups[0];
         if ((e = launch_variant(g.key, b->djobs, g.dwork, g.nwork, 1, g.smem, &g.sched, b->stream)) != cudaSuccess)
             return e;
+    } else {
+        // the kernel-variant groups hold different jobs: sweep them concurrently,
+        // each on its own stream (fork / join through events, which a graph
+        // capture turns into parallel branches), so that groups smaller than
+        // the GPU share it instead of running one after another
+        if ((e = cudaEventRecord(b->fork, b->stream)) != cudaSuccess) return e;
+        for (const auto& g : b->groups) {
+            if ((e = cudaStreamWaitEvent(g.stream, b->fork, 0)) != cudaSuccess) return e;
+            if ((e = launch_variant(g.key, b->djobs, g.dwork, g.nwork, 1, g.smem, &g.sched, g.stream)) != cudaSuccess)
+                return e;
+            if ((e = cudaEventRecord(g.done, g.stream)) != cudaSuccess) return e;
+        }
+        for (const auto& g : b->groups)
+            if ((e = cudaStreamWaitEvent(b->stream, g.done, 0)) != cudaSuccess) return e;
+    }
     if (b->fp32_jobs.empty()) return cudaSuccess;
     // the rebuilds that fall due, for all FP32 jobs at once: tensor-core fields,
     // energy re-anchor, schedule update
