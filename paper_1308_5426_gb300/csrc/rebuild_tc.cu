@@ -8,9 +8,9 @@
 // memory.  X is exact in BF16 (0 or 1); C is carried as three BF16 parts
 // hi + mid + lo of the FP64 J* (representation error ~2^-25 J*), each part one
 // MMA per K-step.  One CTA computes a 128 x TN tile of H (TN = 64 or 128) over
-// all of K in chunks of 64 sites: eight warps build the operand tiles in
+// all of K in chunks of kChunk = 128 sites: eight warps build the operand tiles in
 // shared memory from the split table and the packed spins, one thread issues
-// the 12 MMAs of the chunk (4 K-steps x 3 parts) and commits them to the
+// the 24 MMAs of the chunk (8 K-steps x 3 parts) and commits them to the
 // mbarrier of the chunk's stage; two stages alternate, so chunk t + 1 is
 // built while the MMAs of chunk t run.  The tensor core's FP32 accumulation rounds every MMA's sum into
 // the accumulator, so the accumulation chains are kept short: the hi parts of
@@ -24,7 +24,7 @@
 // byte offset 128 G, stride (row-group) byte offset 128; K-step s at 256 G s).
 // A: the chunk's sites are taken in reverse order (as in B), which makes the
 // circulant tile Hankel: core matrix (g, c) = core matrix g + c of a strip of
-// 23, so both byte offsets are 128 and K-step s starts at 256 s.
+// 31, so both byte offsets are 128 and K-step s starts at 256 s.
 #include <cstdint>
 #include <vector>
 
@@ -37,9 +37,9 @@ namespace {
 constexpr int kTcThreads = 256;      // 8 warps build the tiles; warps w and w + 4 share TMEM lanes 32 (w % 4) ..
 constexpr int kTileM = 128;
 
-constexpr int kChunk = 64;           // K sites per chunk
+constexpr int kChunk = 128;          // K sites per chunk
 constexpr int kHank = kTileM / 8 + kChunk / 8 - 1;  // distinct core matrices of an A tile (Hankel form)
-constexpr int kTileBytes = kHank * 128;            // 2944 B per A tile of one split
+constexpr int kTileBytes = kHank * 128;            // 3968 B per A tile of one split
 constexpr int kSplit = 3;
 constexpr int kTmemCols = 512;       // all of the SM's tensor memory: accumulators of TN columns each
 // per tile width TN (64 or 128 output columns): accumulators, B tile, stage
@@ -47,7 +47,7 @@ template <int TN>
 struct TcShape {
     static constexpr int kAcc = kTmemCols / TN;      // 8 or 4 accumulators
     static constexpr int kAccHi = kAcc - 1;          // rotating accumulators of the hi parts; the last takes mid + lo
-    static constexpr int kTileBytesB = TN * kChunk * 2;  // TN x 64 BF16 B tile
+    static constexpr int kTileBytesB = TN * kChunk * 2;  // TN x kChunk BF16 B tile
     static constexpr int kGB = TN / 8;               // row groups of the B tile
     static constexpr int kStageBytes = kSplit * kTileBytes + kTileBytesB;  // three A tiles + the B tile
 };
@@ -94,7 +94,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
 
 __device__ __forceinline__ uint16_t bf16_one() { return 0x3F80u; }
 
-// (i - k) mod L for i < L + 128 and k < L + 64 (tile and chunk padding past L
+// (i - k) mod L for i < L + 128 and k < L + kChunk (tile and chunk padding past L
 // only meet zero operands, so any in-range index serves there)
 __device__ __forceinline__ int circ(int d, int L)
 {
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* 
         bx[hb] = nvalid[hb] ? nb - brep * q : 0;
         bsp[hb] = jb.spins + (size_t)brep * W;
     }
-    const int bshift = 4 * (6 - kp);  // nibble of site k0 + 62 - 8 kc - kp within its word
+    const int bshift = 4 * (6 - kp);  // nibble of site k0 + kChunk - 2 - 8 kc - kp within its word
 
     // chunk order: decreasing circular distance from the chunk holding the tile's
     // centre, so the large near-diagonal couplings are added last and the many
@@ -193,14 +193,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* 
         c -= c >= nchunks ? nchunks : 0;
         return c;
     };
-    // the spin words of this thread's B rows for a chunk (word 8 c + 7 - kc holds K group kc)
+    // the spin words of this thread's B rows for a chunk (word (kChunk / 8) (c + 1) - 1 - kc
+    // holds K group kc)
     uint32_t wnext[kHB][kChunk / 8];
     auto load_words = [&](int c) {
 #pragma unroll
         for (int hb = 0; hb < kHB; ++hb)
 #pragma unroll
             for (int kc = 0; kc < kChunk / 8; ++kc) {
-                const int wi = 8 * c + 7 - kc;
+                const int wi = (kChunk / 8) * (c + 1) - 1 - kc;
                 wnext[hb][kc] = (nvalid[hb] && wi < W) ? bsp[hb][wi] : 0u;
             }
     };
@@ -229,11 +230,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* 
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         }
-        // The chunk's K sites are taken in reverse, k = k0 + 63 - k', so A[i][k'] =
+        // The chunk's K sites are taken in reverse, k = k0 + kChunk - 1 - k', so A[i][k'] =
         // J*((i - k) mod L) depends on i + k' only: core matrix (g, c) is core
-        // matrix h = g + c of a Hankel strip of 23, which the MMA reads with
+        // matrix h = g + c of a Hankel strip of kHank = 31, which the MMA reads with
         // row-group and K-group strides both 128 bytes.  Element (rr, e) of
-        // core matrix h is J*((m0 - k0 - 63 + 8 h + rr + e) mod L).
+        // core matrix h is J*((m0 - k0 - kChunk + 1 + 8 h + rr + e) mod L).
         for (int h = warp; h < kHank; h += kWarps) {
             const int r0 = circ(m0 - k0 - (kChunk - 1) + 8 * h + rr + kp, L);
             const int r1 = r0 + 1 == L ? 0 : r0 + 1;
@@ -245,9 +246,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* 
             }
         }
         // B tile: row n = (replica, state), X = 1 where the replica's spin at site
-        // k = k0 + 63 - k' is that state (K reversed as for A)
-        // (warp w holds row groups w + 8 hb: the core matrices (g, kc), kc = 0..7;
-        // spin word k0 / 8 + 7 - kc holds the sites of K group kc)
+        // k = k0 + kChunk - 1 - k' is that state (K reversed as for A)
+        // (warp w holds row groups w + 8 hb: the core matrices (g, kc), kc < kChunk / 8;
+        // spin word (k0 + kChunk) / 8 - 1 - kc holds the sites of K group kc)
 #pragma unroll
         for (int hb = 0; hb < kHB; ++hb)
 #pragma unroll
