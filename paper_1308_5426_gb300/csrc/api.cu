@@ -71,6 +71,7 @@ struct potts_lr {
     int4* dtiles;                 // FP32: tensor-core rebuild tiles of this job (job index 0)
     int ntiles;
     int tc_tn;                    // their width (64 or 128 columns)
+    int onehot_blocks;            // FP32: grid width of the rebuild's one-hot kernel
     SweepSched sched;             // placement of the R slots on the SMs
     bool direct;                  // sweeps by the direct O(L) sum: fields are rebuilt on demand
 };
@@ -96,7 +97,7 @@ struct potts_lr_batch {
     int4* dtc_tiles;             // their rebuild tiles (job index into djobs)
     int ntc_tiles;
     int tc_tn;                   // tile width (64 or 128 columns)
-    int tc_tab_Lpad;             // largest staged split table among them
+    int onehot_blocks;           // grid width of their one-hot kernel (the largest job's)
     int2* dfp_work;              // (job, slot) of their slots, for the energy re-anchor
     int nfp_work;
     size_t fp_meas_smem;
@@ -153,7 +154,7 @@ cudaError_t rebuild_launch(const potts_lr_t* h, const JobDev* job_dev, int cond,
 {
     cudaError_t e;
     if (h->precision == POTTS_LR_FP32)
-        e = launch_fields_tc(job_dev, h->dtiles, h->ntiles, h->hj.tc_tab_smem ? h->Lpad : 0, cond, h->tc_tn, st);
+        e = launch_fields_tc(job_dev, nullptr, 1, h->onehot_blocks, h->dtiles, h->ntiles, cond, h->tc_tn, st);
     else
         e = launch_fields_direct(job_dev, h->L, h->R, 0, cond, h->direct_smem, st);
     if (e != cudaSuccess) return e;
@@ -313,6 +314,9 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
         split[h->Lpad + r] = mid;
         split[2 * (size_t)h->Lpad + r] = to_bf16((float)r2);
     }
+    // the same parts as the Hankel core matrices the rebuild copies (its A operand)
+    std::vector<uint16_t> hank;
+    if (h->precision == POTTS_LR_FP32) tc_hank_table(J, split.data(), h->Lpad, hank);
     std::vector<double> beta(R);
     for (int t = 0; t < R; ++t) beta[t] = 1.0 / temps[t];
     // first FP32 rebuild interval: short for long chains with few states (the
@@ -347,7 +351,9 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
     const size_t o_accf = take((size_t)R * 8), o_accs = take((size_t)R * 8), o_near = take(16);
     const size_t o_mE = take((size_t)R * 8), o_mM = take((size_t)R * 8), o_err = take(8);
     const size_t o_job = take(sizeof(JobDev)), o_work = take((size_t)R * sizeof(int2));
-    const size_t o_split = take(3 * Lp * 2), o_status = take(4), o_sched = take(8), o_drift = take(8);
+    const bool tc = h->precision == POTTS_LR_FP32;  // tensor-core rebuild operands
+    const size_t o_hank = take(tc ? tc_hank_bytes(L) : 0), o_xoh = take(tc ? tc_onehot_bytes(L, q, R) : 0);
+    const size_t o_status = take(4), o_sched = take(8), o_drift = take(8);
     std::vector<int4> tiles;
     h->tc_tn = tc_tile_width(tc_tile_count(L, q, R, 64), tc_tile_count(L, q, R, 128), device_sm_count());
     if (h->precision == POTTS_LR_FP32) tc_tiles(0, L, q, R, h->tc_tn, tiles);
@@ -394,8 +400,11 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
     j.meas_E = (double*)(base + o_mE);
     j.meas_M = (double*)(base + o_mM);
     j.err_bits = (unsigned long long*)(base + o_err);
-    j.Jsplit = (const uint16_t*)(base + o_split);
-    j.tc_tab_smem = tc_table_in_smem(h->Lpad);
+    j.Jhank = tc ? (const uint16_t*)(base + o_hank) : nullptr;
+    j.Xoh = tc ? (uint16_t*)(base + o_xoh) : nullptr;
+    j.hank_cores = (int)tc_hank_cores(L);
+    j.NG = tc_ng(q, R);
+    h->onehot_blocks = tc_onehot_blocks(L, q, R);
     j.status = (int*)(base + o_status);
     j.sched = (int*)(base + o_sched);
     h->dtiles = (int4*)(base + o_tiles);
@@ -453,7 +462,9 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
         if ((e = cudaMemcpyAsync(j.map, map.data(), (size_t)R * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
         if ((e = cudaMemcpyAsync(h->dj, &j, sizeof(JobDev), cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
         if ((e = cudaMemcpyAsync(h->dwork, work.data(), (size_t)R * sizeof(int2), cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
-        if ((e = cudaMemcpyAsync((void*)j.Jsplit, split.data(), 3 * Lp * 2, cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
+        if (tc && (e = cudaMemcpyAsync((void*)j.Jhank, hank.data(), hank.size() * 2, cudaMemcpyHostToDevice, st)) !=
+                      cudaSuccess)
+            break;
         if ((e = cudaMemcpyAsync(j.sched, sched0, 8, cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
         if (!tiles.empty() &&
             (e = cudaMemcpyAsync(h->dtiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice, st)) !=
@@ -810,7 +821,7 @@ int potts_lr_batch_create(potts_lr_t* const* jobs, int n, void* cuda_stream, pot
         const potts_lr_t* h = jobs[i];
         tc_tiles(i, h->L, h->q, h->R, b->tc_tn, btiles);
         for (int t = 0; t < h->R; ++t) fwork.push_back(make_int2(i, t));
-        if (h->hj.tc_tab_smem) b->tc_tab_Lpad = std::max(b->tc_tab_Lpad, h->Lpad);
+        b->onehot_blocks = std::max(b->onehot_blocks, h->onehot_blocks);
         b->fp_meas_smem = std::max(b->fp_meas_smem, h->measure_smem);
     }
     b->ntc_tiles = (int)btiles.size();
@@ -912,8 +923,8 @@ static cudaError_t batch_enqueue_sweeps(potts_lr_batch_t* b)
     if (b->fp32_jobs.empty()) return cudaSuccess;
     // the rebuilds that fall due, for all FP32 jobs at once: tensor-core fields,
     // energy re-anchor, schedule update
-    if ((e = launch_fields_tc(b->djobs, b->dtc_tiles, b->ntc_tiles, b->tc_tab_Lpad, 1, b->tc_tn, b->stream)) !=
-        cudaSuccess)
+    if ((e = launch_fields_tc(b->djobs, b->dfp_idx, (int)b->fp32_jobs.size(), b->onehot_blocks, b->dtc_tiles,
+                              b->ntc_tiles, 1, b->tc_tn, b->stream)) != cudaSuccess)
         return e;
     if ((e = launch_measure(b->djobs, b->dfp_work, b->nfp_work, 1, 1, b->fp_meas_smem, b->stream)) != cudaSuccess)
         return e;

@@ -13,6 +13,7 @@ constexpr int kSiteBlock = 32;      // sites decided by one warp between field u
 constexpr int kAuxThreads = 256;    // threads of the init / measure / rebuild CTAs
 constexpr int kMaxQ = 16;           // largest q (4-bit packed spins)
 constexpr int kMaxL = 65536;        // largest L (16-bit positions in the direct rebuild)
+constexpr int kChunk = 128;         // K sites per chunk of the tensor-core rebuild
 
 // Everything a kernel needs to know about one job, resident in device memory.
 // Arrays indexed by "replica" follow the configuration; arrays indexed by
@@ -40,8 +41,12 @@ struct JobDev {
     double* meas_E;       // per slot, written by the measure kernel
     double* meas_M;
     unsigned long long* err_bits;  // fields_error result (double bits, max)
-    const uint16_t* Jsplit;        // FP32 mode: BF16 parts hi, mid, lo of J*, [3][Lpad]
-    int tc_tab_smem;               // tensor-core rebuild stages the split table in shared memory
+    const uint16_t* Jhank;         // FP32 mode: BF16 parts hi, mid, lo of J* as Hankel core matrices,
+                                   // [3][hank_cores][8][8] (the tensor-core rebuild's A operand)
+    uint16_t* Xoh;                 // FP32 mode: one-hot spins, the rebuild's B operand,
+                                   // [Lc / kChunk][NG][16][8][8] (Lc: L rounded up to kChunk)
+    int hank_cores;                // core matrices per part of Jhank: Lc / 4 - 1
+    int NG;                        // 8-row groups of the B operand: q R rounded up to 128, / 8
     int* status;                   // 0 ok; 1 a bounded device wait expired
     int* sched;                    // FP32 rebuild schedule: [0] current interval k, [1] sweep of the next rebuild
     unsigned long long* drift_bits;  // max |h_before - h_rebuilt| / Jtot of the last rebuild (double bits)
@@ -107,17 +112,25 @@ cudaError_t launch_measure(const JobDev* jobs_dev, const int2* work, int nwork, 
 // with the stored fields and fold max |diff| / jtot into err_bits.
 cudaError_t launch_fields_direct(const JobDev* job_dev, int L, int R, int mode, int cond, size_t smem_bytes,
                                  cudaStream_t st);
-// FP32 mode: the split-BF16 tensor-core rebuild H = C . onehot(S) over a tile
-// table of (job index, first row, first column) 128 x tn output tiles (any
-// mix of jobs); max_tab_Lpad: the largest Lpad among jobs that stage their
-// split table in shared memory (0 if none).  Persistent: one CTA per SM.
-// tn: output tile width, 64 or 128 (tc_tile_width picks it from the tile counts).
-cudaError_t launch_fields_tc(const JobDev* jobs_dev, const int4* tiles, int ntiles, int max_tab_Lpad, int cond,
-                             int tn, cudaStream_t st);
+// FP32 mode: the split-BF16 tensor-core rebuild H = C . onehot(S): a one-hot
+// kernel writes the B operand of the listed jobs (jobs_dev[idx[i]], i < njobs;
+// idx null: jobs_dev[i]) on a grid of onehot_blocks x njobs CTAs, then the
+// persistent tensor-core kernel (one CTA per SM) walks a tile table of
+// (job index, first row, first column) 128 x tn output tiles (any mix of
+// jobs).  tn: output tile width, 64 or 128 (tc_tile_width picks it from the
+// tile counts).
+cudaError_t launch_fields_tc(const JobDev* jobs_dev, const int* idx, int njobs, int onehot_blocks,
+                             const int4* tiles, int ntiles, int cond, int tn, cudaStream_t st);
 void tc_tiles(int job, int L, int q, int R, int tn, std::vector<int4>& out);
 long long tc_tile_count(int L, int q, int R, int tn);
 int tc_tile_width(long long tiles64, long long tiles128, int nsm);
-int tc_table_in_smem(int Lpad);
+int tc_onehot_blocks(int L, int q, int R);  // one-hot grid width for one job of this shape
+int tc_ng(int q, int R);                     // JobDev::NG of this shape
+long long tc_hank_cores(int L);              // JobDev::hank_cores of this shape
+size_t tc_hank_bytes(int L);                 // bytes of the Jhank table
+size_t tc_onehot_bytes(int L, int q, int R); // bytes of the Xoh operand
+// the Jhank table from the split table ([3][Lpad], part sp of J*(r) at sp Lpad + r)
+void tc_hank_table(const std::vector<double>& J, const uint16_t* split, int Lpad, std::vector<uint16_t>& out);
 // after a rebuild: adapt the FP32 rebuild interval of jobs[idx[i]] to the
 // measured drift (one thread per job)
 cudaError_t launch_rebuild_policy(const JobDev* jobs_dev, const int* idx, int njobs, int cond, cudaStream_t st);

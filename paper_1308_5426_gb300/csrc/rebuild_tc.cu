@@ -8,23 +8,40 @@
 // memory.  X is exact in BF16 (0 or 1); C is carried as three BF16 parts
 // hi + mid + lo of the FP64 J* (representation error ~2^-25 J*), each part one
 // MMA per K-step.  One CTA computes a 128 x TN tile of H (TN = 64 or 128) over
-// all of K in chunks of kChunk = 128 sites: eight warps build the operand tiles in
-// shared memory from the split table and the packed spins, one thread issues
-// the 24 MMAs of the chunk (8 K-steps x 3 parts) and commits them to the
-// mbarrier of the chunk's stage; two stages alternate, so chunk t + 1 is
-// built while the MMAs of chunk t run.  The tensor core's FP32 accumulation rounds every MMA's sum into
-// the accumulator, so the accumulation chains are kept short: the hi parts of
-// successive chunks rotate over 512 / TN - 1 accumulators (seven or three),
-// and the small mid + lo parts go to one of their own (their rounding is then
-// relative to their own small size); together they fill the 512 TMEM columns.
-// The epilogue adds them in FP64 and stores FP32 fields.
+// all of K in chunks of kChunk = 128 sites.
+//
+// Both operands come from device memory, ready in the MMA's shared-memory
+// layout, by bulk asynchronous copies (cp.async.bulk, completion counted on an
+// mbarrier), so no thread builds operand tiles:
+// - A: the chunk's K sites are taken in reverse order, which makes the
+//   circulant tile Hankel: core matrix (g, c) is core matrix g + c of a strip
+//   of kHank = 31, and the strip of tile row m0 and chunk k0 depends on
+//   m0 - k0 only.  A per-job table (built once at job creation) holds, for
+//   every such offset, the strip's core matrices back to back; one A tile is
+//   one 3968-byte copy per BF16 part.
+// - B: a one-hot kernel writes X before the rebuild, per chunk and 8-row group
+//   the 16 core matrices of the chunk's K groups (2 KB); a TN-row tile of a
+//   chunk is one contiguous copy of TN x 256 bytes.
+// Warp 0 issues the copies into a ring of stages (3 or 4), warp 1 issues the
+// 24 MMAs of each chunk (8 K-steps x 3 parts) and commits them to the stage's
+// "empty" barrier, warps 2..9 read the accumulators.  The FP32 accumulation
+// rounds every MMA's sum into the accumulator, so the chains are kept short:
+// the hi parts of successive chunks rotate over 512 / TN - 1 accumulators
+// (seven or three), and the small mid + lo parts go to one of their own
+// (their rounding is then relative to their own small size); together they
+// fill the 512 TMEM columns.  The epilogue adds them in FP64 and stores FP32
+// fields; the old values (for the drift) are copied to shared memory while
+// the MMAs still run.
 //
 // Operand layout (both K-major, no swizzle): 8-row x 16-byte core matrices.
-// B: core matrix (row group g, K group c) at byte (c G + g) 128 (leading (K)
-// byte offset 128 G, stride (row-group) byte offset 128; K-step s at 256 G s).
-// A: the chunk's sites are taken in reverse order (as in B), which makes the
-// circulant tile Hankel: core matrix (g, c) = core matrix g + c of a strip of
-// 31, so both byte offsets are 128 and K-step s starts at 256 s.
+// A: core matrix h of the strip at byte 128 h; leading (K) and stride (row
+// group) byte offsets both 128; K-step s starts at byte 256 s.
+// B: core matrix (row group g, K group kc) at byte (16 g + kc) 128; leading
+// byte offset 128, stride byte offset 2048; K-step s starts at byte 256 s.
+//
+// Every wait is bounded (a timer): a wait that expires raises a shared abort
+// flag that ends the other roles' loops, the job's status word is set, and the
+// CTA still drains its copies and MMAs before it frees the tensor memory.
 #include <cstdint>
 #include <vector>
 
@@ -34,26 +51,28 @@ namespace plr {
 
 namespace {
 
-constexpr int kTcThreads = 256;      // 8 warps build the tiles; warps w and w + 4 share TMEM lanes 32 (w % 4) ..
+constexpr int kEpiWarps = 8;                       // warps 2..9: two per TMEM lane quarter
+constexpr int kTcThreads = 32 * (2 + kEpiWarps);   // + the copy warp and the MMA warp
 constexpr int kTileM = 128;
-
-constexpr int kChunk = 128;          // K sites per chunk
-constexpr int kHank = kTileM / 8 + kChunk / 8 - 1;  // distinct core matrices of an A tile (Hankel form)
-constexpr int kTileBytes = kHank * 128;            // 3968 B per A tile of one split
 constexpr int kSplit = 3;
+constexpr int kHank = kTileM / 8 + kChunk / 8 - 1;  // distinct core matrices of an A tile (Hankel form)
+constexpr int kTileBytes = kHank * 128;            // 3968 B per A tile of one part
 constexpr int kTmemCols = 512;       // all of the SM's tensor memory: accumulators of TN columns each
+constexpr int kOnehotThreads = 256;
+constexpr unsigned long long kWaitNs = 4000000000ull;  // bounded waits: 4 s
+constexpr size_t kTcMinSmem = 120 * 1024;   // forces one CTA per SM (owner of all 512 columns)
+
 // per tile width TN (64 or 128 output columns): accumulators, B tile, stage
 template <int TN>
 struct TcShape {
     static constexpr int kAcc = kTmemCols / TN;      // 8 or 4 accumulators
     static constexpr int kAccHi = kAcc - 1;          // rotating accumulators of the hi parts; the last takes mid + lo
     static constexpr int kTileBytesB = TN * kChunk * 2;  // TN x kChunk BF16 B tile
-    static constexpr int kGB = TN / 8;               // row groups of the B tile
     static constexpr int kStageBytes = kSplit * kTileBytes + kTileBytesB;  // three A tiles + the B tile
+    static constexpr int kStages = TN == 128 ? 3 : 4;  // copies run up to kStages - 1 chunks ahead of the MMAs
+    static constexpr int kOldBytes = kEpiWarps * 32 * (TN / 2) * 4;  // the replaced fields, per epilogue thread
 };
-constexpr int kStages = 2;           // chunk t + 1 is built while the MMAs of chunk t run
-constexpr long long kWaitLimit = 1ll << 26;  // bounded mbarrier wait (iterations)
-constexpr size_t kTcMinSmem = 120 * 1024;   // forces one CTA per SM (owner of all 512 columns)
+constexpr int kBarBytes = 128;  // full[kStages], empty[kStages], tfull, tempty, drain; TMEM slot; abort flag
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
 {
@@ -76,9 +95,20 @@ __host__ __device__ constexpr uint32_t make_idesc(int M, int N)
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+__device__ __forceinline__ unsigned long long global_ns()
 {
-    for (long long it = 0; it < kWaitLimit; ++it) {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the phase of the given parity to complete; false if the abort
+// flag is raised meanwhile (abort may be null: no early exit) or the time
+// limit passes (which raises the flag).  sleep_ns: back-off between polls.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort, uint32_t sleep_ns = 0)
+{
+    unsigned long long t0 = 0;
+    for (uint32_t it = 0;; ++it) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -88,19 +118,92 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
             : "r"(bar), "r"(parity)
             : "memory");
         if (done) return true;
+        if (abort && *abort) return false;
+        if (sleep_ns) __nanosleep(sleep_ns);
+        if ((it & 255u) == 0) {
+            const unsigned long long t = global_ns();
+            if (it == 0) t0 = t;
+            else if (t - t0 > kWaitNs) {
+                if (abort) *abort = 1;
+                return false;
+            }
+        }
     }
-    return false;
 }
 
-__device__ __forceinline__ uint16_t bf16_one() { return 0x3F80u; }
-
-// (i - k) mod L for i < L + 128 and k < L + kChunk (tile and chunk padding past L
-// only meet zero operands, so any in-range index serves there)
-__device__ __forceinline__ int circ(int d, int L)
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
 {
-    d += d < 0 ? L : 0;
-    d -= d >= L ? L : 0;
-    return (d < 0 || d >= L) ? 0 : d;
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// bulk copy global -> this CTA's shared memory, completion counted on bar
+// (addresses 16-byte aligned, bytes a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// chunk order of a tile: decreasing circular distance from the chunk holding
+// the tile's centre, so the large near-diagonal couplings are added last and
+// the many small far-field sums accumulate while the accumulators are still
+// small
+__device__ __forceinline__ int chunk_of(int t, int m0, int nchunks)
+{
+    const int cc = ((m0 + kTileM / 2) / kChunk) % nchunks;
+    const int kk = nchunks - 1 - t;  // rank in increasing distance: 0, +1, -1, +2, -2, ...
+    const int o = kk == 0 ? 0 : ((kk & 1) ? (kk + 1) / 2 : -(kk / 2));
+    int c = cc + o;  // |o| <= nchunks / 2
+    c += c < 0 ? nchunks : 0;
+    c -= c >= nchunks ? nchunks : 0;
+    return c;
+}
+
+__device__ __forceinline__ bool tile_live(const JobDev& jb, int cond) { return !cond || rebuild_due(jb); }
+
+// One-hot B operand of the jobs due for a rebuild (blockIdx.y: entry of the
+// job list).  Thread u writes the 16-byte row rr of core matrix (row group G,
+// K group kc) of chunk c, u = ((c NG + G) 16 + kc) 8 + rr: element e is 1 when
+// replica r_n of row n = 8 G + rr has state x_n at site
+// k = 128 c + 127 - 8 kc - e (K reversed within the chunk), else 0.
+__global__ void __launch_bounds__(kOnehotThreads) onehot_kernel(const JobDev* __restrict__ jobs,
+                                                                const int* __restrict__ idx, int cond)
+{
+    const JobDev& jb = jobs[idx ? idx[blockIdx.y] : (int)blockIdx.y];
+    if (!tile_live(jb, cond)) return;
+    const int L = jb.L, q = jb.q, W = jb.W, NG = jb.NG;
+    const int N = q * jb.R;
+    const long long total = (long long)((L + kChunk - 1) / kChunk) * NG * 128;
+    uint4* __restrict__ X = (uint4*)jb.Xoh;
+    const long long stride = (long long)gridDim.x * kOnehotThreads;
+    for (long long u = (long long)blockIdx.x * kOnehotThreads + threadIdx.x; u < total; u += stride) {
+        const int rr = (int)(u & 7), kc = (int)((u >> 3) & 15);
+        const long long cg = u >> 7;
+        const int c = (int)(cg / NG), G = (int)(cg - (long long)c * NG);
+        const int n = 8 * G + rr;
+        uint32_t v[4] = {0u, 0u, 0u, 0u};
+        if (n < N) {
+            const int r = n / q, x = n - r * q;
+            const int wi = 16 * c + 15 - kc;  // word of sites 8 wi .. 8 wi + 7: element e is nibble 7 - e
+            const uint32_t word = wi < W ? jb.spins[(size_t)r * W + wi] : 0u;
+            const int k0 = 128 * c + 127 - 8 * kc;
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+                if (k0 - e < L && (int)((word >> (4 * (7 - e))) & 15u) == x) v[e >> 1] |= 0x3F80u << (16 * (e & 1));
+        }
+        X[u] = make_uint4(v[0], v[1], v[2], v[3]);
+    }
 }
 
 template <int TN>
@@ -108,276 +211,284 @@ __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* 
                                                                   const int4* __restrict__ tiles, int ntiles,
                                                                   int cond)
 {
-    constexpr int kTileN = TN;
-    constexpr int kAcc = TcShape<TN>::kAcc, kAccHi = TcShape<TN>::kAccHi;
-    constexpr int kGB = TcShape<TN>::kGB, kStageBytes = TcShape<TN>::kStageBytes;
-    constexpr int kHB = kGB / (kTcThreads / 32);  // B row groups per build warp
+    using S = TcShape<TN>;
+    constexpr int kAcc = S::kAcc, kAccHi = S::kAccHi, kStageBytes = S::kStageBytes, kStages = S::kStages;
     static_assert(kAcc * TN == kTmemCols, "accumulators fill the tensor memory");
+    static_assert(kStageBytes % 128 == 0, "stages stay 128-byte aligned");
     extern __shared__ __align__(1024) unsigned char smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    constexpr int kWarps = kTcThreads / 32;
-    static_assert(kHB * kWarps == kGB, "whole B row groups per build warp");
 
-    // stage b: A tiles at b * kStageBytes, then its B tile
-    uint64_t* mbar = (uint64_t*)(smem + kStages * kStageBytes);  // one per stage
-    uint32_t* tmem_slot = (uint32_t*)(mbar + kStages);
-    uint16_t* tab = (uint16_t*)(smem + kStages * kStageBytes + 64);  // split table [3][Lpad], if staged
+    float* olds = (float*)(smem + kStages * kStageBytes);         // [TN / 2][256]: column e of epilogue thread
+    uint64_t* full = (uint64_t*)(smem + kStages * kStageBytes + S::kOldBytes);  // copies of stage b landed
+    uint64_t* empty = full + kStages;                              // MMAs reading stage b done
+    uint64_t* tfull = empty + kStages;                             // a tile's MMAs done
+    uint64_t* tempty = tfull + 1;                                  // its accumulators read
+    uint64_t* drain = tfull + 2;                                   // every MMA of the CTA done
+    uint32_t* tmem_slot = (uint32_t*)(drain + 1);
+    volatile int* abort = (volatile int*)(tmem_slot + 1);
 
     // skip the whole CTA when none of its tiles is due (no tensor memory taken)
     bool any = false;
-    for (int ti = blockIdx.x; ti < ntiles && !any; ti += gridDim.x) any = !cond || rebuild_due(jobs[tiles[ti].x]);
+    for (int ti = blockIdx.x; ti < ntiles && !any; ti += gridDim.x) any = tile_live(jobs[tiles[ti].x], cond);
     if (!any) return;
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"(kTmemCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        for (int b = 0; b < kStages; ++b)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar + b)) : "memory");
+        for (int b = 0; b < kStages; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(full + b)) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(empty + b)) : "memory");
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(tfull)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(tempty)), "r"(kEpiWarps) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(drain)) : "memory");
+        *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
-    // this thread's place in a core matrix: row rr = lane / 4, sites 2 (lane % 4), +1
-    const int rr = lane >> 2, kp = (lane & 3) * 2;
-    const uint32_t idesc = make_idesc(kTileM, kTileN);
-    bool ok = true;
-    uint32_t parity[kStages] = {0u, 0u};  // phase of each stage's barrier that is awaited next
-    int pending[kStages] = {0, 0};        // commits on each stage's barrier not yet awaited
-    const JobDev* staged = nullptr;       // job whose split table is in shared memory
+    int failed_job = -1;  // job of the tile at which this thread's wait expired
+    uint32_t issued = 0;  // chunks whose copies the copy thread started
 
-    for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x) {
-    const int4 tile = tiles[ti];
-    const JobDev& jb = jobs[tile.x];
-    if (cond && !rebuild_due(jb)) continue;
-    const int L = jb.L, q = jb.q, Lpad = jb.Lpad, W = jb.W;
-    const int N = q * jb.R;
-    const int m0 = tile.y, n0 = tile.z;
-    const bool tab_smem = jb.tc_tab_smem != 0;
-    const uint16_t* gtab = jb.Jsplit;
-    if (tab_smem && staged != &jb) {
-        __syncthreads();  // previous tile done with the old table
-        for (int m = tid; m < kSplit * Lpad; m += kTcThreads) tab[m] = gtab[m];
-        __syncthreads();
-        staged = &jb;
-    }
-    const uint16_t* T = tab_smem ? tab : gtab;
-    const int nchunks = (L + kChunk - 1) / kChunk;
-    // this thread's rows of the B tile: n = n0 + 8 (warp + 8 hb) + rr, hb < kHB, fixed over the tile
-    int bx[kHB];
-    bool nvalid[kHB];
-    const uint32_t* bsp[kHB];
+    if (warp == 0) {
+        // ---- copies: A strips (three parts) and the B tile of each chunk into the stage ring
+        if (lane == 0) {
+            for (int ti = blockIdx.x; ti < ntiles && failed_job < 0 && !*abort; ti += gridDim.x) {
+                const int4 tile = tiles[ti];
+                const JobDev& jb = jobs[tile.x];
+                if (!tile_live(jb, cond)) continue;
+                const int nchunks = (jb.L + kChunk - 1) / kChunk;
+                const int m0 = tile.y, n0 = tile.z;
+                const unsigned char* hank = (const unsigned char*)jb.Jhank;
+                const size_t hank_part = (size_t)jb.hank_cores * 128;
+                const unsigned char* xb = (const unsigned char*)jb.Xoh + (size_t)(n0 / 8) * 2048;
+                const size_t xchunk = (size_t)jb.NG * 2048;
+                for (int t = 0; t < nchunks; ++t) {
+                    const uint32_t b = issued % kStages;
+                    if (issued >= kStages && !mbar_wait(smem_u32(empty + b), ((issued / kStages) - 1) & 1u, abort)) {
+                        failed_job = tile.x;
+                        break;
+                    }
+                    const int c = chunk_of(t, m0, nchunks);
+                    const int j0 = (m0 - c * kChunk) / 8 + 16 * nchunks - 16;  // first core matrix of the strip
+                    const uint32_t st = smem_u32(smem + b * kStageBytes);
+                    const uint32_t fb = smem_u32(full + b);
+                    mbar_expect_tx(fb, (uint32_t)kStageBytes);
 #pragma unroll
-    for (int hb = 0; hb < kHB; ++hb) {
-        const int nb = n0 + 8 * (warp + kWarps * hb) + rr;
-        nvalid[hb] = nb < N;
-        const int brep = nvalid[hb] ? nb / q : 0;
-        bx[hb] = nvalid[hb] ? nb - brep * q : 0;
-        bsp[hb] = jb.spins + (size_t)brep * W;
-    }
-    const int bshift = 4 * (6 - kp);  // nibble of site k0 + kChunk - 2 - 8 kc - kp within its word
-
-    // chunk order: decreasing circular distance from the chunk holding the tile's
-    // centre, so the large near-diagonal couplings are added last and the many
-    // small far-field sums accumulate while the accumulators are still small
-    const int cc = ((m0 + kTileM / 2) / kChunk) % nchunks;
-    auto chunk_of = [&](int t) {
-        const int kk = nchunks - 1 - t;  // rank in increasing distance: 0, +1, -1, +2, -2, ...
-        const int o = kk == 0 ? 0 : ((kk & 1) ? (kk + 1) / 2 : -(kk / 2));
-        int c = cc + o;  // |o| <= nchunks / 2
-        c += c < 0 ? nchunks : 0;
-        c -= c >= nchunks ? nchunks : 0;
-        return c;
-    };
-    // the spin words of this thread's B rows for a chunk (word (kChunk / 8) (c + 1) - 1 - kc
-    // holds K group kc)
-    uint32_t wnext[kHB][kChunk / 8];
-    auto load_words = [&](int c) {
-#pragma unroll
-        for (int hb = 0; hb < kHB; ++hb)
-#pragma unroll
-            for (int kc = 0; kc < kChunk / 8; ++kc) {
-                const int wi = (kChunk / 8) * (c + 1) - 1 - kc;
-                wnext[hb][kc] = (nvalid[hb] && wi < W) ? bsp[hb][wi] : 0u;
+                    for (int sp = 0; sp < kSplit; ++sp)
+                        bulk_g2s(st + sp * kTileBytes, hank + sp * hank_part + (size_t)j0 * 128, kTileBytes, fb);
+                    bulk_g2s(st + kSplit * kTileBytes, xb + (size_t)c * xchunk, S::kTileBytesB, fb);
+                    ++issued;
+                }
             }
-    };
-    load_words(chunk_of(0));
-    for (int t = 0; t < nchunks; ++t) {
-        const int c = chunk_of(t);
-        const int k0 = c * kChunk;
-        uint32_t words[kHB][kChunk / 8];
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ---- MMAs: one thread issues the chunk's 24 MMAs and commits them
+        if (lane == 0) {
+            const uint32_t idesc = make_idesc(kTileM, TN);
+            uint32_t used = 0, ntile = 0;
+            for (int ti = blockIdx.x; ti < ntiles && failed_job < 0 && !*abort; ti += gridDim.x) {
+                const int4 tile = tiles[ti];
+                const JobDev& jb = jobs[tile.x];
+                if (!tile_live(jb, cond)) continue;
+                const int nchunks = (jb.L + kChunk - 1) / kChunk;
+                // the accumulators of the previous tile have been read
+                if (ntile > 0 && !mbar_wait(smem_u32(tempty), (ntile - 1) & 1u, abort)) {
+                    failed_job = tile.x;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                for (int t = 0; t < nchunks; ++t) {
+                    const uint32_t b = used % kStages;
+                    if (!mbar_wait(smem_u32(full + b), (used / kStages) & 1u, abort)) {
+                        failed_job = tile.x;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t sa = smem_u32(smem + b * kStageBytes);
+                    const uint32_t sb = sa + kSplit * kTileBytes;
+                    const uint32_t dhi = tmem + (uint32_t)((t % kAccHi) * TN);
+                    const uint32_t dsmall = tmem + (uint32_t)(kAccHi * TN);
 #pragma unroll
-        for (int hb = 0; hb < kHB; ++hb)
+                    for (int s = 0; s < kChunk / 16; ++s) {
+                        const uint64_t bdesc = make_desc(sb + s * 256, 128, 2048);
 #pragma unroll
-            for (int kc = 0; kc < kChunk / 8; ++kc) words[hb][kc] = wnext[hb][kc];
-        if (t + 1 < nchunks) load_words(chunk_of(t + 1));  // in flight during this chunk
-        const int b = t % kStages;
-        unsigned char* tileA = smem + b * kStageBytes;
-        unsigned char* tileB = tileA + kSplit * kTileBytes;
-        // the MMAs that last read this stage (chunk t - kStages) must be done:
-        // warp 0 waits, the barrier tells the others
-        if (pending[b]) {
-            if (warp == 0 && !mbar_wait(smem_u32(mbar + b), parity[b])) ok = false;
-            parity[b] ^= 1u;
-            pending[b] = 0;
-            if (!__syncthreads_and(ok)) {
-                ok = false;
+                        for (int sp = 0; sp < kSplit; ++sp) {
+                            const uint64_t adesc = make_desc(sa + sp * kTileBytes + s * 256, 128, 128);
+                            const uint32_t dcol = sp == 0 ? dhi : dsmall;
+                            const bool first = s == 0 && (sp == 0 ? t < kAccHi : (t == 0 && sp == 1));
+                            const uint32_t accumulate = first ? 0u : 1u;
+                            asm volatile(
+                                "{\n\t.reg .pred p;\n\t"
+                                "setp.ne.b32 p, %4, 0;\n\t"
+                                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dcol),
+                                "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+                                : "memory");
+                        }
+                    }
+                    tc_commit(smem_u32(empty + b));  // stage b free once these MMAs have read it
+                    ++used;
+                }
+                if (failed_job >= 0) break;
+                tc_commit(smem_u32(tfull));  // the tile's accumulators complete
+                ++ntile;
+            }
+            // every MMA issued by this thread complete before the tensor memory is freed
+            tc_commit(smem_u32(drain));
+            mbar_wait(smem_u32(drain), 0u, nullptr);
+        }
+        __syncwarp();
+    } else {
+        // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 = rows
+        // m0 + 32 (w % 4) + lane, columns half (w - 2) / 4 of the tile
+        const int quad = warp & 3;
+        constexpr int kCols = TN / 2;
+        const int cb0 = ((warp - 2) >> 2) * kCols;
+        uint32_t ntile = 0;
+        for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+            // warp-uniform exit (the accumulator reads below are warp-collective)
+            if (__any_sync(0xffffffffu, *abort != 0)) break;
+            const int4 tile = tiles[ti];
+            const JobDev& jb = jobs[tile.x];
+            if (!tile_live(jb, cond)) continue;
+            const int L = jb.L, Lpad = jb.Lpad, N = jb.q * jb.R;
+            const int nchunks = (L + kChunk - 1) / kChunk;
+            const int m0 = tile.y, n0 = tile.z;
+            const int i = m0 + 32 * quad + lane;
+            float* F = (float*)jb.fields;
+            // the fields being replaced (for the drift): copied to shared memory
+            // (zero-filled outside the job) while the MMAs run
+            float* old = olds + (tid - 64);
+            {
+                const float* src = F + (size_t)(n0 + cb0) * Lpad + i;
+                uint32_t dst = smem_u32(old);
+#pragma unroll 4
+                for (int e = 0; e < kCols; ++e, src += Lpad, dst += 256 * 4) {
+                    const bool in = i < L && n0 + cb0 + e < N;
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(in ? src : F),
+                                 "r"(in ? 4 : 0)
+                                 : "memory");
+                }
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+            // lane 0 polls (backing off: the wait spans the tile's main loop, and
+            // polls compete with the copies and MMAs for shared memory); then
+            // every lane observes the completed phase itself
+            bool got = true;
+            if (lane == 0) got = mbar_wait(smem_u32(tfull), ntile & 1u, abort, 256);
+            if (!__shfl_sync(0xffffffffu, got, 0)) {
+                failed_job = tile.x;
                 break;
             }
+            mbar_wait(smem_u32(tfull), ntile & 1u, nullptr);
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        }
-        // The chunk's K sites are taken in reverse, k = k0 + kChunk - 1 - k', so A[i][k'] =
-        // J*((i - k) mod L) depends on i + k' only: core matrix (g, c) is core
-        // matrix h = g + c of a Hankel strip of kHank = 31, which the MMA reads with
-        // row-group and K-group strides both 128 bytes.  Element (rr, e) of
-        // core matrix h is J*((m0 - k0 - kChunk + 1 + 8 h + rr + e) mod L).
-        for (int h = warp; h < kHank; h += kWarps) {
-            const int r0 = circ(m0 - k0 - (kChunk - 1) + 8 * h + rr + kp, L);
-            const int r1 = r0 + 1 == L ? 0 : r0 + 1;
-            const uint32_t off = (uint32_t)(h * 128 + rr * 16 + kp * 2);
+            asm volatile("cp.async.wait_all;" ::: "memory");
+            const int nhi = nchunks < kAccHi ? nchunks : kAccHi;
+            double dmax = 0.0;
 #pragma unroll
-            for (int sp = 0; sp < kSplit; ++sp) {
-                const uint32_t v = (uint32_t)T[sp * Lpad + r0] | ((uint32_t)T[sp * Lpad + r1] << 16);
-                *(uint32_t*)(tileA + sp * kTileBytes + off) = v;
-            }
-        }
-        // B tile: row n = (replica, state), X = 1 where the replica's spin at site
-        // k = k0 + kChunk - 1 - k' is that state (K reversed as for A)
-        // (warp w holds row groups w + 8 hb: the core matrices (g, kc), kc < kChunk / 8;
-        // spin word (k0 + kChunk) / 8 - 1 - kc holds the sites of K group kc)
+            for (int cb = 0; cb < kCols; cb += 8) {
+                uint32_t v[kAcc][8];
 #pragma unroll
-        for (int hb = 0; hb < kHB; ++hb)
-#pragma unroll
-            for (int kc = 0; kc < kChunk / 8; ++kc) {
-                const int ka = k0 + (kChunk - 1) - (8 * kc + kp);  // site of k' = 8 kc + kp; k' + 1 is ka - 1
-                const uint32_t off = (uint32_t)((kc * kGB + warp + kWarps * hb) * 128 + rr * 16 + kp * 2);
-                uint32_t v = 0;
-                if (nvalid[hb] && ka - 1 < L) {
-                    const uint32_t word = words[hb][kc] >> bshift;
-                    if (ka < L && (int)((word >> 4) & 15u) == bx[hb]) v |= bf16_one();  // next nibble: site ka
-                    if ((int)(word & 15u) == bx[hb]) v |= (uint32_t)bf16_one() << 16;
+                for (int a = 0; a < kAcc; ++a) {
+                    if (a < nhi || a == kAccHi) {  // the used hi accumulators, and mid + lo
+                        const uint32_t taddr = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(a * TN + cb0 + cb);
+                        asm volatile(
+                            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                            : "=r"(v[a][0]), "=r"(v[a][1]), "=r"(v[a][2]), "=r"(v[a][3]), "=r"(v[a][4]),
+                              "=r"(v[a][5]), "=r"(v[a][6]), "=r"(v[a][7])
+                            : "r"(taddr)
+                            : "memory");
+                    }
                 }
-                *(uint32_t*)(tileB + off) = v;
-            }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        if (!__syncthreads_and(ok)) {
-            ok = false;
-            break;
-        }
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t dhi = tmem + (uint32_t)((t % kAccHi) * kTileN);
-            const uint32_t dsmall = tmem + (uint32_t)(kAccHi * kTileN);
-#pragma unroll
-            for (int s = 0; s < kChunk / 16; ++s) {
-                const uint64_t bdesc = make_desc(smem_u32(tileB) + s * 256 * kGB, 128 * kGB, 128);
-#pragma unroll
-                for (int sp = 0; sp < kSplit; ++sp) {
-                    const uint64_t adesc = make_desc(smem_u32(tileA + sp * kTileBytes) + s * 256, 128, 128);
-                    const uint32_t dcol = sp == 0 ? dhi : dsmall;
-                    const bool first = s == 0 && (sp == 0 ? t < kAccHi : (t == 0 && sp == 1));
-                    const uint32_t accumulate = first ? 0u : 1u;
-                    asm volatile(
-                        "{\n\t.reg .pred p;\n\t"
-                        "setp.ne.b32 p, %4, 0;\n\t"
-                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dcol),
-                        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-                        : "memory");
-                }
-            }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_u32(mbar + b))
-                         : "memory");
-        }
-        pending[b] = 1;
-    }
-    // all of the tile's MMAs done before its accumulators are read
-    for (int b = 0; b < kStages; ++b)
-        if (pending[b]) {
-            if (warp == 0 && !mbar_wait(smem_u32(mbar + b), parity[b])) ok = false;
-            parity[b] ^= 1u;
-            pending[b] = 0;
-        }
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (!__syncthreads_and(ok)) ok = false;
-
-    if (ok) {
-        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 = rows m0 + 32 (w % 4) + lane,
-        // columns half (w / 4) of the tile
-        const int quad = warp & 3;
-        const int i = m0 + 32 * quad + lane;
-        const int nhi = nchunks < kAccHi ? nchunks : kAccHi;
-        float* F = (float*)jb.fields;
-        double dmax = 0.0;
-        constexpr int kCols = kTileN / (kWarps / 4);
-        for (int cb = (warp >> 2) * kCols; cb < (warp >> 2) * kCols + kCols; cb += 8) {
-            double sum[8];
-#pragma unroll
-            for (int e = 0; e < 8; ++e) sum[e] = 0.0;
-            for (int a = 0; a <= nhi; ++a) {
-                const int col = a < nhi ? a : kAccHi;  // the used hi accumulators, then mid + lo
-                uint32_t v[8];
-                const uint32_t taddr = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(col * kTileN + cb);
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
-                    : "r"(taddr)
-                    : "memory");
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                double sum[8];
 #pragma unroll
-                for (int e = 0; e < 8; ++e) sum[e] += (double)__uint_as_float(v[e]);
-            }
-            if (i < L) {
+                for (int e = 0; e < 8; ++e) sum[e] = 0.0;
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const int n = n0 + cb + e;
-                    if (n < N) {
-                        const size_t idx = (size_t)n * Lpad + i;
-                        dmax = fmax(dmax, fabs((double)F[idx] - sum[e]));  // drift of the ending period
-                        F[idx] = (float)sum[e];
+                for (int a = 0; a < kAcc; ++a)
+                    if (a < nhi || a == kAccHi)
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) sum[e] += (double)__uint_as_float(v[a][e]);
+                if (i < L) {
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const int n = n0 + cb0 + cb + e;
+                        if (n < N) {
+                            dmax = fmax(dmax, fabs((double)old[(cb + e) * 256] - sum[e]));  // drift of the ending period
+                            F[(size_t)n * Lpad + i] = (float)sum[e];
+                        }
                     }
                 }
             }
+            for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+            if (lane == 0 && dmax > 0.0)
+                atomicMax(jb.drift_bits, (unsigned long long)__double_as_longlong(dmax / jb.jtot));
+            // the accumulator reads above are complete before the next tile's MMAs
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(tempty));
+            ++ntile;
         }
-        for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
-        if (lane == 0 && dmax > 0.0)
-            atomicMax(jb.drift_bits, (unsigned long long)__double_as_longlong(dmax / jb.jtot));
-        // the tensor-memory reads above are complete before the next tile's MMAs
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    } else if (tid == 0) {
-        atomicExch(jb.status, 1);  // a bounded wait expired; the host reports ETIMEOUT
+        asm volatile("cp.async.wait_all;" ::: "memory");  // none still in flight at exit
     }
-    }  // tiles
-    // no MMA may still write tensor memory when it is freed (after an expired
-    // wait, give the outstanding commits a bounded chance to land)
-    if (warp == 0)
-        for (int b = 0; b < kStages; ++b)
-            if (pending[b]) mbar_wait(smem_u32(mbar + b), parity[b]);
+    if (failed_job >= 0) atomicExch(jobs[failed_job].status, 1);  // the host reports ETIMEOUT
+    __syncthreads();
+    // no copy may still write this CTA's shared memory when it exits: the last
+    // phase started on each stage's "full" barrier has completed (immediate
+    // when the MMAs consumed it)
+    if (tid == 0)
+        for (uint32_t g = issued > kStages ? issued - kStages : 0; g < issued; ++g)
+            mbar_wait(smem_u32(full + g % kStages), (g / kStages) & 1u, nullptr);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0)
+    if (warp == 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+}
+
+template <int TN>
+size_t tc_smem_bytes()
+{
+    using S = TcShape<TN>;
+    const size_t b = (size_t)S::kStages * S::kStageBytes + S::kOldBytes + kBarBytes;
+    return b < kTcMinSmem ? kTcMinSmem : b;
 }
 
 }  // namespace
 
-size_t tc_smem_bytes(int Lpad, int tab_smem)
+int tc_ng(int q, int R) { return ((q * R + 127) / 128) * 16; }
+
+long long tc_hank_cores(int L) { return (long long)((L + kChunk - 1) / kChunk) * (kChunk / 4) - 1; }
+
+size_t tc_hank_bytes(int L) { return (size_t)kSplit * (size_t)tc_hank_cores(L) * 128; }
+
+size_t tc_onehot_bytes(int L, int q, int R)
 {
-    // sized for the wider tile, so either width fits
-    size_t b = (size_t)kStages * TcShape<128>::kStageBytes + 64 + (tab_smem ? (size_t)kSplit * Lpad * 2 : 0);
-    b = (b + 127) & ~(size_t)127;
-    return b < kTcMinSmem ? kTcMinSmem : b;
+    return (size_t)((L + kChunk - 1) / kChunk) * (size_t)tc_ng(q, R) * 2048;
 }
 
-int tc_table_in_smem(int Lpad)
+void tc_hank_table(const std::vector<double>& J, const uint16_t* split, int Lpad, std::vector<uint16_t>& out)
 {
-    return (size_t)kStages * TcShape<128>::kStageBytes + 64 + (size_t)kSplit * Lpad * 2 <= 200 * 1024;
+    // core matrix j of part sp, row rr, element e: part sp of J*(u mod L),
+    // u = 8 j + rr + e + 1 - Lc (the strip of tile row m0 and chunk k0 starts
+    // at j0 = (m0 - k0) / 8 + Lc / 8 - 16)
+    const int L = (int)J.size();
+    const long long ncores = tc_hank_cores(L);
+    const long long Lc = (long long)((L + kChunk - 1) / kChunk) * kChunk;
+    out.assign((size_t)kSplit * (size_t)ncores * 64, 0);
+    for (int sp = 0; sp < kSplit; ++sp)
+        for (long long j = 0; j < ncores; ++j)
+            for (int rr = 0; rr < 8; ++rr)
+                for (int e = 0; e < 8; ++e) {
+                    const long long u = 8 * j + rr + e + 1 - Lc;
+                    const int r = (int)(((u % L) + L) % L);
+                    out[((size_t)sp * ncores + j) * 64 + rr * 8 + e] = split[(size_t)sp * Lpad + r];
+                }
 }
 
 int tc_tile_width(long long tiles64, long long tiles128, int nsm)
@@ -390,16 +501,25 @@ int tc_tile_width(long long tiles64, long long tiles128, int nsm)
     return 1.4 * w128 < w64 ? 128 : 64;
 }
 
-cudaError_t launch_fields_tc(const JobDev* jobs_dev, const int4* tiles, int ntiles, int any_tab_smem_Lpad,
-                             int cond, int tn, cudaStream_t st)
+int tc_onehot_blocks(int L, int q, int R)
 {
-    if (ntiles <= 0) return cudaSuccess;
-    const size_t smem = tc_smem_bytes(any_tab_smem_Lpad, any_tab_smem_Lpad > 0);
-    auto k = tn == 128 ? fields_tc_kernel<128> : fields_tc_kernel<64>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const long long rows = (long long)((L + kChunk - 1) / kChunk) * tc_ng(q, R) * 128;
+    const long long b = (rows + kOnehotThreads - 1) / kOnehotThreads;
+    return (int)(b < 4096 ? b : 4096);
+}
+
+cudaError_t launch_fields_tc(const JobDev* jobs_dev, const int* idx, int njobs, int onehot_blocks,
+                             const int4* tiles, int ntiles, int cond, int tn, cudaStream_t st)
+{
+    if (ntiles <= 0 || njobs <= 0) return cudaSuccess;
+    onehot_kernel<<<dim3(onehot_blocks > 0 ? onehot_blocks : 1, njobs), kOnehotThreads, 0, st>>>(jobs_dev, idx, cond);
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    int dev = 0, sms = 148;
-    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    auto k = tn == 128 ? fields_tc_kernel<128> : fields_tc_kernel<64>;
+    const size_t smem = tn == 128 ? tc_smem_bytes<128>() : tc_smem_bytes<64>();
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int sms = device_sm_count() > 0 ? device_sm_count() : 148;
     const int grid = ntiles < sms ? ntiles : sms;  // persistent: one CTA per SM walks the tile table
     k<<<grid, kTcThreads, smem, st>>>(jobs_dev, tiles, ntiles, cond);
     return cudaGetLastError();
