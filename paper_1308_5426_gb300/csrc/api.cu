@@ -101,10 +101,12 @@ struct potts_lr_batch {
     int2* dfp_work;              // (job, slot) of their slots, for the energy re-anchor
     int nfp_work;
     size_t fp_meas_smem;
+    int fp_meas_parts;           // the largest measure split among them
     int* dfp_idx;                // their job indices, for the schedule policy
     int2* dmeas;                 // (job, slot) of every slot, job order
     int nmeas;
     size_t meas_smem;
+    int meas_parts;              // the largest measure split among the jobs
     double* meas_buf;            // device staging: 2 * nmeas doubles
     std::vector<int> meas_off;   // first row of each job
     cudaGraphExec_t exec;
@@ -158,7 +160,7 @@ cudaError_t rebuild_launch(const potts_lr_t* h, const JobDev* job_dev, int cond,
     else
         e = launch_fields_direct(job_dev, h->L, h->R, 0, cond, h->direct_smem, st);
     if (e != cudaSuccess) return e;
-    e = launch_measure(job_dev, h->dwork, h->R, 1, cond, h->measure_smem, st);
+    e = launch_measure(job_dev, h->dwork, h->R, 1, cond, h->measure_smem, h->hj.meas_parts, st);
     if (e != cudaSuccess || h->precision != POTTS_LR_FP32) return e;
     return launch_rebuild_policy(job_dev, nullptr, 1, cond, st);
 }
@@ -350,6 +352,7 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
     const size_t o_nsw = take((size_t)R * 4), o_nex = take(4);
     const size_t o_accf = take((size_t)R * 8), o_accs = take((size_t)R * 8), o_near = take(16);
     const size_t o_mE = take((size_t)R * 8), o_mM = take((size_t)R * 8), o_err = take(8);
+    const size_t o_mpart = take((size_t)R * kMeasMaxParts * 8), o_mtick = take((size_t)R * 4);
     const size_t o_job = take(sizeof(JobDev)), o_work = take((size_t)R * sizeof(int2));
     const bool tc = h->precision == POTTS_LR_FP32;  // tensor-core rebuild operands
     const size_t o_hank = take(tc ? tc_hank_bytes(L) : 0), o_xoh = take(tc ? tc_onehot_bytes(L, q, R) : 0);
@@ -399,6 +402,9 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
     j.near = (unsigned long long*)(base + o_near);
     j.meas_E = (double*)(base + o_mE);
     j.meas_M = (double*)(base + o_mM);
+    j.meas_part = (double*)(base + o_mpart);
+    j.meas_ticket = (int*)(base + o_mtick);
+    j.meas_parts = measure_parts(L);
     j.err_bits = (unsigned long long*)(base + o_err);
     j.Jhank = tc ? (const uint16_t*)(base + o_hank) : nullptr;
     j.Xoh = tc ? (uint16_t*)(base + o_xoh) : nullptr;
@@ -472,7 +478,7 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
             break;
         if ((e = launch_init_spins(h->dj, 0, L, h->W, R, st)) != cudaSuccess) break;
         if ((e = launch_fields_direct(h->dj, L, R, 0, 0, h->direct_smem, st)) != cudaSuccess) break;
-        if ((e = launch_measure(h->dj, h->dwork, R, 1, 0, h->measure_smem, st)) != cudaSuccess) break;
+        if ((e = launch_measure(h->dj, h->dwork, R, 1, 0, h->measure_smem, j.meas_parts, st)) != cudaSuccess) break;
         e = cudaStreamSynchronize(st);
     } while (0);
     if (e != cudaSuccess) rc2 = cuda_fail(e, "potts_lr_create");
@@ -522,7 +528,7 @@ int potts_lr_exchange(potts_lr_t* h)
 int potts_lr_measure_device(potts_lr_t* h, double* E, double* M)
 {
     if (!h) return fail(POTTS_LR_EINVAL, "handle is NULL");
-    cudaError_t e = launch_measure(h->dj, h->dwork, h->R, 0, 0, h->measure_smem, h->stream);
+    cudaError_t e = launch_measure(h->dj, h->dwork, h->R, 0, 0, h->measure_smem, h->hj.meas_parts, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "measure kernel");
     const size_t b = (size_t)h->R * sizeof(double);
     if (E) PLR_CUDA(cudaMemcpyAsync(E, h->hj.meas_E, b, cudaMemcpyDeviceToDevice, h->stream));
@@ -533,7 +539,7 @@ int potts_lr_measure_device(potts_lr_t* h, double* E, double* M)
 int potts_lr_measure(potts_lr_t* h, double* E, double* M)
 {
     if (!h) return fail(POTTS_LR_EINVAL, "handle is NULL");
-    cudaError_t e = launch_measure(h->dj, h->dwork, h->R, 0, 0, h->measure_smem, h->stream);
+    cudaError_t e = launch_measure(h->dj, h->dwork, h->R, 0, 0, h->measure_smem, h->hj.meas_parts, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "measure kernel");
     const size_t b = (size_t)h->R * sizeof(double);
     PLR_CUDA(cudaMemcpyAsync(h->pinned, h->hj.meas_E, b, cudaMemcpyDeviceToHost, h->stream));
@@ -807,6 +813,7 @@ int potts_lr_batch_create(potts_lr_t* const* jobs, int n, void* cuda_stream, pot
         b->meas_off.push_back((int)mwork.size());
         for (int t = 0; t < jobs[i]->R; ++t) mwork.push_back(make_int2(i, t));
         b->meas_smem = std::max(b->meas_smem, jobs[i]->measure_smem);
+        b->meas_parts = std::max(b->meas_parts, jobs[i]->hj.meas_parts);
     }
     b->nmeas = (int)mwork.size();
     std::vector<int4> btiles;
@@ -823,6 +830,7 @@ int potts_lr_batch_create(potts_lr_t* const* jobs, int n, void* cuda_stream, pot
         for (int t = 0; t < h->R; ++t) fwork.push_back(make_int2(i, t));
         b->onehot_blocks = std::max(b->onehot_blocks, h->onehot_blocks);
         b->fp_meas_smem = std::max(b->fp_meas_smem, h->measure_smem);
+        b->fp_meas_parts = std::max(b->fp_meas_parts, h->hj.meas_parts);
     }
     b->ntc_tiles = (int)btiles.size();
     b->nfp_work = (int)fwork.size();
@@ -926,7 +934,8 @@ static cudaError_t batch_enqueue_sweeps(potts_lr_batch_t* b)
     if ((e = launch_fields_tc(b->djobs, b->dfp_idx, (int)b->fp32_jobs.size(), b->onehot_blocks, b->dtc_tiles,
                               b->ntc_tiles, 1, b->tc_tn, b->stream)) != cudaSuccess)
         return e;
-    if ((e = launch_measure(b->djobs, b->dfp_work, b->nfp_work, 1, 1, b->fp_meas_smem, b->stream)) != cudaSuccess)
+    if ((e = launch_measure(b->djobs, b->dfp_work, b->nfp_work, 1, 1, b->fp_meas_smem, b->fp_meas_parts,
+                            b->stream)) != cudaSuccess)
         return e;
     return launch_rebuild_policy(b->djobs, b->dfp_idx, (int)b->fp32_jobs.size(), 1, b->stream);
 }
@@ -987,7 +996,7 @@ static int batch_measure_enqueue(potts_lr_batch_t* b, double* E, double* M, cuda
 {
     int rc = batch_begin(b);
     if (rc) return rc;
-    cudaError_t e = launch_measure(b->djobs, b->dmeas, b->nmeas, 0, 0, b->meas_smem, b->stream);
+    cudaError_t e = launch_measure(b->djobs, b->dmeas, b->nmeas, 0, 0, b->meas_smem, b->meas_parts, b->stream);
     if (e != cudaSuccess) return cuda_fail(e, "batch measure");
     for (size_t i = 0; i < b->jobs.size(); ++i) {
         const potts_lr_t* h = b->jobs[i];

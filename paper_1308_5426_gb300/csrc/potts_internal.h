@@ -14,6 +14,7 @@ constexpr int kAuxThreads = 256;    // threads of the init / measure / rebuild C
 constexpr int kMaxQ = 16;           // largest q (4-bit packed spins)
 constexpr int kMaxL = 65536;        // largest L (16-bit positions in the direct rebuild)
 constexpr int kChunk = 128;         // K sites per chunk of the tensor-core rebuild
+constexpr int kMeasMaxParts = 32;   // largest split of one slot's measurement over CTAs
 
 // Everything a kernel needs to know about one job, resident in device memory.
 // Arrays indexed by "replica" follow the configuration; arrays indexed by
@@ -40,6 +41,9 @@ struct JobDev {
     unsigned long long* near;      // [2]: Metropolis, exchange near ties
     double* meas_E;       // per slot, written by the measure kernel
     double* meas_M;
+    double* meas_part;    // [slot][kMeasMaxParts]: the measure kernel's partial energy sums
+    int* meas_ticket;     // per slot: parts of the running measurement done (0 between launches)
+    int meas_parts;       // CTAs per slot of the measure kernel (measure_parts(L))
     unsigned long long* err_bits;  // fields_error result (double bits, max)
     const uint16_t* Jhank;         // FP32 mode: BF16 parts hi, mid, lo of J* as Hankel core matrices,
                                    // [3][hank_cores][8][8] (the tensor-core rebuild's A operand)
@@ -105,8 +109,10 @@ cudaError_t launch_exchange(const JobDev* jobs_dev, int njobs, cudaStream_t st);
 // of its schedule), which lets a captured CUDA graph carry the rebuild every
 // step.
 // anchor: 0 = measure only, 1 = measure and re-anchor the running energy.
+// max_parts: the largest meas_parts among the work items' jobs.
 cudaError_t launch_measure(const JobDev* jobs_dev, const int2* work, int nwork, int anchor, int cond,
-                           size_t smem_bytes, cudaStream_t st);
+                           size_t smem_bytes, int max_parts, cudaStream_t st);
+int measure_parts(int L);  // CTAs per slot of the measure kernel for chain length L
 // FP64 direct rebuild of the fields of every replica of job jobs_dev[0]
 // (grid over element tiles x replicas).  mode 0: write fields; mode 1: compare
 // with the stored fields and fold max |diff| / jtot into err_bits.
