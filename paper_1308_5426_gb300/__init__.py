@@ -41,15 +41,17 @@ def probe(what: str) -> float:
     return v.value
 
 
-SWEEP_VARIANTS = ("auto", "memory", "registers", "global", "direct") + tuple("registers%d" % c for c in range(1, 9))
+SWEEP_VARIANTS = ("auto", "memory", "registers", "global", "direct", "cluster") + tuple(
+    "registers%d" % c for c in range(1, 9))
 
 
 def sweep_variant_code(name):
     """potts_lr_opts.sweep_variant for a variant name: "auto", "memory",
-    "registers", "global", "direct" (the paper's O(L)-per-attempt sweep, FP64)
-    or "registers<c>" (register configuration c = 1..8)."""
-    if name in ("auto", "memory", "registers", "global", "direct"):
-        return {"auto": 0, "memory": 1, "registers": 2, "global": 3, "direct": 4}[name]
+    "registers", "global", "direct" (the paper's O(L)-per-attempt sweep, FP64),
+    "cluster" (FP32: a slot's fields shared by a cluster of 2, 4 or 8 CTAs) or
+    "registers<c>" (register configuration c = 1..8)."""
+    if name in ("auto", "memory", "registers", "global", "direct", "cluster"):
+        return {"auto": 0, "memory": 1, "registers": 2, "global": 3, "direct": 4, "cluster": 5}[name]
     if isinstance(name, str) and name.startswith("registers") and name[9:].isdigit() and 1 <= int(name[9:]) <= 8:
         return 16 + int(name[9:])
     raise ValueError("unknown sweep variant %r" % (name,))

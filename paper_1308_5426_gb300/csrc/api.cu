@@ -138,8 +138,10 @@ int check_opts(const potts_lr_opts* o)
         return fail(POTTS_LR_EINVAL, "precision must be POTTS_LR_FP64 or POTTS_LR_FP32");
     if (o->pair_factor != 1 && o->pair_factor != 2) return fail(POTTS_LR_EINVAL, "pair_factor must be 1 or 2");
     if (o->recompute_every < 0) return fail(POTTS_LR_EINVAL, "recompute_every must be >= 0");
-    if (o->sweep_variant < 0 || (o->sweep_variant > 4 && (o->sweep_variant < 17 || o->sweep_variant > 24)))
-        return fail(POTTS_LR_EINVAL, "sweep_variant must be 0..4 or 17..24");
+    if (o->sweep_variant < 0 || (o->sweep_variant > 5 && (o->sweep_variant < 17 || o->sweep_variant > 24)))
+        return fail(POTTS_LR_EINVAL, "sweep_variant must be 0..5 or 17..24");
+    if (o->sweep_variant == 5 && o->precision != POTTS_LR_FP32)
+        return fail(POTTS_LR_EINVAL, "the cluster sweep (sweep_variant 5) runs in FP32 mode only");
     if (o->sweep_variant == 4 && o->precision != POTTS_LR_FP64)
         return fail(POTTS_LR_EINVAL, "the direct sweep (sweep_variant 4) runs in FP64 mode only");
     if (o->site_order != 0 && o->site_order != 1) return fail(POTTS_LR_EINVAL, "site_order must be 0 or 1");
@@ -167,17 +169,23 @@ cudaError_t rebuild_launch(const potts_lr_t* h, const JobDev* job_dev, int cond,
 
 // the sweep kernel variant of a job: register-resident (per configuration and
 // q) or memory-resident (per precision and shared-memory residency)
+// keys: memory kernel 0..7 (precision, fields and table residency), direct
+// sweep 99, register kernel 100 + 32 configuration + q (132..372), cluster
+// kernel kClusterKey + cluster size
 constexpr int kDirectKey = 99;
+constexpr int kClusterKey = 1000;
 
 int variant_key(const potts_lr_t* h)
 {
     if (h->direct) return kDirectKey;
+    if (h->hj.cl) return kClusterKey + h->hj.cl;
     return h->hj.rf ? 100 + h->hj.rf * 32 + h->q : h->precision * 4 + h->hj.h_smem * 2 + h->hj.j_smem;
 }
 
 cudaError_t launch_variant(int key, const JobDev* jobs, const int2* work, int nwork, int nsweeps, size_t smem,
                            const SweepSched* sched, cudaStream_t st)
 {
+    if (key > kClusterKey) return launch_sweep_cluster(key - kClusterKey, jobs, work, nwork, nsweeps, smem, st);
     if (key >= 100)
         return launch_sweep_rf((key - 100) / 32, (key - 100) % 32, jobs, work, nwork, nsweeps, smem, sched, st);
     if (key == kDirectKey) return launch_sweep_direct(jobs, work, nwork, nsweeps, smem, st);
@@ -446,6 +454,18 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
     h->dj = (JobDev*)(base + o_job);
     h->dwork = (int2*)(base + o_work);
     h->sweep_smem = j.rf ? rf_smem_bytes(j.rf, q, L, h->Lpad) : sweep_smem_bytes(j);
+    // FP32 fields that fit neither registers nor one CTA's shared memory: a
+    // cluster of CTAs shares them (automatic, or asked for with variant 5)
+    if (h->precision == POTTS_LR_FP32 && !j.rf &&
+        ((o.sweep_variant == 0 && !j.h_smem) || o.sweep_variant == 5)) {
+        j.cl = cluster_size_for(L, q, kSmemBudget);
+        if (j.cl) h->sweep_smem = cluster_sweep_smem(L, q, j.cl);
+        else if (o.sweep_variant == 5) {
+            potts_lr_destroy(h);
+            return fail(POTTS_LR_EINVAL, "the cluster sweep holds at most 8 x %zu bytes of fields and spins",
+                        kSmemBudget);
+        }
+    }
     j.random_sites = o.site_order;
     if (o.sweep_variant == 4 || o.site_order == 1) {
         h->direct = true;

@@ -24,6 +24,7 @@ struct JobDev {
     int recompute_every;  // FP32 mode: longest interval K between field rebuilds (0 = on request only)
     int h_smem, j_smem;   // sweep kernel: fields / coupling table staged in shared memory
     int rf;               // FP32 mode: register-resident sweep configuration (0 = none, 1..8)
+    int cl;               // FP32 mode: CTAs of the cluster that shares a slot's fields (0 = none; 2, 4, 8)
     int random_sites;     // direct sweep: attempt m at a site drawn from Philox counter (m, slot, sweep, 3)
     uint32_t key0, key1;  // Philox key (seed low, high)
     double jtot;          // sum_r J*(r)
@@ -148,6 +149,13 @@ size_t sweep_smem_bytes(const JobDev& j);
 size_t direct_sweep_smem_bytes(int L, int Lpad);
 cudaError_t launch_sweep_direct(const JobDev* jobs_dev, const int2* work, int nwork, int nsweeps, size_t smem,
                                 cudaStream_t st);
+
+// Cluster FP32 sweep (sweep_cluster.cu): a slot's fields spread over the
+// shared memory of a cluster of C = 2, 4 or 8 CTAs.
+size_t cluster_sweep_smem(int L, int q, int C);
+int cluster_size_for(int L, int q, size_t budget);  // smallest C whose share fits budget (0: none)
+cudaError_t launch_sweep_cluster(int C, const JobDev* jobs_dev, const int2* work, int nwork, int nsweeps,
+                                 size_t smem, cudaStream_t st);
 
 // Register-resident FP32 sweep (sweep_rf.cuh): configuration 1..8 =
 // (E sites per update thread, update warps) = (1, 7), (2, 7), (5, 7) for

@@ -1,0 +1,311 @@
+// FP32 Metropolis sweep with a slot's fields spread over the shared memory of
+// a thread-block cluster (Eq. 8, Sec. 4.2; the local-field scheme of sweep.cu).
+//
+// Fields of a long chain (q L FP32 words: 320 KB at L = 16384, q = 5) fit no
+// single CTA's shared memory; one CTA working on them in global memory waits
+// on L2 round trips and leaves most SMs idle when a job has fewer slots than
+// the GPU has SMs.  Here the C CTAs of a cluster (C = 2, 4 or 8) share one
+// slot: CTA r holds the fields h[x][i] of every state x for the sites of
+// blocks [r P, (r + 1) P) (P = ceil(nblk / C) blocks of 32 sites), and its
+// spins.  Per block g of the sweep:
+// - the CTA owning the block decides it with warp 0, exactly as the
+//   single-CTA kernel does (corrections for block g-1's flips, in-order scan),
+//   writes the accepted flips (site, a, b) into every CTA's flip list through
+//   distributed shared memory, and brings its own 32 sites up to date;
+// - meanwhile every CTA's update warps apply block g-1's flips to the sites it
+//   holds (all but the block being decided);
+// - one cluster barrier (release / acquire) ends the step.
+// Each field element receives the same FP32 updates in the same order as in
+// the single-CTA kernels, and the decisions are the same, so spins and fields
+// are bit-identical to theirs.  The FP32 energy change is accumulated per lane
+// of the deciding warp in block order; the 32 lane sums move to the next
+// owner's shared memory when a block's owner changes, so the final energy is
+// bit-identical too.
+#include <cooperative_groups.h>
+
+#include "sweep_common.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace plr {
+
+namespace {
+
+constexpr int kClThreads = 512;  // warp 0 decides, warps 1..15 update
+
+// all threads of the cluster: writes before (local and distributed shared
+// memory) visible to every thread after
+__device__ __forceinline__ void cluster_barrier()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+struct ClLayout {
+    // carve-up of the dynamic shared memory (must match the kernel)
+    int Lp;        // local row stride: P * 32 sites
+    size_t o_dacc, o_lk, o_lab, o_lcnt, o_jn, o_h, o_s, bytes;
+    __host__ __device__ ClLayout(int L, int q, int C)
+    {
+        const int nblk = (L + kSiteBlock - 1) / kSiteBlock;
+        const int P = (nblk + C - 1) / C;
+        Lp = P * kSiteBlock;
+        size_t o = 0;
+        o_dacc = o;  // [32] double: the lane energy sums handed to the next owner
+        o += 32 * sizeof(double);
+        o_lk = o;    // [2][32] flip sites
+        o += 2 * kSiteBlock * sizeof(int);
+        o_lab = o;   // [2][32] (a << 8) | b
+        o += 2 * kSiteBlock * sizeof(int);
+        o_lcnt = o;  // [2] flip counts (+ padding)
+        o += 16;
+        o_jn = o;    // J*(r), r < 64, FP32
+        o += kNearTable * sizeof(float);
+        o_h = o;     // [q][Lp] fields of this CTA's sites
+        o += (size_t)q * Lp * sizeof(float);
+        o_s = o;     // [Lp] spins of this CTA's sites
+        o += (size_t)Lp;
+        bytes = (o + 15) & ~(size_t)15;
+    }
+};
+
+// Rank-1 updates of the flips (pk, pab)[0..nf) on this CTA's sites: local
+// element j (site lo + j), j in [0, n) except [x0, x0 + nx):
+// h[a][j] -= J*((lo + j - k) mod L), h[b][j] += J*((lo + j - k) mod L).
+// Four consecutive sites per thread with 16-byte accesses, two groups in
+// flight; the coupling table J runs past L (J[m] = J*(m mod L), m < 2L).
+__device__ __forceinline__ void apply_flips_part(float* __restrict__ h, int Lp, int lo, int n,
+                                                 const float* __restrict__ J, int L, const int* pk, const int* pab,
+                                                 int nf, int x0, int nx, int u)
+{
+    constexpr int nw = kClThreads - 32;
+    const int ng = (n + 3) >> 2;
+    const int g0 = x0 >> 2, g1 = (x0 + nx + 3) >> 2;  // groups of the decided block (x0 % 32 == 0)
+    const int m = ng - (g1 - g0);
+    for (int jg = u; jg < m; jg += 2 * nw) {
+        int j0[2];
+        bool ok[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int gg = jg + e * nw;
+            ok[e] = gg < m;
+            const int gs = ok[e] ? gg : jg;
+            j0[e] = 4 * (gs < g0 ? gs : gs + (g1 - g0));
+        }
+        for (int f = 0; f < nf; ++f) {
+            const int kf = pk[f], af = pab[f] >> 8, bf = pab[f] & 255;
+            float4 xa[2], xb[2], v[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                int r = lo + j0[e] - kf;
+                r += r < 0 ? L : 0;
+                v[e] = make_float4(J[r], J[r + 1], J[r + 2], J[r + 3]);
+                xa[e] = *(const float4*)(h + (size_t)af * Lp + j0[e]);
+                xb[e] = *(const float4*)(h + (size_t)bf * Lp + j0[e]);
+            }
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                if (!ok[e]) continue;
+                xa[e].x -= v[e].x; xa[e].y -= v[e].y; xa[e].z -= v[e].z; xa[e].w -= v[e].w;
+                xb[e].x += v[e].x; xb[e].y += v[e].y; xb[e].z += v[e].z; xb[e].w += v[e].w;
+                *(float4*)(h + (size_t)af * Lp + j0[e]) = xa[e];
+                *(float4*)(h + (size_t)bf * Lp + j0[e]) = xb[e];
+            }
+        }
+    }
+}
+
+// One cluster of C CTAs per work item (blockIdx.x / C); nsweeps sweeps.
+template <int C>
+__global__ void __launch_bounds__(kClThreads, 1) sweep_cluster_kernel(const JobDev* __restrict__ jobs,
+                                                                      const int2* __restrict__ work, int nsweeps)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int2 wk = work[blockIdx.x / C];
+    const JobDev* jp = jobs + wk.x;
+    const int t = wk.y;
+    const int L = jp->L, q = jp->q, Lpad = jp->Lpad, W = jp->W, c = jp->c;
+    const uint32_t key0 = jp->key0, key1 = jp->key1;
+    const int rep = jp->map[t];
+    const double beta = jp->beta[t];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const ClLayout lay(L, q, C);
+    const int Lp = lay.Lp, P = Lp / kSiteBlock;
+    const int lo = rank * Lp;
+    const int n = max(0, min(L, lo + Lp) - lo);  // sites held here
+
+    const float* __restrict__ J = jp->J32d;
+    float* __restrict__ hg = (float*)jp->fields + (size_t)rep * q * Lpad;
+    uint32_t* __restrict__ spins = jp->spins + (size_t)rep * W;
+    double* dacc = (double*)(smem + lay.o_dacc);
+    int* lk = (int*)(smem + lay.o_lk);
+    int* lab = (int*)(smem + lay.o_lab);
+    int* lcnt = (int*)(smem + lay.o_lcnt);
+    float* Jn = (float*)(smem + lay.o_jn);
+    float* h = (float*)(smem + lay.o_h);
+    uint8_t* s = smem + lay.o_s;
+
+    for (int x = 0; x < q; ++x)
+        for (int j = tid; j < n; j += kClThreads) h[(size_t)x * Lp + j] = hg[(size_t)x * Lpad + lo + j];
+    for (int j = tid; j < n; j += kClThreads) {
+        const int i = lo + j;
+        s[j] = (uint8_t)((spins[i >> 3] >> (4 * (i & 7))) & 15u);
+    }
+    if (tid < kNearTable) Jn[tid] = tid < L ? (float)jp->J64d[tid] : 0.0f;
+    if (tid < 2) lcnt[tid] = 0;
+    // every CTA initialised before any flip list arrives from another
+    cluster_barrier();
+
+    const uint32_t n0 = jp->nsweep[t];
+    const float cb32 = (float)(beta * (double)c);
+    const int nblk = (L + kSiteBlock - 1) / kSiteBlock;
+    const int total = nsweeps * nblk;
+    double dE_acc = 0.0;  // warp 0 of the owning CTA: energy change of this lane's flips, in block order
+    unsigned long long nacc = 0;
+    unsigned long long nnear = 0;
+
+    for (int g = 0; g <= total; ++g) {
+        const int pb = (g + 1) & 1;  // list of block g-1 (pending)
+        const int npend = g > 0 ? lcnt[pb] : 0;
+        const int* pk = lk + pb * kSiteBlock;
+        const int* pab = lab + pb * kSiteBlock;
+        const int blk = g < total ? g % nblk : 0;
+        const int owner = g < total ? blk / P : -1;
+        const int k0 = blk * kSiteBlock;
+        const int nv = g < total ? min(kSiteBlock, L - k0) : 0;
+
+        if (warp == 0) {
+            if (owner == rank) {
+                // the lane sums arrive with the first block this CTA owns in a run
+                if (g > 0 && ((g - 1) % nblk) / P != rank) dE_acc = dacc[lane];
+                const int k = k0 + lane;
+                const int kl = k - lo;
+                const bool valid = lane < nv;
+                const uint32_t nsw = n0 + (uint32_t)(g / nblk);
+                int a = 0, b = 0;
+                float nlu = 0.0f, d32 = 0.0f;
+                uint32_t ux1 = 0, ux2 = 0;
+                if (valid) {
+                    a = s[kl];
+                    draw_proposal<false>(k, t, nsw, key0, key1, q, a, b, nlu, ux1, ux2);
+                    d32 = h[(size_t)a * Lp + kl] - h[(size_t)b * Lp + kl];
+                }
+                const int cbuf = g & 1;
+                int* ck = lk + cbuf * kSiteBlock;
+                int* cab = lab + cbuf * kSiteBlock;
+                bool mine;
+                float dmine;
+                const int nf = decide_block<false>(lane, nv, k, L, a, b, nlu, ux1, ux2, d32, 0.0, pk, pab, npend,
+                                                   cb32, 0.0, 0.0f, Jn, nullptr, ck, cab, mine, dmine, nnear);
+                if (mine) {
+                    s[kl] = (uint8_t)b;
+                    dE_acc += (double)((float)c * dmine);
+                }
+                if (lane == 0) {
+                    lcnt[cbuf] = nf;
+                    nacc += (unsigned long long)nf;
+                }
+                // the block's flips to every other CTA of the cluster
+                for (int r = 0; r < C; ++r) {
+                    if (r == rank) continue;
+                    int* rk = cl.map_shared_rank(ck, r);
+                    int* rab = cl.map_shared_rank(cab, r);
+                    if (lane < nf) {
+                        rk[lane] = ck[lane];
+                        rab[lane] = cab[lane];
+                    }
+                    if (lane == 0) cl.map_shared_rank(lcnt, r)[cbuf] = nf;
+                }
+                // hand the lane sums on when the next block belongs to another CTA
+                if (g + 1 < total && ((g + 1) % nblk) / P != rank)
+                    cl.map_shared_rank(dacc, ((g + 1) % nblk) / P)[lane] = dE_acc;
+                __threadfence_cluster();
+                // bring the block's own sites up to date with block g-1's flips
+                if (valid) {
+                    for (int f = 0; f < npend; ++f) {
+                        const int kf = pk[f], af = pab[f] >> 8, bf = pab[f] & 255;
+                        int r = k - kf;
+                        r += r < 0 ? L : 0;
+                        const float v = J[r];
+                        h[(size_t)af * Lp + kl] -= v;
+                        h[(size_t)bf * Lp + kl] += v;
+                    }
+                }
+            }
+        } else if (npend > 0) {
+            // block g-1's flips on this CTA's sites, except the block being decided here
+            const bool here = owner == rank;
+            apply_flips_part(h, Lp, lo, n, J, L, pk, pab, npend, here ? k0 - lo : 0, here ? nv : 0, tid - 32);
+        }
+        cluster_barrier();
+    }
+
+    // write back this CTA's sites (whole packed words: lo is a multiple of 32)
+    for (int w = tid; w < (n + 7) / 8; w += kClThreads) {
+        uint32_t word = 0;
+        for (int m = 0; m < 8; ++m) {
+            const int j = 8 * w + m;
+            if (j < n) word |= (uint32_t)s[j] << (4 * m);
+        }
+        spins[lo / 8 + w] = word;
+    }
+    for (int x = 0; x < q; ++x)
+        for (int j = tid; j < n; j += kClThreads) hg[(size_t)x * Lpad + lo + j] = h[(size_t)x * Lp + j];
+    if (warp == 0 && total > 0 && (nblk - 1) / P == rank) {
+        // this CTA decided the last block: it holds the lane sums
+        for (int o = 16; o > 0; o >>= 1) dE_acc += __shfl_xor_sync(kFullMask, dE_acc, o);
+        if (lane == 0) jp->E[rep] += dE_acc;
+    }
+    if (tid == 0) {
+        if (rank == 0) jp->nsweep[t] = n0 + (uint32_t)nsweeps;
+        if (nacc) atomicAdd(&jp->acc_flip[t], nacc);
+        if (nnear) atomicAdd(&jp->near[0], nnear);
+    }
+}
+
+template <int C>
+cudaError_t launch_c(const JobDev* jobs_dev, const int2* work, int nwork, int nsweeps, size_t smem, cudaStream_t st)
+{
+    auto k = sweep_cluster_kernel<C>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(nwork * C));
+    cfg.blockDim = dim3(kClThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, jobs_dev, work, nsweeps);
+}
+
+}  // namespace
+
+size_t cluster_sweep_smem(int L, int q, int C) { return ClLayout(L, q, C).bytes; }
+
+int cluster_size_for(int L, int q, size_t budget)
+{
+    for (int C = 2; C <= 8; C *= 2)
+        if (cluster_sweep_smem(L, q, C) <= budget) return C;
+    return 0;
+}
+
+cudaError_t launch_sweep_cluster(int C, const JobDev* jobs_dev, const int2* work, int nwork, int nsweeps,
+                                 size_t smem, cudaStream_t st)
+{
+    if (nwork <= 0 || nsweeps <= 0) return cudaSuccess;
+    switch (C) {
+    case 2: return launch_c<2>(jobs_dev, work, nwork, nsweeps, smem, st);
+    case 4: return launch_c<4>(jobs_dev, work, nwork, nsweeps, smem, st);
+    case 8: return launch_c<8>(jobs_dev, work, nwork, nsweeps, smem, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace plr

@@ -1,6 +1,6 @@
 """Autotuner of the sweep kernel's shape: for a job shape (L, q, precision) it
 times every sweep variant that can hold it -- fields in shared memory, in
-global memory, and each register configuration (E sites per update thread x
+global memory, shared by a cluster of CTAs, and each register configuration (E sites per update thread x
 update warps) -- on this GPU and keeps the fastest.
 
 All variants give bit-identical results, so the choice affects speed only.
@@ -25,7 +25,8 @@ def candidates(L, q, precision):
     """Variant names that can hold a job of this shape."""
     if precision == "fp64":
         return ["memory", "global"]
-    return ["memory", "global"] + [v for v in SWEEP_VARIANTS if v.startswith("registers") and v != "registers"]
+    return ["memory", "global", "cluster"] + [v for v in SWEEP_VARIANTS
+                                               if v.startswith("registers") and v != "registers"]
 
 
 def _time_variant(L, q, sigma, temps, variant, precision, sweeps, warm, torch):

@@ -162,3 +162,39 @@ def test_shared_and_global_field_residency_agree(plr, precision, L, q, sigma, R)
         np.testing.assert_array_equal(jobs[0].spins(), j.spins())
         np.testing.assert_array_equal(jobs[0].fields(), j.fields())
         np.testing.assert_array_equal(jobs[0].running_energy(), j.running_energy())
+
+
+@pytest.mark.parametrize("L,q,sigma,R,rounds", [
+    (2048, 5, 0.4, 3, 12),    # asked for explicitly: two CTAs, 32 blocks each
+    (10000, 7, 0.5, 3, 6),    # automatic, two CTAs, ragged last block
+    (16384, 12, 0.6, 2, 4),   # four CTAs
+    (24000, 16, 0.3, 2, 2),   # eight CTAs
+])
+def test_cluster_sweep_equals_global_sweep(plr, L, q, sigma, R, rounds):
+    """A slot's fields spread over the shared memory of a CTA cluster run the
+    same arithmetic as the single-CTA sweep with the fields in global memory:
+    spins, fields, running energies and counters agree bit for bit after
+    sweeps, exchanges and tensor-core rebuilds."""
+    temps = workloads.geometric_ratios(R, 0.05, 1.0) * oracle.jtot(L, sigma)
+    a = plr.Job(L, q, sigma, temps, 23, precision="fp32", recompute_every=3, sweep_variant="global")
+    b = plr.Job(L, q, sigma, temps, 23, precision="fp32", recompute_every=3, sweep_variant="cluster")
+    for _ in range(rounds):
+        for j in (a, b):
+            j.sweep(1)
+            j.exchange()
+    a.sweep(2)
+    b.sweep(2)
+    np.testing.assert_array_equal(a.spins(), b.spins())
+    np.testing.assert_array_equal(a.fields(), b.fields())
+    np.testing.assert_array_equal(a.running_energy(), b.running_energy())
+    np.testing.assert_array_equal(a.stats()["acc_flip"], b.stats()["acc_flip"])
+    a.close()
+    b.close()
+
+
+def test_cluster_sweep_rejects_fp64_and_oversize(plr):
+    temps = np.linspace(1.0, 2.0, 2)
+    with pytest.raises(plr.PottsError):
+        plr.Job(1024, 5, 0.5, temps, 1, precision="fp64", sweep_variant="cluster")
+    with pytest.raises(plr.PottsError):  # 4 MB of fields per slot: more than eight CTAs hold
+        plr.Job(65536, 16, 0.5, temps, 1, precision="fp32", sweep_variant="cluster")

@@ -9,18 +9,19 @@ from paper_1308_5426_gb300.tune import candidates
 
 
 def test_variant_codes():
-    assert [sweep_variant_code(v) for v in ("auto", "memory", "registers", "global", "direct")] == [0, 1, 2, 3, 4]
+    assert [sweep_variant_code(v) for v in ("auto", "memory", "registers", "global", "direct", "cluster")] == [
+        0, 1, 2, 3, 4, 5]
     assert [sweep_variant_code("registers%d" % c) for c in range(1, 9)] == list(range(17, 25))
     for bad in ("registers0", "registers9", "fast", 5):
         with pytest.raises(ValueError):
             sweep_variant_code(bad)
-    assert len(SWEEP_VARIANTS) == 13
+    assert len(SWEEP_VARIANTS) == 14
 
 
 def test_candidates():
     assert candidates(1000, 5, "fp64") == ["memory", "global"]
     c = candidates(1000, 5, "fp32")
-    assert c[:2] == ["memory", "global"] and c[2:] == ["registers%d" % k for k in range(1, 9)]
+    assert c[:3] == ["memory", "global", "cluster"] and c[3:] == ["registers%d" % k for k in range(1, 9)]
 
 
 @pytest.fixture(scope="module")
