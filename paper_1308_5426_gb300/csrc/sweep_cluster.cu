@@ -71,45 +71,54 @@ struct ClLayout {
 // Rank-1 updates of the flips (pk, pab)[0..nf) on this CTA's sites: local
 // element j (site lo + j), j in [0, n) except [x0, x0 + nx):
 // h[a][j] -= J*((lo + j - k) mod L), h[b][j] += J*((lo + j - k) mod L).
-// Four consecutive sites per thread with 16-byte accesses, two groups in
-// flight; the coupling table J runs past L (J[m] = J*(m mod L), m < 2L).
+// One site per thread with consecutive threads on consecutive sites (the
+// field rows and the coupling table are read without bank conflicts or
+// misaligned vectors), four sites in flight per thread (stride nw), all flips
+// applied to those four before moving on.
 __device__ __forceinline__ void apply_flips_part(float* __restrict__ h, int Lp, int lo, int n,
                                                  const float* __restrict__ J, int L, const int* pk, const int* pab,
                                                  int nf, int x0, int nx, int u)
 {
     constexpr int nw = kClThreads - 32;
-    const int ng = (n + 3) >> 2;
-    const int g0 = x0 >> 2, g1 = (x0 + nx + 3) >> 2;  // groups of the decided block (x0 % 32 == 0)
-    const int m = ng - (g1 - g0);
-    for (int jg = u; jg < m; jg += 2 * nw) {
-        int j0[2];
-        bool ok[2];
+    constexpr int G = 4;
+    const int m = n - nx;
+    int j = u;
+    for (; j + (G - 1) * nw < m; j += G * nw) {
+        int idx[G];
 #pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const int gg = jg + e * nw;
-            ok[e] = gg < m;
-            const int gs = ok[e] ? gg : jg;
-            j0[e] = 4 * (gs < g0 ? gs : gs + (g1 - g0));
+        for (int e = 0; e < G; ++e) {
+            const int jj = j + e * nw;
+            idx[e] = jj < x0 ? jj : jj + nx;
         }
         for (int f = 0; f < nf; ++f) {
             const int kf = pk[f], af = pab[f] >> 8, bf = pab[f] & 255;
-            float4 xa[2], xb[2], v[2];
+            float* __restrict__ ha = h + (size_t)af * Lp;
+            float* __restrict__ hb = h + (size_t)bf * Lp;
+            float v[G], xa[G], xb[G];
 #pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                int r = lo + j0[e] - kf;
+            for (int e = 0; e < G; ++e) {
+                int r = lo + idx[e] - kf;
                 r += r < 0 ? L : 0;
-                v[e] = make_float4(J[r], J[r + 1], J[r + 2], J[r + 3]);
-                xa[e] = *(const float4*)(h + (size_t)af * Lp + j0[e]);
-                xb[e] = *(const float4*)(h + (size_t)bf * Lp + j0[e]);
+                v[e] = J[r];
+                xa[e] = ha[idx[e]];
+                xb[e] = hb[idx[e]];
             }
 #pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                if (!ok[e]) continue;
-                xa[e].x -= v[e].x; xa[e].y -= v[e].y; xa[e].z -= v[e].z; xa[e].w -= v[e].w;
-                xb[e].x += v[e].x; xb[e].y += v[e].y; xb[e].z += v[e].z; xb[e].w += v[e].w;
-                *(float4*)(h + (size_t)af * Lp + j0[e]) = xa[e];
-                *(float4*)(h + (size_t)bf * Lp + j0[e]) = xb[e];
+            for (int e = 0; e < G; ++e) {
+                ha[idx[e]] = xa[e] - v[e];
+                hb[idx[e]] = xb[e] + v[e];
             }
+        }
+    }
+    for (; j < m; j += nw) {
+        const int i = j < x0 ? j : j + nx;
+        for (int f = 0; f < nf; ++f) {
+            const int kf = pk[f], af = pab[f] >> 8, bf = pab[f] & 255;
+            int r = lo + i - kf;
+            r += r < 0 ? L : 0;
+            const float v = J[r];
+            h[(size_t)af * Lp + i] -= v;
+            h[(size_t)bf * Lp + i] += v;
         }
     }
 }

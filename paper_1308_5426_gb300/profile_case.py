@@ -8,6 +8,7 @@ cases:
   precision_fp32  L=4096 q=8 R=128, FP32 (register-resident sweep), 3 sweeps
   rebuild_fp32  L=4096 q=8 R=128, FP32: 3 tensor-core field rebuilds + measurements
   long_fp32     one job L=16384 q=5 R=64, FP32, fields in global memory (memory kernel), 3 sweeps
+  long_fp32_cluster  the same job with its fields shared by a two-CTA cluster, 3 sweeps
 Each case builds its jobs, runs, synchronises and exits 0; inputs are the
 seeded workloads of paper_1308_5426_gb300.workloads.
 """
@@ -23,11 +24,11 @@ def main(argv):
         specs, prec, nsw = workloads.chains_jobs(), case[-4:], 4
     elif case == "precision_fp32":
         specs, prec, nsw = [workloads.precision_job("fp32")], "fp32", 3
-    elif case == "long_fp32":
+    elif case in ("long_fp32", "long_fp32_cluster"):
         from paper_1308_5426_gb300.workloads import geometric_ratios
         L, q = 16384, 5
         j = plr.Job(L, q, 0.4, geometric_ratios(64, 0.05, 1.0) * plr.jtot(L, 0.4), 3, precision="fp32",
-                    recompute_every=0, sweep_variant="memory")
+                    recompute_every=0, sweep_variant="memory" if case == "long_fp32" else "cluster")
         for _ in range(3):
             j.sweep(1)
             j.exchange()
