@@ -90,8 +90,10 @@ typedef struct {
                             about 24000); FP32 mode: 5 = the slot's fields spread over
                             the shared memory of a cluster of 2, 4 or 8 CTAs (the
                             smallest that holds them; EINVAL if 8 do not; chosen by 0
-                            where the fields fit neither registers nor one CTA's
-                            shared memory); FP32 mode: 16 + c (c = 1..8) = register
+                            where the fields fit no registers and either fit no
+                            single CTA's shared memory or take more than 88 KB of
+                            it with R x C at most the SM count); FP32 mode:
+                            16 + c (c = 1..8) = register
                             configuration c (E sites per update thread x update warps:
                             1x7, 2x7, 5x7, 5x15, 9x15, 16x15, 26x15, 35x15; q at most
                             16, 16, 16, 8, 8, 5, 3, 2; EINVAL if L > 32 x E x warps or q

@@ -41,6 +41,7 @@ int cuda_fail(cudaError_t e, const char* where)
     } while (0)
 
 constexpr size_t kSmemBudget = 220 * 1024;  // dynamic shared memory a sweep CTA may take
+constexpr size_t kClusterFieldBytes = 88 * 1024;  // FP32 fields above this go to a cluster (see create)
 constexpr uint32_t kStateMagic = 0x31524c50u; // "PLR1"
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -454,16 +455,24 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
     h->dj = (JobDev*)(base + o_job);
     h->dwork = (int2*)(base + o_work);
     h->sweep_smem = j.rf ? rf_smem_bytes(j.rf, q, L, h->Lpad) : sweep_smem_bytes(j);
-    // FP32 fields that fit neither registers nor one CTA's shared memory: a
-    // cluster of CTAs shares them (automatic, or asked for with variant 5)
-    if (h->precision == POTTS_LR_FP32 && !j.rf &&
-        ((o.sweep_variant == 0 && !j.h_smem) || o.sweep_variant == 5)) {
-        j.cl = cluster_size_for(L, q, kSmemBudget);
-        if (j.cl) h->sweep_smem = cluster_sweep_smem(L, q, j.cl);
-        else if (o.sweep_variant == 5) {
-            potts_lr_destroy(h);
-            return fail(POTTS_LR_EINVAL, "the cluster sweep holds at most 8 x %zu bytes of fields and spins",
-                        kSmemBudget);
+    // FP32 fields that fit no registers: a cluster of CTAs shares them when
+    // they fit no single CTA's shared memory, or fill most of one (then one
+    // CTA per SM sweeps the slot with few update warps) while the job's
+    // clusters fit on the GPU at once (measured: 2-2.6x faster at 64 slots;
+    // on a GPU already filled by many jobs' slots, about even); or when asked
+    // for (variant 5)
+    if (h->precision == POTTS_LR_FP32 && !j.rf && (o.sweep_variant == 0 || o.sweep_variant == 5)) {
+        const int C = cluster_size_for(L, q, kSmemBudget);
+        const bool big = (size_t)q * h->Lpad * 4 > kClusterFieldBytes;
+        const bool fits_gpu = (long long)R * C <= (long long)std::max(1, device_sm_count());
+        if (o.sweep_variant == 5 || (C && (!j.h_smem || (big && fits_gpu)))) {
+            if (!C) {
+                potts_lr_destroy(h);
+                return fail(POTTS_LR_EINVAL, "the cluster sweep holds at most 8 x %zu bytes of fields and spins",
+                            kSmemBudget);
+            }
+            j.cl = C;
+            h->sweep_smem = cluster_sweep_smem(L, q, C);
         }
     }
     j.random_sites = o.site_order;
