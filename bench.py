@@ -342,26 +342,24 @@ def timed_device(plr, torch, specs, steps, warmup, dev, with_events=True, varian
 
 def timed_e2e(plr, torch, specs, steps, warmup, dev):
     """Through the public API with host buffers: each step restores every
-    chain from a pinned host checkpoint (H2D), runs 10 sweeps + exchanges,
-    measures into host arrays (D2H) and checkpoints back (D2H)."""
+    chain from a pinned host checkpoint (H2D, one batch call), runs 10 sweeps +
+    exchanges, measures into host arrays (D2H) and checkpoints every chain back
+    (D2H, one batch call)."""
     st = torch.cuda.Stream(device=dev)
     jobs = make_jobs(plr, specs, st.cuda_stream)
     batch = plr.Batch(jobs, stream=st.cuda_stream)
-    sizes = [j.state_size() for j in jobs]
-    bufs = [torch.empty(n, dtype=torch.uint8, pin_memory=True) for n in sizes]
-    for j, b, n in zip(jobs, bufs, sizes):
-        j.get_state_into(b.data_ptr(), n)
+    size = batch.state_size()  # every chain's checkpoint, back to back
+    buf = torch.empty(size, dtype=torch.uint8, pin_memory=True)
+    batch.get_state_into(buf.data_ptr(), size)
     E = np.zeros(batch.nslots)
     M = np.zeros(batch.nslots)
     att_step = SWEEPS_PER_STEP * sum(s.L * s.R for s in specs)
 
     def step():
-        for j, b, n in zip(jobs, bufs, sizes):
-            j.set_state_from(b.data_ptr(), n)
+        batch.set_state_from(buf.data_ptr(), size)
         batch.run(SWEEPS_PER_STEP, SWEEPS_PER_STEP)
         E[:], M[:] = batch.measure()
-        for j, b, n in zip(jobs, bufs, sizes):
-            j.get_state_into(b.data_ptr(), n)
+        batch.get_state_into(buf.data_ptr(), size)
 
     for _ in range(warmup):
         step()
@@ -371,8 +369,8 @@ def timed_e2e(plr, torch, specs, steps, warmup, dev):
         step()
     torch.cuda.synchronize(dev)
     dt = time.perf_counter() - t0
-    h2d = sum(sizes)
-    d2h = sum(sizes) + 2 * 8 * batch.nslots
+    h2d = size
+    d2h = size + 2 * 8 * batch.nslots
     batch.close()
     for j in jobs:
         j.close()

@@ -225,6 +225,18 @@ int potts_lr_batch_measure_device(potts_lr_batch_t* b, double* E, double* M);
 int potts_lr_batch_sync(potts_lr_batch_t* b);
 void potts_lr_batch_destroy(potts_lr_batch_t* b);
 
+/* Checkpoint of every job of the batch in one call: the jobs' checkpoints
+ * (each exactly what potts_lr_get_state writes for that job) back to back in
+ * job order, len = potts_lr_batch_state_size bytes.  All copies are issued on
+ * the batch stream with one synchronisation at the end (pinned host memory
+ * makes them run at link speed).  potts_lr_batch_set_state checks every job's
+ * part (size, L, q, R, precision, slot map) before it changes any device
+ * memory; a mismatch returns ESTATE and leaves every job as it was.  Errors:
+ * EINVAL (NULL), ESTATE (len or a part does not match), ECUDA. */
+int potts_lr_batch_state_size(potts_lr_batch_t* b, size_t* len);
+int potts_lr_batch_get_state(potts_lr_batch_t* b, void* buf, size_t len);
+int potts_lr_batch_set_state(potts_lr_batch_t* b, const void* buf, size_t len);
+
 /* Allocation-free measurement (the paper has no counterpart).  Same energy
  * (Eq. 2 via the distance counts N_r) and magnetisation (Eq. 10) as
  * potts_lr_measure, for callers that cannot allocate device memory and so

@@ -228,6 +228,30 @@ class Batch:
     def sync(self):
         _lib.check(self._lib.potts_lr_batch_sync(self._h))
 
+    def state_size(self) -> int:
+        """Bytes of the batch checkpoint (the jobs' checkpoints back to back)."""
+        n = ctypes.c_size_t()
+        _lib.check(self._lib.potts_lr_batch_state_size(self._h, ctypes.byref(n)))
+        return n.value
+
+    def get_state_into(self, ptr: int, nbytes: int):
+        """Checkpoint every job into caller memory at host address ptr (e.g.
+        pinned), one synchronisation."""
+        _lib.check(self._lib.potts_lr_batch_get_state(self._h, ctypes.c_void_p(ptr), int(nbytes)))
+
+    def set_state_from(self, ptr: int, nbytes: int):
+        _lib.check(self._lib.potts_lr_batch_set_state(self._h, ctypes.c_void_p(ptr), int(nbytes)))
+
+    def get_state(self) -> bytes:
+        n = self.state_size()
+        buf = ctypes.create_string_buffer(n)
+        self.get_state_into(ctypes.addressof(buf), n)
+        return buf.raw[:n]
+
+    def set_state(self, state: bytes):
+        buf = ctypes.create_string_buffer(state, len(state))
+        self.set_state_from(ctypes.addressof(buf), len(state))
+
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
             self._lib.potts_lr_batch_destroy(self._h)

@@ -25,7 +25,8 @@ EXPORTS = [
     "potts_lr_sync", "potts_lr_destroy", "potts_lr_last_error", "potts_lr_jstar",
     "potts_lr_batch_create", "potts_lr_batch_run", "potts_lr_batch_sync", "potts_lr_batch_destroy",
     "potts_lr_batch_sweep", "potts_lr_batch_exchange", "potts_lr_batch_measure",
-    "potts_lr_batch_measure_device", "potts_lr_probe", "potts_lr_measure_static",
+    "potts_lr_batch_measure_device", "potts_lr_batch_state_size", "potts_lr_batch_get_state",
+    "potts_lr_batch_set_state", "potts_lr_probe", "potts_lr_measure_static",
 ]
 
 
@@ -78,6 +79,9 @@ def load(path: str = LIB_PATH):
         "potts_lr_batch_exchange": [P],
         "potts_lr_batch_measure": [P, P, P],
         "potts_lr_batch_measure_device": [P, P, P],
+        "potts_lr_batch_state_size": [P, P],
+        "potts_lr_batch_get_state": [P, P, SZ],
+        "potts_lr_batch_set_state": [P, P, SZ],
         "potts_lr_probe": [I, P],
         "potts_lr_measure_static": [P, I, I, I, P, I, P, P, P],
     }

@@ -622,16 +622,16 @@ static size_t state_bytes(const potts_lr_t* h)
            R * 8 /*acc_swap*/ + 16 /*near*/ + 8 /*sched*/ + 8 /*drift*/;
 }
 
-int potts_lr_get_state(potts_lr_t* h, void* buf, size_t* len)
+// Checkpoint of one job: a StateHeader, then map, E, spins, fields, sweep
+// counters, flip / swap / near-tie counters, rebuild schedule and drift, in
+// that order (state_bytes(h) bytes).  The *_enqueue helpers only issue
+// asynchronous copies on stream st; the caller synchronises.
+static int state_out_enqueue(potts_lr_t* h, char* p, cudaStream_t st)
 {
-    if (!h || !len) return fail(POTTS_LR_EINVAL, "NULL argument");
-    const size_t need = state_bytes(h);
-    if (!buf) {
-        *len = need;
-        return POTTS_LR_OK;
+    if (h->direct) {  // the direct sweep keeps no fields: rebuild them (FP64, exact) first
+        cudaError_t e = launch_fields_direct(h->dj, h->L, h->R, 0, 0, h->direct_smem, st);
+        if (e != cudaSuccess) return cuda_fail(e, "field rebuild");
     }
-    if (*len < need) return fail(POTTS_LR_ESTATE, "checkpoint buffer too small (%zu < %zu)", *len, need);
-    if (int rc = fresh_fields(h)) return rc;
     StateHeader hd;
     std::memset(&hd, 0, sizeof(hd));
     hd.magic = kStateMagic;
@@ -645,7 +645,6 @@ int potts_lr_get_state(potts_lr_t* h, void* buf, size_t* len)
     hd.seed = h->seed;
     hd.nsweep = h->nsweep;
     hd.nexch = h->nexch;
-    char* p = (char*)buf;
     std::memcpy(p, &hd, sizeof(hd));
     p += sizeof(hd);
     const size_t R = h->R;
@@ -664,34 +663,41 @@ int potts_lr_get_state(potts_lr_t* h, void* buf, size_t* len)
                   {j.sched, 8},
                   {j.drift_bits, 8}};
     for (const Piece& pc : pieces) {
-        PLR_CUDA(cudaMemcpyAsync(p, pc.src, pc.bytes, cudaMemcpyDeviceToHost, h->stream));
+        PLR_CUDA(cudaMemcpyAsync(p, pc.src, pc.bytes, cudaMemcpyDeviceToHost, st));
         p += pc.bytes;
     }
-    PLR_CUDA(cudaStreamSynchronize(h->stream));
-    *len = need;
     return POTTS_LR_OK;
 }
 
-int potts_lr_set_state(potts_lr_t* h, const void* buf, size_t len)
+// a checkpoint of len bytes at p fits job h (size, shape, a permutation as slot map)
+static int state_in_check(const potts_lr_t* h, const char* p, size_t len)
 {
-    if (!h || !buf) return fail(POTTS_LR_EINVAL, "NULL argument");
     if (len != state_bytes(h)) return fail(POTTS_LR_ESTATE, "checkpoint size %zu does not match %zu", len, state_bytes(h));
     StateHeader hd;
-    std::memcpy(&hd, buf, sizeof(hd));
+    std::memcpy(&hd, p, sizeof(hd));
     if (hd.magic != kStateMagic || hd.version != 2 || hd.L != h->L || hd.q != h->q || hd.R != h->R ||
         hd.precision != h->precision || hd.Lpad != h->Lpad)
         return fail(POTTS_LR_ESTATE, "checkpoint does not match this job's L, q, R or precision");
-    const char* p = (const char*)buf + sizeof(hd);
     const size_t R = h->R;
-    const JobDev& j = h->hj;
-    // validate the slot map before touching the device
     std::vector<int> map(R);
-    std::memcpy(map.data(), p, R * 4);
+    std::memcpy(map.data(), p + sizeof(hd), R * 4);
     std::vector<char> seen(R, 0);
     for (size_t t = 0; t < R; ++t) {
         if (map[t] < 0 || (size_t)map[t] >= R || seen[map[t]]) return fail(POTTS_LR_ESTATE, "corrupt slot map");
         seen[map[t]] = 1;
     }
+    return POTTS_LR_OK;
+}
+
+// copies of a checked checkpoint into job h (p must stay valid until st has run them)
+static int state_in_enqueue(potts_lr_t* h, const char* p, cudaStream_t st)
+{
+    StateHeader hd;
+    std::memcpy(&hd, p, sizeof(hd));
+    const char* nexch_src = p + offsetof(StateHeader, nexch);
+    p += sizeof(hd);
+    const size_t R = h->R;
+    const JobDev& j = h->hj;
     struct Piece {
         void* dst;
         size_t bytes;
@@ -706,13 +712,36 @@ int potts_lr_set_state(potts_lr_t* h, const void* buf, size_t len)
                   {j.sched, 8},
                   {j.drift_bits, 8}};
     for (const Piece& pc : pieces) {
-        PLR_CUDA(cudaMemcpyAsync(pc.dst, p, pc.bytes, cudaMemcpyHostToDevice, h->stream));
+        PLR_CUDA(cudaMemcpyAsync(pc.dst, p, pc.bytes, cudaMemcpyHostToDevice, st));
         p += pc.bytes;
     }
-    PLR_CUDA(cudaMemcpyAsync(j.nexch, &hd.nexch, 4, cudaMemcpyHostToDevice, h->stream));
-    PLR_CUDA(cudaStreamSynchronize(h->stream));
+    PLR_CUDA(cudaMemcpyAsync(j.nexch, nexch_src, 4, cudaMemcpyHostToDevice, st));
     h->nsweep = hd.nsweep;
     h->nexch = hd.nexch;
+    return POTTS_LR_OK;
+}
+
+int potts_lr_get_state(potts_lr_t* h, void* buf, size_t* len)
+{
+    if (!h || !len) return fail(POTTS_LR_EINVAL, "NULL argument");
+    const size_t need = state_bytes(h);
+    if (!buf) {
+        *len = need;
+        return POTTS_LR_OK;
+    }
+    if (*len < need) return fail(POTTS_LR_ESTATE, "checkpoint buffer too small (%zu < %zu)", *len, need);
+    if (int rc = state_out_enqueue(h, (char*)buf, h->stream)) return rc;
+    PLR_CUDA(cudaStreamSynchronize(h->stream));
+    *len = need;
+    return POTTS_LR_OK;
+}
+
+int potts_lr_set_state(potts_lr_t* h, const void* buf, size_t len)
+{
+    if (!h || !buf) return fail(POTTS_LR_EINVAL, "NULL argument");
+    if (int rc = state_in_check(h, (const char*)buf, len)) return rc;
+    if (int rc = state_in_enqueue(h, (const char*)buf, h->stream)) return rc;
+    PLR_CUDA(cudaStreamSynchronize(h->stream));
     return POTTS_LR_OK;
 }
 
@@ -1100,6 +1129,53 @@ int potts_lr_batch_run(potts_lr_batch_t* b, int nsteps, int steps_per_graph)
         h->nexch += (uint32_t)nsteps;
     }
     return batch_end(b);
+}
+
+int potts_lr_batch_state_size(potts_lr_batch_t* b, size_t* len)
+{
+    if (!b || !len) return fail(POTTS_LR_EINVAL, "NULL argument");
+    size_t n = 0;
+    for (const potts_lr_t* h : b->jobs) n += state_bytes(h);
+    *len = n;
+    return POTTS_LR_OK;
+}
+
+int potts_lr_batch_get_state(potts_lr_batch_t* b, void* buf, size_t len)
+{
+    if (!b || !buf) return fail(POTTS_LR_EINVAL, "NULL argument");
+    size_t need = 0;
+    for (const potts_lr_t* h : b->jobs) need += state_bytes(h);
+    if (len != need) return fail(POTTS_LR_ESTATE, "batch checkpoint size %zu does not match %zu", len, need);
+    if (int rc = batch_begin(b)) return rc;
+    char* p = (char*)buf;
+    for (potts_lr_t* h : b->jobs) {
+        if (int rc = state_out_enqueue(h, p, b->stream)) return rc;
+        p += state_bytes(h);
+    }
+    PLR_CUDA(cudaStreamSynchronize(b->stream));
+    return POTTS_LR_OK;
+}
+
+int potts_lr_batch_set_state(potts_lr_batch_t* b, const void* buf, size_t len)
+{
+    if (!b || !buf) return fail(POTTS_LR_EINVAL, "NULL argument");
+    size_t need = 0;
+    for (const potts_lr_t* h : b->jobs) need += state_bytes(h);
+    if (len != need) return fail(POTTS_LR_ESTATE, "batch checkpoint size %zu does not match %zu", len, need);
+    // every job's part checked before any device memory changes
+    const char* p = (const char*)buf;
+    for (const potts_lr_t* h : b->jobs) {
+        if (int rc = state_in_check(h, p, state_bytes(h))) return rc;
+        p += state_bytes(h);
+    }
+    if (int rc = batch_begin(b)) return rc;
+    p = (const char*)buf;
+    for (potts_lr_t* h : b->jobs) {
+        if (int rc = state_in_enqueue(h, p, b->stream)) return rc;
+        p += state_bytes(h);
+    }
+    PLR_CUDA(cudaStreamSynchronize(b->stream));
+    return POTTS_LR_OK;
 }
 
 int potts_lr_batch_sync(potts_lr_batch_t* b)

@@ -92,3 +92,61 @@ def test_batch_split_calls_equal_run(plr):
     for x, y in zip(a, b):
         np.testing.assert_array_equal(x.spins(), y.spins())
         np.testing.assert_array_equal(x.fields(), y.fields())
+
+
+def test_batch_checkpoint_resume(plr):
+    """potts_lr_batch_get_state / set_state: the batch checkpoint is the jobs'
+    own checkpoints back to back; restoring it and re-running the same steps
+    reproduces every job bit for bit; a corrupt part is refused before any job
+    changes (a long FP32 job on the cluster kernel included)."""
+    specs = JOBS + [(10000, 7, 0.5, 2, 7, "fp32", 4)]
+    jobs = [_make(plr, s) for s in specs]
+    b = plr.Batch(jobs)
+    b.run(5, 5)
+    b.sync()
+    state = b.get_state()
+    assert len(state) == b.state_size()
+    assert state == b"".join(j.get_state() for j in jobs)
+
+    def snapshot():
+        return [(j.spins(), j.fields(), j.running_energy(), j.stats()["acc_flip"]) for j in jobs]
+
+    b.run(6, 3)
+    b.sync()
+    first = snapshot()
+    b.set_state(state)
+    b.run(6, 3)
+    b.sync()
+    again = snapshot()
+    for x, y in zip(first, again):
+        for u, v in zip(x, y):
+            np.testing.assert_array_equal(u, v)
+
+    # a corrupt slot map in the last job's part: refused, nothing changes
+    bad = bytearray(state)
+    off = len(state) - len(jobs[-1].get_state())  # the last part's header starts here
+    before = snapshot()
+    import struct
+    from paper_1308_5426_gb300 import _lib
+    map_off = off + _header_bytes(plr, jobs[-1])
+    bad[map_off:map_off + 8] = struct.pack("<ii", 0, 0)  # slot 0 and 1 -> replica 0 twice
+    with pytest.raises(plr.PottsError) as e:
+        b.set_state(bytes(bad))
+    assert e.value.code == _lib.ESTATE
+    after = snapshot()
+    for x, y in zip(before, after):
+        for u, v in zip(x, y):
+            np.testing.assert_array_equal(u, v)
+    b.close()
+    for j in jobs:
+        j.close()
+
+
+def _header_bytes(plr, job):
+    """Size of a job checkpoint's header: the checkpoint minus its arrays."""
+    R, L, q = job.R, job.L, job.q
+    W = (L + 7) // 8
+    Lpad = (L + 31) // 32 * 32
+    w = 8 if job.precision == "fp64" else 4
+    arrays = R * 4 + R * 8 + R * W * 4 + R * q * Lpad * w + R * 4 + R * 8 + R * 8 + 16 + 8 + 8
+    return len(job.get_state()) - arrays
