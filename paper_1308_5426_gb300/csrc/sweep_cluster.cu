@@ -74,7 +74,8 @@ struct ClLayout {
 // One site per thread with consecutive threads on consecutive sites (the
 // field rows and the coupling table are read without bank conflicts or
 // misaligned vectors), four sites in flight per thread (stride nw), all flips
-// applied to those four before moving on.
+// applied to those four before moving on.  J is the doubled table (J[m] =
+// J*(m mod L), m < 2L).
 __device__ __forceinline__ void apply_flips_part(float* __restrict__ h, int Lp, int lo, int n,
                                                  const float* __restrict__ J, int L, const int* pk, const int* pab,
                                                  int nf, int x0, int nx, int u)
@@ -84,11 +85,12 @@ __device__ __forceinline__ void apply_flips_part(float* __restrict__ h, int Lp, 
     const int m = n - nx;
     int j = u;
     for (; j + (G - 1) * nw < m; j += G * nw) {
-        int idx[G];
+        int idx[G], r0[G];
 #pragma unroll
         for (int e = 0; e < G; ++e) {
             const int jj = j + e * nw;
             idx[e] = jj < x0 ? jj : jj + nx;
+            r0[e] = lo + idx[e] + L;  // J[r0 - k] = J*((lo + idx - k) mod L): the table runs to 2L
         }
         for (int f = 0; f < nf; ++f) {
             const int kf = pk[f], af = pab[f] >> 8, bf = pab[f] & 255;
@@ -97,9 +99,7 @@ __device__ __forceinline__ void apply_flips_part(float* __restrict__ h, int Lp, 
             float v[G], xa[G], xb[G];
 #pragma unroll
             for (int e = 0; e < G; ++e) {
-                int r = lo + idx[e] - kf;
-                r += r < 0 ? L : 0;
-                v[e] = J[r];
+                v[e] = J[r0[e] - kf];
                 xa[e] = ha[idx[e]];
                 xb[e] = hb[idx[e]];
             }
@@ -229,7 +229,6 @@ __global__ void __launch_bounds__(kClThreads, 1) sweep_cluster_kernel(const JobD
                 // hand the lane sums on when the next block belongs to another CTA
                 if (g + 1 < total && ((g + 1) % nblk) / P != rank)
                     cl.map_shared_rank(dacc, ((g + 1) % nblk) / P)[lane] = dE_acc;
-                __threadfence_cluster();
                 // bring the block's own sites up to date with block g-1's flips
                 if (valid) {
                     for (int f = 0; f < npend; ++f) {
