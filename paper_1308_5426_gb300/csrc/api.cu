@@ -75,6 +75,7 @@ struct potts_lr {
     int onehot_blocks;            // FP32: grid width of the rebuild's one-hot kernel
     SweepSched sched;             // placement of the R slots on the SMs
     bool direct;                  // sweeps by the direct O(L) sum: fields are rebuilt on demand
+    bool cl_auto;                 // the cluster sweep was chosen automatically (not asked for)
 };
 
 struct potts_lr_batch {
@@ -472,6 +473,7 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
                             kSmemBudget);
             }
             j.cl = C;
+            h->cl_auto = o.sweep_variant == 0;
             h->sweep_smem = cluster_sweep_smem(L, q, C);
         }
     }
@@ -853,11 +855,25 @@ int potts_lr_batch_create(potts_lr_t* const* jobs, int n, void* cuda_stream, pot
     std::vector<JobDev> hjobs(n);
     std::map<int, std::vector<int2>> works;
     std::map<int, size_t> smem;
+    // A batch whose slots fill the GPU many times over is bound by per-SM
+    // throughput, not by the latency of single slots: there jobs that took the
+    // cluster sweep automatically although their fields fit one CTA's shared
+    // memory sweep with one CTA per slot (measured: about even per SM, and
+    // fewer CTAs; identical results either way).
+    long long total_slots = 0;
+    for (int i = 0; i < n; ++i) total_slots += jobs[i]->R;
+    const bool crowded = total_slots > 16LL * std::max(1, device_sm_count());
     for (int i = 0; i < n; ++i) {
         hjobs[i] = jobs[i]->hj;
-        const int key = variant_key(jobs[i]);
+        int key = variant_key(jobs[i]);
+        size_t sm = jobs[i]->sweep_smem;
+        if (crowded && jobs[i]->cl_auto && jobs[i]->hj.h_smem) {
+            hjobs[i].cl = 0;
+            key = jobs[i]->precision * 4 + 2 + jobs[i]->hj.j_smem;
+            sm = sweep_smem_bytes(hjobs[i]);
+        }
         for (int t = 0; t < jobs[i]->R; ++t) works[key].push_back(make_int2(i, t));
-        smem[key] = std::max(smem[key], jobs[i]->sweep_smem);
+        smem[key] = std::max(smem[key], sm);
         if (jobs[i]->precision == POTTS_LR_FP32 && jobs[i]->K > 0) b->fp32_jobs.push_back(i);
     }
     for (auto& kv : works)

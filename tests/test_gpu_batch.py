@@ -150,3 +150,28 @@ def _header_bytes(plr, job):
     w = 8 if job.precision == "fp64" else 4
     arrays = R * 4 + R * 8 + R * W * 4 + R * q * Lpad * w + R * 4 + R * 8 + R * 8 + 16 + 8 + 8
     return len(job.get_state()) - arrays
+
+
+def test_crowded_batch_equals_alone(plr):
+    """40 jobs of L = 6000, q = 4, R = 64 (2560 slots, more than 16 per SM):
+    alone each sweeps on a CTA cluster (94 KB of fields per slot), in the
+    crowded batch on one CTA per slot; spins, fields and energies agree bit for
+    bit."""
+    L, q, sigma, R, n = 6000, 4, 0.5, 64, 40
+    temps = workloads.geometric_ratios(R, 0.05, 1.0) * oracle.jtot(L, sigma)
+    alone = [plr.Job(L, q, sigma, temps, 100 + i, precision="fp32", recompute_every=0) for i in range(n)]
+    for j in alone:
+        for _ in range(3):
+            j.sweep(1)
+            j.exchange()
+    batched = [plr.Job(L, q, sigma, temps, 100 + i, precision="fp32", recompute_every=0) for i in range(n)]
+    b = plr.Batch(batched)
+    b.run(3, 3)
+    b.sync()
+    for x, y in zip(alone, batched):
+        np.testing.assert_array_equal(x.spins(), y.spins())
+        np.testing.assert_array_equal(x.fields(), y.fields())
+        np.testing.assert_array_equal(x.running_energy(), y.running_energy())
+    b.close()
+    for j in alone + batched:
+        j.close()
