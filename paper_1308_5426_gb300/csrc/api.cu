@@ -43,6 +43,7 @@ int cuda_fail(cudaError_t e, const char* where)
 constexpr size_t kSmemBudget = 220 * 1024;  // dynamic shared memory a sweep CTA may take
 constexpr size_t kClusterFieldBytes = 88 * 1024;  // FP32 fields above this go to a cluster (see create)
 constexpr uint32_t kStateMagic = 0x31524c50u; // "PLR1"
+constexpr uint32_t kStateVersion = 3;          // header + the job's checkpoint block
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -76,6 +77,7 @@ struct potts_lr {
     SweepSched sched;             // placement of the R slots on the SMs
     bool direct;                  // sweeps by the direct O(L) sum: fields are rebuilt on demand
     bool cl_auto;                 // the cluster sweep was chosen automatically (not asked for)
+    size_t state_off, state_len;  // the checkpointed arrays: one block of the arena
 };
 
 struct potts_lr_batch {
@@ -356,17 +358,32 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
         return o2;
     };
     const size_t o_J64 = take(2 * Lp * 8), o_J32 = take(2 * Lp * 4);
-    const size_t o_spins = take((size_t)R * h->W * 4);
-    const size_t o_fields = take((size_t)R * q * Lp * h->wsize);
-    const size_t o_E = take((size_t)R * 8), o_map = take((size_t)R * 4), o_beta = take((size_t)R * 8);
-    const size_t o_nsw = take((size_t)R * 4), o_nex = take(4);
-    const size_t o_accf = take((size_t)R * 8), o_accs = take((size_t)R * 8), o_near = take(16);
+    // the checkpointed arrays, contiguous in checkpoint order (a checkpoint is
+    // a host header and one copy of this block)
+    size_t sb = 0;
+    auto in_block = [&](size_t bytes) {
+        size_t o2 = sb;
+        sb += align256(bytes);
+        return o2;
+    };
+    const size_t r_map = in_block((size_t)R * 4), r_E = in_block((size_t)R * 8);
+    const size_t r_spins = in_block((size_t)R * h->W * 4), r_fields = in_block((size_t)R * q * Lp * h->wsize);
+    const size_t r_nsw = in_block((size_t)R * 4), r_accf = in_block((size_t)R * 8), r_accs = in_block((size_t)R * 8);
+    const size_t r_near = in_block(16), r_sched = in_block(8), r_drift = in_block(8), r_nex = in_block(4);
+    const size_t o_state = take(sb);
+    h->state_off = o_state;
+    h->state_len = sb;
+    const size_t o_map = o_state + r_map, o_E = o_state + r_E, o_spins = o_state + r_spins;
+    const size_t o_fields = o_state + r_fields, o_nsw = o_state + r_nsw, o_accf = o_state + r_accf;
+    const size_t o_accs = o_state + r_accs, o_near = o_state + r_near, o_sched = o_state + r_sched;
+    const size_t o_drift = o_state + r_drift, o_nex = o_state + r_nex;
+    const size_t o_beta = take((size_t)R * 8);
     const size_t o_mE = take((size_t)R * 8), o_mM = take((size_t)R * 8), o_err = take(8);
     const size_t o_mpart = take((size_t)R * kMeasMaxParts * 8), o_mtick = take((size_t)R * 4);
     const size_t o_job = take(sizeof(JobDev)), o_work = take((size_t)R * sizeof(int2));
     const bool tc = h->precision == POTTS_LR_FP32;  // tensor-core rebuild operands
     const size_t o_hank = take(tc ? tc_hank_bytes(L) : 0), o_xoh = take(tc ? tc_onehot_bytes(L, q, R) : 0);
-    const size_t o_status = take(4), o_sched = take(8), o_drift = take(8);
+    const size_t o_status = take(4);
     std::vector<int4> tiles;
     h->tc_tn = tc_tile_width(tc_tile_count(L, q, R, 64), tc_tile_count(L, q, R, 128), device_sm_count());
     if (h->precision == POTTS_LR_FP32) tc_tiles(0, L, q, R, h->tc_tn, tiles);
@@ -616,18 +633,14 @@ int potts_lr_counters(potts_lr_t* h, uint32_t* nsweep, uint32_t* nexch)
     return POTTS_LR_OK;
 }
 
-static size_t state_bytes(const potts_lr_t* h)
-{
-    const size_t R = h->R;
-    return sizeof(StateHeader) + R * 4 /*map*/ + R * 8 /*E*/ + R * h->W * 4 /*spins*/ +
-           R * h->q * (size_t)h->Lpad * h->wsize /*fields*/ + R * 4 /*nsweep*/ + R * 8 /*acc_flip*/ +
-           R * 8 /*acc_swap*/ + 16 /*near*/ + 8 /*sched*/ + 8 /*drift*/;
-}
+static size_t state_bytes(const potts_lr_t* h) { return sizeof(StateHeader) + h->state_len; }
 
-// Checkpoint of one job: a StateHeader, then map, E, spins, fields, sweep
-// counters, flip / swap / near-tie counters, rebuild schedule and drift, in
-// that order (state_bytes(h) bytes).  The *_enqueue helpers only issue
-// asynchronous copies on stream st; the caller synchronises.
+// Checkpoint of one job: a StateHeader, then the job's checkpoint block as it
+// sits in device memory -- map, E, spins, fields, sweep counters, flip / swap /
+// near-tie counters, rebuild schedule, drift and the exchange counter, each at
+// a 256-byte aligned offset in that order (state_bytes(h) bytes in all).  The
+// *_enqueue helpers only issue asynchronous copies on stream st; the caller
+// synchronises.
 static int state_out_enqueue(potts_lr_t* h, char* p, cudaStream_t st)
 {
     if (h->direct) {  // the direct sweep keeps no fields: rebuild them (FP64, exact) first
@@ -637,7 +650,7 @@ static int state_out_enqueue(potts_lr_t* h, char* p, cudaStream_t st)
     StateHeader hd;
     std::memset(&hd, 0, sizeof(hd));
     hd.magic = kStateMagic;
-    hd.version = 2;
+    hd.version = kStateVersion;
     hd.L = h->L;
     hd.q = h->q;
     hd.R = h->R;
@@ -648,26 +661,8 @@ static int state_out_enqueue(potts_lr_t* h, char* p, cudaStream_t st)
     hd.nsweep = h->nsweep;
     hd.nexch = h->nexch;
     std::memcpy(p, &hd, sizeof(hd));
-    p += sizeof(hd);
-    const size_t R = h->R;
-    const JobDev& j = h->hj;
-    struct Piece {
-        const void* src;
-        size_t bytes;
-    } pieces[] = {{j.map, R * 4},
-                  {j.E, R * 8},
-                  {j.spins, R * h->W * 4},
-                  {j.fields, R * h->q * (size_t)h->Lpad * h->wsize},
-                  {j.nsweep, R * 4},
-                  {j.acc_flip, R * 8},
-                  {j.acc_swap, R * 8},
-                  {j.near, 16},
-                  {j.sched, 8},
-                  {j.drift_bits, 8}};
-    for (const Piece& pc : pieces) {
-        PLR_CUDA(cudaMemcpyAsync(p, pc.src, pc.bytes, cudaMemcpyDeviceToHost, st));
-        p += pc.bytes;
-    }
+    PLR_CUDA(cudaMemcpyAsync(p + sizeof(hd), (const char*)h->arena + h->state_off, h->state_len,
+                             cudaMemcpyDeviceToHost, st));
     return POTTS_LR_OK;
 }
 
@@ -677,7 +672,7 @@ static int state_in_check(const potts_lr_t* h, const char* p, size_t len)
     if (len != state_bytes(h)) return fail(POTTS_LR_ESTATE, "checkpoint size %zu does not match %zu", len, state_bytes(h));
     StateHeader hd;
     std::memcpy(&hd, p, sizeof(hd));
-    if (hd.magic != kStateMagic || hd.version != 2 || hd.L != h->L || hd.q != h->q || hd.R != h->R ||
+    if (hd.magic != kStateMagic || hd.version != kStateVersion || hd.L != h->L || hd.q != h->q || hd.R != h->R ||
         hd.precision != h->precision || hd.Lpad != h->Lpad)
         return fail(POTTS_LR_ESTATE, "checkpoint does not match this job's L, q, R or precision");
     const size_t R = h->R;
@@ -696,28 +691,8 @@ static int state_in_enqueue(potts_lr_t* h, const char* p, cudaStream_t st)
 {
     StateHeader hd;
     std::memcpy(&hd, p, sizeof(hd));
-    const char* nexch_src = p + offsetof(StateHeader, nexch);
-    p += sizeof(hd);
-    const size_t R = h->R;
-    const JobDev& j = h->hj;
-    struct Piece {
-        void* dst;
-        size_t bytes;
-    } pieces[] = {{j.map, R * 4},
-                  {j.E, R * 8},
-                  {j.spins, R * h->W * 4},
-                  {j.fields, R * h->q * (size_t)h->Lpad * h->wsize},
-                  {j.nsweep, R * 4},
-                  {j.acc_flip, R * 8},
-                  {j.acc_swap, R * 8},
-                  {j.near, 16},
-                  {j.sched, 8},
-                  {j.drift_bits, 8}};
-    for (const Piece& pc : pieces) {
-        PLR_CUDA(cudaMemcpyAsync(pc.dst, p, pc.bytes, cudaMemcpyHostToDevice, st));
-        p += pc.bytes;
-    }
-    PLR_CUDA(cudaMemcpyAsync(j.nexch, nexch_src, 4, cudaMemcpyHostToDevice, st));
+    PLR_CUDA(cudaMemcpyAsync((char*)h->arena + h->state_off, p + sizeof(hd), h->state_len, cudaMemcpyHostToDevice,
+                             st));
     h->nsweep = hd.nsweep;
     h->nexch = hd.nexch;
     return POTTS_LR_OK;

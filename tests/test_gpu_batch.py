@@ -122,17 +122,22 @@ def test_batch_checkpoint_resume(plr):
         for u, v in zip(x, y):
             np.testing.assert_array_equal(u, v)
 
-    # a corrupt slot map in the last job's part: refused, nothing changes
+    # a corrupt slot map in the last job's part (the map follows the 48-byte
+    # header: magic, version, L, q, R, precision, c, Lpad, seed, nsweep,
+    # nexch): refused, nothing changes
     bad = bytearray(state)
-    off = len(state) - len(jobs[-1].get_state())  # the last part's header starts here
+    off = len(state) - len(jobs[-1].get_state())  # the last part starts here
     before = snapshot()
     import struct
     from paper_1308_5426_gb300 import _lib
-    map_off = off + _header_bytes(plr, jobs[-1])
-    bad[map_off:map_off + 8] = struct.pack("<ii", 0, 0)  # slot 0 and 1 -> replica 0 twice
+    bad[off + 48:off + 56] = struct.pack("<ii", 0, 0)  # slots 0 and 1 -> replica 0 twice
     with pytest.raises(plr.PottsError) as e:
         b.set_state(bytes(bad))
     assert e.value.code == _lib.ESTATE
+    bad = bytearray(state)
+    bad[off + 4:off + 8] = struct.pack("<I", 2)  # an older format version
+    with pytest.raises(plr.PottsError):
+        b.set_state(bytes(bad))
     after = snapshot()
     for x, y in zip(before, after):
         for u, v in zip(x, y):
@@ -140,16 +145,6 @@ def test_batch_checkpoint_resume(plr):
     b.close()
     for j in jobs:
         j.close()
-
-
-def _header_bytes(plr, job):
-    """Size of a job checkpoint's header: the checkpoint minus its arrays."""
-    R, L, q = job.R, job.L, job.q
-    W = (L + 7) // 8
-    Lpad = (L + 31) // 32 * 32
-    w = 8 if job.precision == "fp64" else 4
-    arrays = R * 4 + R * 8 + R * W * 4 + R * q * Lpad * w + R * 4 + R * 8 + R * 8 + 16 + 8 + 8
-    return len(job.get_state()) - arrays
 
 
 def test_crowded_batch_equals_alone(plr):
