@@ -87,7 +87,7 @@ typedef struct {
                             in shared memory; FP64 mode: 4 = the direct sweep of the
                             paper (Sec. 4.2: every proposal sums its O(L) interaction,
                             no fields; same decisions up to rounding of the sum; L up to
-                            about 24000); FP32 mode: 5 = the slot's fields spread over
+                            about 27000); FP32 mode: 5 = the slot's fields spread over
                             the shared memory of a cluster of 2, 4 or 8 CTAs (the
                             smallest that holds them; EINVAL if 8 do not; chosen by 0
                             where the fields fit no registers and either fit no

@@ -500,7 +500,7 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
         h->sweep_smem = direct_sweep_smem_bytes(L, h->Lpad);
         if (h->sweep_smem > kSmemBudget) {
             potts_lr_destroy(h);
-            return fail(POTTS_LR_EINVAL, "the direct sweep keeps J* and the spins in shared memory: L too large");
+            return fail(POTTS_LR_EINVAL, "the direct sweep keeps the spins of its slot in shared memory: L too large");
         }
     }
     h->measure_smem = measure_smem_bytes(L, h->W);
