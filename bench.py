@@ -43,8 +43,9 @@ def parse():
     ap.add_argument("--serve-jobs", type=int, default=32)
     ap.add_argument("--serve-sweeps", type=int, default=100)
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--precision", default=None, choices=[None, "fp64", "fp32"])
+    ap.add_argument("--precision", default=None, choices=[None, "fp64", "fp32", "fx64"])
     ap.add_argument("--no-fp32-compare", action="store_true")
+    ap.add_argument("--no-fx64-compare", action="store_true")
     ap.add_argument("--no-direct-compare", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
@@ -208,6 +209,28 @@ def rf_fits_shape(L, q):
         if L <= maxL and q <= maxq:
             return True
     return False
+
+
+# shared-memory bytes of one FX64 field update (one element of one accepted
+# flip): the two 8-byte field words read and written, the 8-byte coupling read
+FX64_SMEM_BYTES_PER_UPDATE = 5 * 8
+
+
+def fx64_smem_roofline(plr, res, specs):
+    """Shared-memory traffic of the FX64 sweep kernel's field updates (A L
+    element updates per attempt, 40 bytes each) over its average launch time,
+    against the measured shared-memory probe."""
+    att_launch = sum(s.L * s.R for s in specs)
+    sweep_s = float(np.mean(res["sweep_ms"])) / 1e3
+    A, L = res["acceptance"], specs[0].L
+    achieved = att_launch * A * L * FX64_SMEM_BYTES_PER_UPDATE / sweep_s
+    peak = plr.probe("smem")
+    return {"bound": "smem", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None,
+            "kernel": "sweep_kernel<long long> (FX64 fields and table in shared memory)",
+            "work": "A*L element updates per attempt, %d shared-memory bytes each, A=%.4f measured; "
+                    "%d attempts per launch" % (FX64_SMEM_BYTES_PER_UPDATE, A, att_launch),
+            "peak_source": "measured shared-memory probe (potts_lr_probe)", "sweep_ms_avg": sweep_s * 1e3}
 
 
 def alu_peak(kind, sm_max_mhz):
@@ -599,11 +622,11 @@ def main():
     att_launch = sum(s.L * s.R for s in specs)
     sweep_avg_s = float(np.mean(res["sweep_ms"])) / 1e3
     flops_launch = att_launch * A * 2 * L  # the rank-1 field updates: 2L adds per accepted flip
-    peak_adds = alu_peak(prec, ck.get("sm_max_mhz"))
+    peak_adds = alu_peak("fp32" if prec == "fp32" else "fp64", ck.get("sm_max_mhz"))
     achieved = flops_launch / sweep_avg_s
     traffic = profiled_traffic() if (args.workload == "chains" and prec == "fp64") else None
-    measured = plr.probe("fp64_add" if prec == "fp64" else "fp32_add")
-    roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_adds / 1e12, "unit": "TFLOP/s",
+    measured = plr.probe("fp32_add" if prec == "fp32" else "fp64_add")
+    roof = fx64_smem_roofline(plr, res, specs) if prec == "fx64" else {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_adds / 1e12, "unit": "TFLOP/s",
             "frac": achieved / peak_adds, "traffic": traffic,
             "peak_measured_probe": measured / 1e12, "frac_of_measured_probe": achieved / measured,
             "kernel": ("sweep_kernel<double> (fields in shared memory)" if prec == "fp64" else
@@ -613,7 +636,7 @@ def main():
             "peak_source": "unit counts x max SM clock (2 FP64 / 128 FP32 add lanes per SM per clock, 152 SMs)",
             "sweep_ms_avg": sweep_avg_s * 1e3}
     nsms = torch.cuda.get_device_properties(dev).multi_processor_count
-    if att_launch // L < nsms:  # fewer slots than SMs: also against the SMs the slots occupy
+    if att_launch // L < nsms and prec != "fx64":  # fewer slots than SMs: also against the SMs they occupy
         occ = (att_launch // L) / nsms
         roof["frac_of_occupied_sms"] = achieved / (peak_adds * occ)
         roof["occupied_sms"] = att_launch // L
@@ -624,6 +647,14 @@ def main():
         r32 = timed_device(plr, torch, specs32, max(3, args.steps // 3), args.warmup, dev, with_events=False)
         extra["fp32_same_workload"] = {"value": world * r32["steps"] * r32["att_step"] / (r32["step_ms"] / 1e3),
                                        "unit": "attempts/s", "acceptance": r32["acceptance"]}
+    if args.workload == "chains" and not args.no_fx64_compare and prec == "fp64":
+        # the same chains with 64-bit fixed-point fields: exact integer updates,
+        # the same FP64 decisions
+        specsx, _ = workload_specs(args.workload, rank, "fx64")
+        rx = timed_device(plr, torch, specsx, max(3, args.steps // 3), args.warmup, dev)
+        extra["fx64_same_workload"] = {
+            "value": world * rx["steps"] * rx["att_step"] / (rx["step_ms"] / 1e3), "unit": "attempts/s",
+            "acceptance": rx["acceptance"], "roofline": fx64_smem_roofline(plr, rx, specsx)}
     if args.workload == "chains" and not args.no_direct_compare and prec == "fp64":
         # the paper's scheme on the same workload: every proposal sums its O(L)
         # interaction (no fields), FP64
@@ -660,7 +691,7 @@ def main():
         line = {"metric": "spin-flip attempts/s", "value": value, "unit": "attempts/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f64" if prec == "fp64" else "f32", "data": "synthetic", "config": desc,
+                "dtype": {"fp64": "f64", "fp32": "f32", "fx64": "int64"}[prec], "data": "synthetic", "config": desc,
                 "clocks": ck, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
                 "cpu_baseline": cpu, "acceptance": A}
         line.update(extra)

@@ -40,6 +40,20 @@
  *     fields stay within 1e-5 Jtot of exact.  The first interval is
  *     min(recompute_every, max(1, 2500 q / L)).  The schedule lives on the
  *     device, is part of the checkpoint and is the same alone or batched.
+ *   POTTS_LR_FX64 -- fields as 64-bit integers in units of 2^-F, F = 61 - e
+ *     where Jtot < 2^e (F = 58 for Jtot in [4, 8)), built from the couplings
+ *     rounded to that grid, Jx(r) = round(J*(r) 2^F), |Jx(r) 2^-F - J*(r)| <=
+ *     2^-(F+1).  Every field update is an exact integer add, so the fields
+ *     never drift: they are, bit for bit, the direct sums of the rounded
+ *     couplings (potts_lr_fields_recompute leaves them unchanged), and any
+ *     energy difference is within L 2^-(F+1) <= L 2^-61 Jtot of the FP64
+ *     couplings' (below 3e-14 Jtot at L = 65536).  Decisions follow FP64
+ *     mode's rule, the exact difference converted to FP64 once, so
+ *     trajectories equal FP64 mode's except where |beta dE + ln u| is within
+ *     rounding of zero (counted as near ties).  Same memory as FP64 mode; the updates run on the integer pipes
+ *     instead of GB300's narrow FP64 pipe.  sweep_variant 0, 1 or 3.  EINVAL if
+ *     sigma is so small that F would fall below 24.  Energies and fields come
+ *     out in FP64 (fields converted from field units).
  *
  * Errors: every int-returning call returns POTTS_LR_OK (0) or one of the codes
  * below; potts_lr_last_error() gives a message for the calling thread.  A call
@@ -68,13 +82,14 @@ extern "C" {
 
 #define POTTS_LR_FP64 0
 #define POTTS_LR_FP32 1
+#define POTTS_LR_FX64 2
 
 #define POTTS_LR_MAX_Q 16
 
 typedef struct potts_lr potts_lr_t;
 
 typedef struct {
-    int precision;       /* POTTS_LR_FP64 (default) or POTTS_LR_FP32 */
+    int precision;       /* POTTS_LR_FP64 (default), POTTS_LR_FP32 or POTTS_LR_FX64 */
     int recompute_every; /* FP32 mode: longest interval K between tensor-core field
                             rebuilds (default 100; 0 = only on explicit request) */
     int pair_factor;     /* c in Eq. 2: 2 (default) or 1 */
@@ -84,7 +99,8 @@ typedef struct {
                             does not fit: L <= 1120, or L <= 4320 with q <= 8, L <= 7680
                             with q <= 5, L <= 12480 with q <= 3, L <= 16800 with q = 2);
                             either mode: 3 = fields in global memory even where they fit
-                            in shared memory; FP64 mode: 4 = the direct sweep of the
+                            in shared memory (FX64 mode: 0, 1 and 3 only); FP64 mode:
+                            4 = the direct sweep of the
                             paper (Sec. 4.2: every proposal sums its O(L) interaction,
                             no fields; same decisions up to rounding of the sum; L up to
                             about 27000); FP32 mode: 5 = the slot's fields spread over
@@ -140,7 +156,9 @@ int potts_lr_measure_device(potts_lr_t* h, double* E, double* M);
 
 /* Rebuild the local fields from the spins: FP32 mode -- split-BF16 tensor-core
  * product H = C . onehot(S) with FP32 accumulation; FP64 mode -- direct FP64
- * sums.  Re-anchors the running energies from the spins.  Asynchronous. */
+ * sums; FX64 mode -- direct integer sums of the rounded couplings (identical,
+ * bit for bit, to the swept fields).  Re-anchors the running energies from
+ * the spins.  Asynchronous. */
 int potts_lr_fields_recompute(potts_lr_t* h);
 
 /* Largest |h - h_exact| / Jtot over all fields of all slots, h_exact the FP64
@@ -162,7 +180,7 @@ int potts_lr_set_state(potts_lr_t* h, const void* buf, size_t len);
 int potts_lr_get_spins(potts_lr_t* h, uint8_t* out);
 
 /* Local fields of every slot as doubles, out[(t*q + x)*L + i] (host array of
- * R*q*L doubles). Syncs. */
+ * R*q*L doubles; FX64 mode: field units times 2^-F, exact). Syncs. */
 int potts_lr_get_fields(potts_lr_t* h, double* out);
 
 /* Running energies (the value the exchange step uses) of every slot. Syncs. */

@@ -15,9 +15,9 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import FP32, FP64, PottsError  # noqa: F401
+from ._lib import FP32, FP64, FX64, PottsError  # noqa: F401
 
-__all__ = ["Job", "Batch", "jstar", "jtot", "FP32", "FP64", "PottsError"]
+__all__ = ["Job", "Batch", "jstar", "jtot", "FP32", "FP64", "FX64", "PottsError"]
 
 
 def jstar(L: int, sigma: float) -> np.ndarray:
@@ -60,8 +60,9 @@ def sweep_variant_code(name):
 class Job:
     """One PT job on the GPU (potts_lr_create).
 
-    temps: absolute temperatures, ascending (slot order); precision "fp64" or
-    "fp32"; recompute_every: FP32 tensor-core field rebuild interval K;
+    temps: absolute temperatures, ascending (slot order); precision "fp64",
+    "fp32" or "fx64" (64-bit fixed-point fields: exact integer updates, FP64
+    decisions, no drift); recompute_every: FP32 tensor-core field rebuild interval K;
     pair_factor: c of Eq. 2; stream: optional cudaStream_t handle as an int
     (e.g. torch.cuda.current_stream().cuda_stream); sweep_variant: "auto",
     "memory" or "registers" (FP32 field residency), "global" (fields in global

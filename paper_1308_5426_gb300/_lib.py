@@ -13,8 +13,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libpotts_lr.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE = 0, 1, 2, 3, 4, 5
-FP64, FP32 = 0, 1
-PRECISIONS = {"fp64": FP64, "fp32": FP32}
+FP64, FP32, FX64 = 0, 1, 2
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "fx64": FX64}
 
 # every entry point the header declares (checked by the ABI test)
 EXPORTS = [

@@ -138,8 +138,8 @@ double from_bf16(uint16_t b)
 
 int check_opts(const potts_lr_opts* o)
 {
-    if (o->precision != POTTS_LR_FP64 && o->precision != POTTS_LR_FP32)
-        return fail(POTTS_LR_EINVAL, "precision must be POTTS_LR_FP64 or POTTS_LR_FP32");
+    if (o->precision != POTTS_LR_FP64 && o->precision != POTTS_LR_FP32 && o->precision != POTTS_LR_FX64)
+        return fail(POTTS_LR_EINVAL, "precision must be POTTS_LR_FP64, POTTS_LR_FP32 or POTTS_LR_FX64");
     if (o->pair_factor != 1 && o->pair_factor != 2) return fail(POTTS_LR_EINVAL, "pair_factor must be 1 or 2");
     if (o->recompute_every < 0) return fail(POTTS_LR_EINVAL, "recompute_every must be >= 0");
     if (o->sweep_variant < 0 || (o->sweep_variant > 5 && (o->sweep_variant < 17 || o->sweep_variant > 24)))
@@ -154,9 +154,9 @@ int check_opts(const potts_lr_opts* o)
     return POTTS_LR_OK;
 }
 
-// Field rebuild of one job: FP32 mode on the tensor cores where the shape is
-// supported (else the FP64 direct sums rounded to FP32), FP64 mode by direct
-// sums; then the energies are re-anchored from the spins.  job_dev is the
+// Field rebuild of one job: FP32 mode on the tensor cores, FP64 mode by
+// direct sums, FX64 mode by direct integer sums (which reproduce the swept
+// fields bit for bit); then the energies are re-anchored from the spins.  job_dev is the
 // job's descriptor in device memory (its own, or its entry in a batch table).
 cudaError_t rebuild_launch(const potts_lr_t* h, const JobDev* job_dev, int cond, cudaStream_t st)
 {
@@ -292,7 +292,7 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
     h->c = o.pair_factor;
     h->sigma = sigma;
     h->seed = seed;
-    h->wsize = o.precision == POTTS_LR_FP64 ? 8 : 4;
+    h->wsize = o.precision == POTTS_LR_FP32 ? 4 : 8;
     if (o.cuda_stream) {
         h->stream = (cudaStream_t)o.cuda_stream;
         h->own_stream = false;
@@ -311,6 +311,21 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
     double jt = 0.0;
     for (int r = 1; r < L; ++r) jt += J[r];
     h->jtot = jt;
+    // FX64 field grid 2^-F: F = 61 - e with Jtot < 2^e, so every field, being
+    // at most Jtot (+ L/2 units of rounding), stays below 2^62 units
+    const bool fx = h->precision == POTTS_LR_FX64;
+    int fx_bits = 0;
+    if (fx) {
+        int e2 = 0;
+        std::frexp(jt, &e2);  // jt = m 2^e2, m in [0.5, 1)
+        fx_bits = 61 - std::max(e2, 0);
+        if (fx_bits < 24) {
+            potts_lr_destroy(h);
+            return fail(POTTS_LR_EINVAL, "sigma too small for FX64 fields (sum of couplings %g)", jt);
+        }
+    }
+    std::vector<long long> Jfxd(fx ? 2 * (size_t)h->Lpad : 0, 0);
+    for (int m = 0; fx && m < 2 * L; ++m) Jfxd[m] = std::llrint(std::ldexp(J[m % L], fx_bits));
     std::vector<double> J64d(2 * (size_t)h->Lpad, 0.0);
     std::vector<float> J32d(2 * (size_t)h->Lpad, 0.0f);
     for (int m = 0; m < 2 * L; ++m) {
@@ -357,7 +372,7 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
         off += align256(bytes);
         return o2;
     };
-    const size_t o_J64 = take(2 * Lp * 8), o_J32 = take(2 * Lp * 4);
+    const size_t o_J64 = take(2 * Lp * 8), o_J32 = take(2 * Lp * 4), o_Jfx = take(fx ? 2 * Lp * 8 : 0);
     // the checkpointed arrays, contiguous in checkpoint order (a checkpoint is
     // a host header and one copy of this block)
     size_t sb = 0;
@@ -417,6 +432,8 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
     j.jtot = jt;
     j.J64d = (const double*)(base + o_J64);
     j.J32d = (const float*)(base + o_J32);
+    j.Jfxd = fx ? (const long long*)(base + o_Jfx) : nullptr;
+    j.fx_scale = std::ldexp(1.0, -fx_bits);
     j.spins = (uint32_t*)(base + o_spins);
     j.fields = (void*)(base + o_fields);
     j.E = (double*)(base + o_E);
@@ -512,6 +529,9 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
         if ((e = cudaMemsetAsync(h->arena, 0, off, st)) != cudaSuccess) break;
         if ((e = cudaMemcpyAsync((void*)j.J64d, J64d.data(), 2 * Lp * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
         if ((e = cudaMemcpyAsync((void*)j.J32d, J32d.data(), 2 * Lp * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
+        if (fx && (e = cudaMemcpyAsync((void*)j.Jfxd, Jfxd.data(), 2 * Lp * 8, cudaMemcpyHostToDevice, st)) !=
+                      cudaSuccess)
+            break;
         if ((e = cudaMemcpyAsync((void*)j.beta, beta.data(), (size_t)R * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
         if ((e = cudaMemcpyAsync(j.map, map.data(), (size_t)R * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
         if ((e = cudaMemcpyAsync(h->dj, &j, sizeof(JobDev), cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
@@ -752,7 +772,9 @@ int potts_lr_get_fields(potts_lr_t* h, double* out)
             for (int i = 0; i < h->L; ++i) {
                 const size_t src = (size_t)map[t] * per + (size_t)x * h->Lpad + i;
                 out[((size_t)t * h->q + x) * h->L + i] =
-                    h->wsize == 8 ? ((const double*)raw.data())[src] : (double)((const float*)raw.data())[src];
+                    h->precision == POTTS_LR_FP64   ? ((const double*)raw.data())[src]
+                    : h->precision == POTTS_LR_FX64 ? (double)((const long long*)raw.data())[src] * h->hj.fx_scale
+                                                    : (double)((const float*)raw.data())[src];
             }
     return POTTS_LR_OK;
 }

@@ -150,7 +150,9 @@ __global__ void __launch_bounds__(kAuxThreads) exchange_kernel(const JobDev* __r
 // FP64 direct fields of one replica, element tile per CTA:
 //   h[x][i] = sum_{j : s_j = x} J*((i - j) mod L)   (J*(0) = 0 drops j = i),
 // summed over the positions of state x in ascending j.  mode 0 stores the
-// result (as double or float); mode 1 compares it with the stored fields.
+// result (as double or float; FX64 mode: the same sum of the rounded integer
+// couplings, exact in any order); mode 1 compares the stored fields (FX64:
+// converted from field units) with the FP64 sum.
 __global__ void __launch_bounds__(kAuxThreads) fields_direct_kernel(const JobDev* __restrict__ job, int mode,
                                                                     int cond)
 {
@@ -199,15 +201,26 @@ __global__ void __launch_bounds__(kAuxThreads) fields_direct_kernel(const JobDev
     if (i >= L) return;
     const double* Jc = jb.J64d + (L + i);  // Jc[-j] = J*((i - j) mod L)
     double err = 0.0;
+    if (mode == 0 && jb.precision == kPrecFX64) {
+        const long long* Jx = jb.Jfxd + (L + i);
+        for (int x = 0; x < q; ++x) {
+            long long acc = 0;
+            for (int p = offs[x]; p < offs[x + 1]; ++p) acc += Jx[-pos[p]];
+            ((long long*)jb.fields)[((size_t)rep * q + x) * Lpad + i] = acc;
+        }
+        return;
+    }
     for (int x = 0; x < q; ++x) {
         double acc = 0.0;
         for (int p = offs[x]; p < offs[x + 1]; ++p) acc += Jc[-pos[p]];
         const size_t e = ((size_t)rep * q + x) * Lpad + i;
         if (mode == 0) {
-            if (jb.precision == 0) ((double*)jb.fields)[e] = acc;
+            if (jb.precision == kPrecFP64) ((double*)jb.fields)[e] = acc;
             else ((float*)jb.fields)[e] = (float)acc;
         } else {
-            const double cur = jb.precision == 0 ? ((const double*)jb.fields)[e] : (double)((const float*)jb.fields)[e];
+            const double cur = jb.precision == kPrecFP64   ? ((const double*)jb.fields)[e]
+                               : jb.precision == kPrecFX64 ? (double)((const long long*)jb.fields)[e] * jb.fx_scale
+                                                           : (double)((const float*)jb.fields)[e];
             err = fmax(err, fabs(cur - acc));
         }
     }

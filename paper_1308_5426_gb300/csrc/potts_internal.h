@@ -15,6 +15,10 @@ constexpr int kMaxQ = 16;           // largest q (4-bit packed spins)
 constexpr int kMaxL = 65536;        // largest L (16-bit positions in the direct rebuild)
 constexpr int kChunk = 128;         // K sites per chunk of the tensor-core rebuild
 constexpr int kMeasMaxParts = 32;   // largest split of one slot's measurement over CTAs
+// precision modes (JobDev::precision, the C ABI's POTTS_LR_FP64 / FP32 / FX64)
+constexpr int kPrecFP64 = 0;        // FP64 fields
+constexpr int kPrecFP32 = 1;        // FP32 fields, tensor-core rebuilds
+constexpr int kPrecFX64 = 2;        // 64-bit fixed-point fields: exact integer updates
 
 // Everything a kernel needs to know about one job, resident in device memory.
 // Arrays indexed by "replica" follow the configuration; arrays indexed by
@@ -30,8 +34,10 @@ struct JobDev {
     double jtot;          // sum_r J*(r)
     const double* J64d;   // doubled table: J64d[m] = J*(m mod L), m = 0..2L-1
     const float* J32d;    // the same in FP32
+    const long long* Jfxd;  // FX64 mode: the same rounded to the field grid, llrint(J*(m mod L) 2^F)
+    double fx_scale;        // FX64 mode: 2^-F, the value of one field unit
     uint32_t* spins;      // [replica][W] packed, 4 bits per spin, spin i at bits 4(i%8) of word i/8
-    void* fields;         // [replica][q][Lpad], double (FP64) or float (FP32)
+    void* fields;         // [replica][q][Lpad], double (FP64), float (FP32) or long long (FX64, units of 2^-F)
     double* E;            // running energy per replica
     int* map;             // slot -> replica
     const double* beta;   // per slot

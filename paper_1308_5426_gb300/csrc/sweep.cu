@@ -22,7 +22,15 @@
 // (|d32 - d64| <= 1.2e-5 Jtot, see decide_fp64_filter); only when the margin is
 // too small does the lane rebuild d in FP64 and apply the FP64 rule
 // u < exp(-beta dE) itself.  FP32 mode decides in FP32.
+//
+// FX64 mode (T = long long) keeps the fields as integers in units of 2^-F,
+// built from the couplings rounded to that grid: every update is an exact
+// integer add (two 32-bit integer instructions, on pipes 64 times wider than
+// GB300's FP64 pipe), so the fields hold the exact local fields of the
+// rounded couplings whatever the order of the updates.  Decisions are those
+// of FP64 mode, the exact difference converted to FP64 once.
 #include <cmath>
+#include <type_traits>
 
 #include "sweep_common.cuh"
 #include "sweep_sched.cuh"
@@ -167,7 +175,9 @@ template <typename T, bool HS, bool JS>
 __device__ __forceinline__ void sweep_item(const JobDev* __restrict__ jobs, const int2 wk, int nsweeps,
                                            unsigned char* __restrict__ smem)
 {
-    constexpr bool kFP64 = sizeof(T) == 8;
+    constexpr bool kFP64 = sizeof(T) == 8;  // FP64 rule (FP64 and FX64 modes)
+    constexpr bool kFX = std::is_same<T, long long>::value;
+    constexpr int kMode = kFX ? 2 : (kFP64 ? 1 : 0);
     constexpr int NT = sweep_threads<HS>();
     const JobDev* jp = jobs + wk.x;
     const int t = wk.y;
@@ -177,7 +187,9 @@ __device__ __forceinline__ void sweep_item(const JobDev* __restrict__ jobs, cons
     const double beta = jp->beta[t];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-    const T* __restrict__ Jg = kFP64 ? (const T*)(const void*)jp->J64d : (const T*)(const void*)jp->J32d;
+    const T* __restrict__ Jg = kFX     ? (const T*)(const void*)jp->Jfxd
+                               : kFP64 ? (const T*)(const void*)jp->J64d
+                                       : (const T*)(const void*)jp->J32d;
     T* __restrict__ hg = (T*)jp->fields + (size_t)rep * q * Lpad;
     uint32_t* __restrict__ spins = jp->spins + (size_t)rep * W;
 
@@ -218,6 +230,8 @@ __device__ __forceinline__ void sweep_item(const JobDev* __restrict__ jobs, cons
     const double cb64 = beta * (double)c;
     const float cb32 = (float)cb64;
     const float errd = (float)(2.4e-5 * jp->jtot);
+    const double fxs = kFX ? jp->fx_scale : 1.0;  // value of one field unit
+    const float fxs32 = (float)fxs;                // a power of two: exact
     const int nblk = (L + kSiteBlock - 1) / kSiteBlock;
     const int total = nsweeps * nblk;
 
@@ -242,23 +256,30 @@ __device__ __forceinline__ void sweep_item(const JobDev* __restrict__ jobs, cons
                 int a = 0, b = 0;
                 float nlu = 0.0f, d32 = 0.0f;
                 double base = 0.0;
+                long long basefx = 0;
                 uint32_t ux1 = 0, ux2 = 0;
                 if (valid) {
                     a = s[k];
                     draw_proposal<kFP64>(k, t, n, key0, key1, q, a, b, nlu, ux1, ux2);
                     const T dd = h[(size_t)a * Lpad + k] - h[(size_t)b * Lpad + k];
-                    base = (double)dd;
-                    d32 = (float)dd;
+                    if constexpr (kFX) {
+                        basefx = (long long)dd;
+                        d32 = (float)dd * fxs32;
+                    } else {
+                        base = (double)dd;
+                        d32 = (float)dd;
+                    }
                 }
                 const int cbuf = g & 1;
                 int* ck = lk + cbuf * kSiteBlock;
                 int* cab = lab + cbuf * kSiteBlock;
                 bool mine;
                 float dmine;
-                const int nf = decide_block<kFP64>(lane, nv, k, L, a, b, nlu, ux1, ux2, d32, base, pk, pab, npend,
+                const int nf = decide_block<kMode>(lane, nv, k, L, a, b, nlu, ux1, ux2, d32, base, pk, pab, npend,
                                                    cb32, cb64, errd, Jn,
-                                                   kFP64 ? (const double*)(const void*)J : nullptr, ck, cab, mine,
-                                                   dmine, nnear);
+                                                   kMode == 1 ? (const double*)(const void*)J : nullptr, ck, cab,
+                                                   mine, dmine, nnear, basefx,
+                                                   kFX ? (const long long*)(const void*)J : nullptr, fxs);
                 if (mine) {
                     s[k] = (uint8_t)b;
                     if constexpr (!kFP64) dE_acc += (double)((float)c * dmine);
@@ -324,7 +345,7 @@ __device__ __forceinline__ void sweep_item(const JobDev* __restrict__ jobs, cons
         if constexpr (kFP64) {
             double tot = 0.0;
             for (int w = 0; w < kSweepThreads / 32; ++w) tot += red[w];
-            jp->E[rep] = -0.5 * (double)c * tot;
+            jp->E[rep] = -0.5 * (double)c * tot * fxs;  // fxs: FX64 field units (a power of two)
         } else {
             jp->E[rep] += dE_acc;
         }
@@ -392,21 +413,20 @@ cudaError_t launch_variant(const JobDev* jobs_dev, const int2* work, int nwork, 
 
 size_t sweep_smem_bytes(const JobDev& j)
 {
-    if (j.precision == 0) return SweepSmem<double>::bytes(j.L, j.Lpad, j.q, j.h_smem, j.j_smem);
-    return SweepSmem<float>::bytes(j.L, j.Lpad, j.q, j.h_smem, j.j_smem);
+    return sweep_smem_bytes_for(j.precision, j.L, j.Lpad, j.q, j.h_smem, j.j_smem);
 }
 
 size_t sweep_smem_bytes_for(int precision, int L, int Lpad, int q, int h_smem, int j_smem)
 {
-    if (precision == 0) return SweepSmem<double>::bytes(L, Lpad, q, h_smem, j_smem);
-    return SweepSmem<float>::bytes(L, Lpad, q, h_smem, j_smem);
+    if (precision == kPrecFP32) return SweepSmem<float>::bytes(L, Lpad, q, h_smem, j_smem);
+    return SweepSmem<double>::bytes(L, Lpad, q, h_smem, j_smem);  // FP64 or FX64: 8-byte words
 }
 
 cudaError_t launch_sweep(const JobDev* jobs_dev, const int2* work, int nwork, int nsweeps, int precision,
                          int h_smem, int j_smem, size_t smem, const SweepSched* sched, cudaStream_t st)
 {
     if (nwork <= 0 || nsweeps <= 0) return cudaSuccess;
-    const int v = (precision ? 4 : 0) | (h_smem ? 2 : 0) | (j_smem ? 1 : 0);
+    const int v = precision * 4 + (h_smem ? 2 : 0) + (j_smem ? 1 : 0);
     switch (v) {
     case 0: return launch_variant<double, false, false>(jobs_dev, work, nwork, nsweeps, smem, sched, st);
     case 1: return launch_variant<double, false, true>(jobs_dev, work, nwork, nsweeps, smem, sched, st);
@@ -415,7 +435,12 @@ cudaError_t launch_sweep(const JobDev* jobs_dev, const int2* work, int nwork, in
     case 4: return launch_variant<float, false, false>(jobs_dev, work, nwork, nsweeps, smem, sched, st);
     case 5: return launch_variant<float, false, true>(jobs_dev, work, nwork, nsweeps, smem, sched, st);
     case 6: return launch_variant<float, true, false>(jobs_dev, work, nwork, nsweeps, smem, sched, st);
-    default: return launch_variant<float, true, true>(jobs_dev, work, nwork, nsweeps, smem, sched, st);
+    case 7: return launch_variant<float, true, true>(jobs_dev, work, nwork, nsweeps, smem, sched, st);
+    case 8: return launch_variant<long long, false, false>(jobs_dev, work, nwork, nsweeps, smem, sched, st);
+    case 9: return launch_variant<long long, false, true>(jobs_dev, work, nwork, nsweeps, smem, sched, st);
+    case 10: return launch_variant<long long, true, false>(jobs_dev, work, nwork, nsweeps, smem, sched, st);
+    case 11: return launch_variant<long long, true, true>(jobs_dev, work, nwork, nsweeps, smem, sched, st);
+    default: return cudaErrorInvalidValue;
     }
 }
 

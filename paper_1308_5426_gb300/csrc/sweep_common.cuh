@@ -71,13 +71,21 @@ __device__ __forceinline__ void draw_proposal(int k, int t, uint32_t n, uint32_t
 // one round per accepted flip.  Accepted flips are appended to (ck, cab) in
 // site order; returns their number.  Jn: J*(r) in FP32 for r < 64; J64: the
 // FP64 table (for the exact rule in FP64 mode).
-template <bool kFP64>
+// kMode: 0 = FP32 rule; 1 = FP64 rule (FP32 filter, exact FP64 difference
+// where the filter is unsure); 2 = FX64: the FP64 rule with the exact
+// difference kept in fixed point -- basefx = h[a][k] - h[b][k] in field
+// units, Jfx the rounded integer table, fxs = 2^-F the value of one unit; the
+// corrections are integer adds, so the difference is exact before its one
+// conversion to FP64.
+template <int kMode>
 __device__ __forceinline__ int decide_block(int lane, int nv, int k, int L, int a, int b, float nlu, uint32_t ux1,
                                             uint32_t ux2, float d32, double base64, const int* pk, const int* pab,
                                             int npend, float cb32, double cb64, float errd, const float* Jn,
                                             const double* J64, int* ck, int* cab, bool& mine, float& dmine,
-                                            unsigned long long& nnear)
+                                            unsigned long long& nnear, long long basefx = 0,
+                                            const long long* Jfx = nullptr, double fxs = 0.0)
 {
+    constexpr bool kFP64 = kMode != 0;
     const bool valid = lane < nv;
     // corrections for the previous block's flips, four independent loads at a time
     int f = 0;
@@ -129,19 +137,37 @@ __device__ __forceinline__ int decide_block(int lane, int nv, int k, int L, int 
                 __syncwarp();
                 bool dec = false;
                 if (lane == j) {
-                    double d64 = base64;
-                    for (int g = 0; g < npend; ++g) {
-                        const int kf = pk[g], af = pab[g] >> 8, bf = pab[g] & 255;
-                        int r = k - kf;
-                        r += r < 0 ? L : 0;
-                        const int coef = (a == bf) - (a == af) - (b == bf) + (b == af);
-                        if (coef) d64 += (double)coef * J64[r];
-                    }
+                    double d64;
                     const int nb = __popc(before);
-                    for (int g = 0; g < nb; ++g) {
-                        const int kf = ck[g], af = cab[g] >> 8, bf = cab[g] & 255;
-                        const int coef = (a == bf) - (a == af) - (b == bf) + (b == af);
-                        if (coef) d64 += (double)coef * J64[k - kf];
+                    if constexpr (kMode == 2) {
+                        long long dx = basefx;
+                        for (int g = 0; g < npend; ++g) {
+                            const int kf = pk[g], af = pab[g] >> 8, bf = pab[g] & 255;
+                            int r = k - kf;
+                            r += r < 0 ? L : 0;
+                            const int coef = (a == bf) - (a == af) - (b == bf) + (b == af);
+                            if (coef) dx += (long long)coef * Jfx[r];
+                        }
+                        for (int g = 0; g < nb; ++g) {
+                            const int kf = ck[g], af = cab[g] >> 8, bf = cab[g] & 255;
+                            const int coef = (a == bf) - (a == af) - (b == bf) + (b == af);
+                            if (coef) dx += (long long)coef * Jfx[k - kf];
+                        }
+                        d64 = (double)dx * fxs;
+                    } else {
+                        d64 = base64;
+                        for (int g = 0; g < npend; ++g) {
+                            const int kf = pk[g], af = pab[g] >> 8, bf = pab[g] & 255;
+                            int r = k - kf;
+                            r += r < 0 ? L : 0;
+                            const int coef = (a == bf) - (a == af) - (b == bf) + (b == af);
+                            if (coef) d64 += (double)coef * J64[r];
+                        }
+                        for (int g = 0; g < nb; ++g) {
+                            const int kf = ck[g], af = cab[g] >> 8, bf = cab[g] & 255;
+                            const int coef = (a == bf) - (a == af) - (b == bf) + (b == af);
+                            if (coef) d64 += (double)coef * J64[k - kf];
+                        }
                     }
                     dec = decide_fp64_exact(d64, cb64, unit53(ux1, ux2), nnear);
                 }

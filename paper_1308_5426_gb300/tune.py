@@ -23,7 +23,7 @@ _cache = {}
 
 def candidates(L, q, precision):
     """Variant names that can hold a job of this shape."""
-    if precision == "fp64":
+    if precision in ("fp64", "fx64"):
         return ["memory", "global"]
     return ["memory", "global", "cluster"] + [v for v in SWEEP_VARIANTS
                                                if v.startswith("registers") and v != "registers"]

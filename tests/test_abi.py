@@ -53,6 +53,28 @@ def test_error_paths_without_gpu(lib):
     assert lib.potts_lr_jstar(1, 0.5, None) == _lib.EINVAL
 
 
+def test_option_checks_without_gpu(lib):
+    """Unknown precisions and the kernel variants a precision cannot run are
+    rejected before any device work (FX64 sweeps only on the shared/global
+    memory kernel)."""
+    import ctypes
+    from paper_1308_5426_gb300 import _lib
+    T = np.ones(4)
+    bad = [dict(precision=3), dict(precision=-1), dict(precision=_lib.FX64, sweep_variant=5),
+           dict(precision=_lib.FX64, sweep_variant=4), dict(precision=_lib.FX64, site_order=1),
+           dict(precision=_lib.FP64, sweep_variant=5), dict(precision=_lib.FP32, sweep_variant=4),
+           dict(pair_factor=3), dict(sweep_variant=6)]
+    for kw in bad:
+        o = _lib.Opts()
+        assert lib.potts_lr_default_opts(ctypes.byref(o)) == _lib.OK
+        for k, v in kw.items():
+            setattr(o, k, v)
+        h = ctypes.c_void_p()
+        rc = lib.potts_lr_create(64, 3, 0.5, _lib._ptr(T), 4, 1, ctypes.byref(o), ctypes.byref(h))
+        assert rc == _lib.EINVAL, kw
+        assert h.value is None
+
+
 @pytest.mark.parametrize("L", [2, 3, 64, 1000, 1024, 4096, 16384])
 @pytest.mark.parametrize("sigma", [0.1, 0.2, 0.5, 1.0, 1.5])
 def test_jstar_builder_matches_oracle(lib, L, sigma):
