@@ -5,6 +5,7 @@
 cases:
   chains_fp64   8 chains L=1024 q=5 R=64, FP64 fields (shared-memory sweep kernel), 4 sweeps
   chains_fp32   the same chains in FP32 (register-resident sweep kernel), 4 sweeps
+  chains_fx64   the same chains with 64-bit fixed-point fields (shared-memory sweep kernel), 4 sweeps
   precision_fp32  L=4096 q=8 R=128, FP32 (register-resident sweep), 3 sweeps
   rebuild_fp32  L=4096 q=8 R=128, FP32: 3 tensor-core field rebuilds + measurements
   long_fp32     one job L=16384 q=5 R=64, FP32, fields in global memory (memory kernel), 3 sweeps
@@ -20,7 +21,7 @@ def main(argv):
     from paper_1308_5426_gb300 import workloads
 
     case = argv[1] if len(argv) > 1 else ""
-    if case in ("chains_fp64", "chains_fp32"):
+    if case in ("chains_fp64", "chains_fp32", "chains_fx64"):
         specs, prec, nsw = workloads.chains_jobs(), case[-4:], 4
     elif case == "precision_fp32":
         specs, prec, nsw = [workloads.precision_job("fp32")], "fp32", 3
