@@ -2,7 +2,8 @@
 
 Requests (phase-diagram points: q, sigma, L, temperature grid, seed, sweeps)
 arrive over time.  The loop admits queued requests, first come first served,
-while their field memory (L q R 4 bytes, the FP32 local fields) fits in the
+while their field memory (L q R w bytes: w = 4 for the FP32 local fields of
+the served mixed-precision jobs, 8 for FP64 or FX64 fields) fits in the
 budget; every active job keeps its spins and fields on the device between
 chunks; each chunk runs `chunk` batch steps (one sweep of every slot of every
 active job + one exchange step per job) as one graph-captured batch, then
@@ -41,8 +42,9 @@ class Request:
 
     @property
     def footprint(self) -> int:
-        """Admission footprint: the FP32 field memory L q R 4 bytes."""
-        return self.L * self.q * self.R * 4
+        """Admission footprint: the field memory L q R w bytes, w the field
+        word (4 bytes in FP32 mode, 8 in FP64 and FX64 modes)."""
+        return self.L * self.q * self.R * (4 if self.precision == "fp32" else 8)
 
     @property
     def attempts(self) -> int:
@@ -194,17 +196,23 @@ class Server:
         if not self.active:
             return bool(self.queue)
         ids = tuple(sorted(self.active))
-        if self._batch is None or self._batch_ids != ids:
-            self._drop_batch()
-            self._batch = self.engine.batch([self.active[i][1] for i in ids])
-            self._batch_ids = ids
         n = min(self.chunk, min(self.active[i][0].sweeps - self.results[i].sweeps_done for i in ids))
         t0 = time.perf_counter()
         try:
+            if self._batch is None or self._batch_ids != ids:
+                self._drop_batch()
+                self._batch = self.engine.batch([self.active[i][1] for i in ids])
+                self._batch_ids = ids
             self.engine.run(self._batch, n)
             E, M = self.engine.measure(self._batch)
         except Exception as e:
-            # an engine failure fails the jobs of this chunk, not the service
+            # an engine failure (batch set-up, step or measurement) fails the
+            # jobs of this chunk, not the service
+            if self._batch is not None:
+                try:
+                    self.engine.destroy_batch(self._batch)
+                except Exception:
+                    pass
             for i in ids:
                 req, job = self.active.pop(i)
                 self.results[i].status = "failed"

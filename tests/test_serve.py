@@ -16,12 +16,15 @@ class FakeJob:
 
 
 class FakeEngine:
-    def __init__(self, fail_seeds=(), fail_run_at=None):
+    def __init__(self, fail_seeds=(), fail_run_at=None, fail_batch_at=None):
         self.fail_seeds = set(fail_seeds)
         self.fail_run_at = fail_run_at
+        self.fail_batch_at = fail_batch_at
         self.runs = 0
         self.live = set()
         self.max_live_bytes = 0
+        self.batches = 0
+        self.batches_destroyed = 0
 
     def create(self, req):
         if req.seed in self.fail_seeds:
@@ -32,6 +35,10 @@ class FakeEngine:
         return j
 
     def batch(self, jobs):
+        if self.fail_batch_at is not None and self.batches + 1 == self.fail_batch_at:
+            self.fail_batch_at = None
+            raise RuntimeError("batch set-up failed")
+        self.batches += 1
         return list(jobs)
 
     def run(self, batch, n):
@@ -46,7 +53,7 @@ class FakeEngine:
         return E, -E
 
     def destroy_batch(self, batch):
-        pass
+        self.batches_destroyed += 1
 
     def destroy(self, job):
         self.live.discard(job)
@@ -152,3 +159,37 @@ def test_duplicate_ids_refused():
     srv.submit(_req(0))
     with pytest.raises(ValueError):
         srv.submit(_req(0))
+
+
+def test_footprint_follows_the_field_word():
+    """Admission counts 4-byte FP32 fields and 8-byte FP64 / FX64 fields."""
+    r32 = _req(0, L=100, q=5, R=8)
+    assert r32.footprint == 100 * 5 * 8 * 4
+    for prec in ("fp64", "fx64"):
+        r = Request(rid=1, L=100, q=5, sigma=0.5, temps=np.ones(8), seed=1, sweeps=1, precision=prec)
+        assert r.footprint == 100 * 5 * 8 * 8
+    # a budget that holds the FP32 form of a request but not its FP64 form
+    srv = Server(FakeEngine(), budget_bytes=100 * 5 * 8 * 4, chunk=5, clock=Clock())
+    assert srv.submit(Request(rid=2, L=100, q=5, sigma=0.5, temps=np.ones(8), seed=1, sweeps=1,
+                              precision="fp64")).status == "rejected"
+    assert srv.submit(_req(3, L=100, q=5, R=8)).status == "queued"
+
+
+def test_failed_step_releases_its_batch():
+    """A failing device step destroys the chunk's batch as well as its jobs."""
+    eng = FakeEngine(fail_run_at=2)
+    srv = Server(eng, budget_bytes=10 ** 9, chunk=10, clock=Clock())
+    srv.run([_req(0, sweeps=50), _req(1, sweeps=50)], idle_sleep=0.0)
+    assert eng.batches == eng.batches_destroyed
+    assert not eng.live and srv.used == 0
+
+
+def test_failed_batch_setup_fails_only_that_chunk():
+    """A batch that cannot be set up fails the jobs it would have held; jobs
+    that arrive later are served normally."""
+    eng = FakeEngine(fail_batch_at=1)
+    srv = Server(eng, budget_bytes=10 ** 9, chunk=10, clock=Clock())
+    res = srv.run([_req(0, sweeps=20), _req(1, sweeps=20, arrival=0.5)], idle_sleep=0.0)
+    assert res[0].status == "failed" and "batch set-up" in res[0].error
+    assert res[1].status == "done" and res[1].sweeps_done == 20
+    assert not eng.live and srv.used == 0
