@@ -179,6 +179,49 @@ def test_fx64_batch_and_checkpoint(plr):
     c.close()
 
 
+def test_fx64_full_size_chains_in_bench_configuration(plr):
+    """The eight L=1024, q=5, R=64 chains (seeds 1..8) stepped as one batch, the
+    bench's launch configuration (512 slots, SM placement plan), for 20 steps in
+    FX64 and in FP64: identical spins and acceptance counts at full size;
+    energies and magnetisations of two chains against the oracle's plain double
+    sum on the GPU's configurations; the running energy against the measured
+    one; FX64 fields unchanged by a rebuild."""
+    specs = workloads.chains_jobs()
+
+    def run(prec):
+        jobs = [plr.Job(s.L, s.q, s.sigma, s.ratios * oracle.jtot(s.L, s.sigma), s.seed, precision=prec)
+                for s in specs]
+        b = plr.Batch(jobs)
+        for _ in range(20):
+            b.sweep(1)
+            b.exchange()
+        b.sync()
+        return b, jobs
+
+    bx, jx = run("fx64")
+    b64, j64 = run("fp64")
+    for s, a, c in zip(specs, jx, j64):
+        np.testing.assert_array_equal(a.spins(), c.spins(), err_msg="seed %d" % s.seed)
+        sa, sc = a.stats(), c.stats()
+        np.testing.assert_array_equal(sa["acc_flip"], sc["acc_flip"])
+        np.testing.assert_array_equal(sa["acc_swap"], sc["acc_swap"])
+    for s, a in list(zip(specs, jx))[:2]:
+        temps = s.ratios * oracle.jtot(s.L, s.sigma)
+        E, M = a.measure()
+        o = oracle.Oracle(s.L, s.q, s.sigma, temps, s.seed, fields=False)
+        o.set_spins(a.spins())
+        np.testing.assert_allclose(E, o.energy(), rtol=1e-10)
+        np.testing.assert_allclose(M, o.magnetisation(), rtol=0, atol=1e-14)
+        np.testing.assert_allclose(a.running_energy(), E, rtol=1e-10)
+    F = jx[0].fields()
+    jx[0].fields_recompute()
+    np.testing.assert_array_equal(jx[0].fields(), F)
+    for b in (bx, b64):
+        b.close()
+    for j in jx + j64:
+        j.close()
+
+
 @pytest.mark.parametrize("variant", ["registers", "cluster", "direct", "registers3"])
 def test_fx64_rejects_fp32_and_direct_variants(plr, variant):
     from paper_1308_5426_gb300 import _lib
