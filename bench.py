@@ -216,20 +216,36 @@ def rf_fits_shape(L, q):
 FX64_SMEM_BYTES_PER_UPDATE = 5 * 8
 
 
+def fx64_fields_in_smem(L, q):
+    """Whether the FX64 sweep kernel keeps a slot's fields and coupling table
+    in shared memory: the library's carve-up (table of Lpad + 4 words, q Lpad
+    field words, spins, flip lists, near table, reduction scratch) within its
+    220 KB budget."""
+    lpad = (L + 31) // 32 * 32
+    b = (lpad + 4) * 8 + q * lpad * 8 + lpad + 4 * 32 * 4 + 64 * 4 + 32 * 8 + 16
+    return (b + 15) // 16 * 16 <= 220 * 1024
+
+
 def fx64_smem_roofline(plr, res, specs):
     """Shared-memory traffic of the FX64 sweep kernel's field updates (A L
     element updates per attempt, 40 bytes each) over its average launch time,
-    against the measured shared-memory probe."""
+    against the measured shared-memory probe.  Where the fields sit in global
+    memory the same bytes go to L2 and no shared-memory roofline applies."""
     att_launch = sum(s.L * s.R for s in specs)
     sweep_s = float(np.mean(res["sweep_ms"])) / 1e3
     A, L = res["acceptance"], specs[0].L
     achieved = att_launch * A * L * FX64_SMEM_BYTES_PER_UPDATE / sweep_s
+    work = ("A*L element updates per attempt, %d bytes each, A=%.4f measured; %d attempts per launch"
+            % (FX64_SMEM_BYTES_PER_UPDATE, A, att_launch))
+    if not all(fx64_fields_in_smem(s.L, s.q) for s in specs):
+        return {"bound": None, "achieved_update_bytes_gbs": achieved / 1e9, "traffic": None,
+                "kernel": "sweep_kernel<long long> (FX64 fields in global memory)", "work": work,
+                "note": "fields in global memory: the updates run against L2; no shared-memory roofline",
+                "sweep_ms_avg": sweep_s * 1e3}
     peak = plr.probe("smem")
     return {"bound": "smem", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "GB/s",
             "frac": achieved / peak, "traffic": None,
-            "kernel": "sweep_kernel<long long> (FX64 fields and table in shared memory)",
-            "work": "A*L element updates per attempt, %d shared-memory bytes each, A=%.4f measured; "
-                    "%d attempts per launch" % (FX64_SMEM_BYTES_PER_UPDATE, A, att_launch),
+            "kernel": "sweep_kernel<long long> (FX64 fields and table in shared memory)", "work": work,
             "peak_source": "measured shared-memory probe (potts_lr_probe)", "sweep_ms_avg": sweep_s * 1e3}
 
 
