@@ -75,6 +75,43 @@ def test_option_checks_without_gpu(lib):
         assert h.value is None
 
 
+def test_entry_point_argument_checks_without_gpu(lib):
+    """NULL handles and out-of-range sizes are rejected before any device work:
+    the batch calls, the allocation-free measurement (sizes beyond its fixed
+    scratch included) and the probe."""
+    import ctypes
+    from paper_1308_5426_gb300 import _lib
+    P = ctypes.c_void_p
+    b = P()
+    assert lib.potts_lr_batch_create(None, 1, None, ctypes.byref(b)) == _lib.EINVAL
+    arr = (P * 2)(None, None)
+    assert lib.potts_lr_batch_create(arr, 2, None, ctypes.byref(b)) == _lib.EINVAL
+    assert lib.potts_lr_batch_create(arr, 0, None, ctypes.byref(b)) == _lib.EINVAL
+    assert b.value is None
+    assert lib.potts_lr_batch_run(None, 1, 1) == _lib.EINVAL
+    assert lib.potts_lr_batch_sweep(None, 1) == _lib.EINVAL
+    assert lib.potts_lr_batch_exchange(None) == _lib.EINVAL
+    assert lib.potts_lr_batch_sync(None) == _lib.EINVAL
+    n = ctypes.c_size_t()
+    assert lib.potts_lr_batch_state_size(None, ctypes.byref(n)) == _lib.EINVAL
+    assert lib.potts_lr_measure(None, None, None) == _lib.EINVAL
+    assert lib.potts_lr_fields_recompute(None) == _lib.EINVAL
+    assert lib.potts_lr_exchange(None) == _lib.EINVAL
+    # potts_lr_measure_static(spins, L, q, R, jstar, pair_factor, E, M, stream):
+    # the pointers are never dereferenced on these paths
+    d = P(16)
+    ok = dict(spins=d, L=64, q=3, R=4, jstar=d, c=2, E=d, M=d)
+    for bad in (dict(spins=None), dict(jstar=None), dict(E=None), dict(M=None), dict(L=1), dict(q=1),
+                dict(q=17), dict(R=0), dict(R=4097), dict(c=3)):
+        a = dict(ok, **bad)
+        rc = lib.potts_lr_measure_static(a["spins"], a["L"], a["q"], a["R"], a["jstar"], a["c"], a["E"], a["M"],
+                                         None)
+        assert rc == _lib.EINVAL, bad
+    v = ctypes.c_double()
+    assert lib.potts_lr_probe(3, ctypes.byref(v)) == _lib.EINVAL
+    assert lib.potts_lr_probe(0, None) == _lib.EINVAL
+
+
 @pytest.mark.parametrize("L", [2, 3, 64, 1000, 1024, 4096, 16384])
 @pytest.mark.parametrize("sigma", [0.1, 0.2, 0.5, 1.0, 1.5])
 def test_jstar_builder_matches_oracle(lib, L, sigma):
