@@ -112,8 +112,8 @@ def test_entry_point_argument_checks_without_gpu(lib):
     assert lib.potts_lr_probe(0, None) == _lib.EINVAL
 
 
-@pytest.mark.parametrize("L", [2, 3, 64, 1000, 1024, 4096, 16384])
-@pytest.mark.parametrize("sigma", [0.1, 0.2, 0.5, 1.0, 1.5])
+@pytest.mark.parametrize("L", [2, 3, 64, 1000, 1024, 4096, 16384, 65536])
+@pytest.mark.parametrize("sigma", [0.01, 0.1, 0.2, 0.5, 1.0, 1.5, 3.0])
 def test_jstar_builder_matches_oracle(lib, L, sigma):
     """Library J* (Euler-Maclaurin Hurwitz zeta, own code) vs the oracle's
     (scipy Hurwitz zeta) to 1e-14 relative, and exactly symmetric."""
