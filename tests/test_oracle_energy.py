@@ -31,7 +31,7 @@ def test_worked_example_sigma_one(c):
     np.testing.assert_allclose(o.magnetisation(), [0.0, 0.0, 1.0])
 
 
-@pytest.mark.parametrize("L,q,sigma", [(64, 3, 0.5), (1000, 5, 0.4), (37, 16, 0.1)])
+@pytest.mark.parametrize("L,q,sigma", [(64, 3, 0.5), (1000, 5, 0.4), (37, 16, 0.1), (2, 2, 0.5), (3, 16, 2.0)])
 @pytest.mark.parametrize("c", [1, 2])
 def test_ground_state(L, q, sigma, c):
     """Ordered configuration: E_gs = -(c/2) L Jtot, M = 1 (Eq. 2, Eq. 10)."""
@@ -52,7 +52,8 @@ def test_magnetisation_balanced(L, q):
     assert o.magnetisation()[0] == pytest.approx((q * nmax / L - 1) / (q - 1))
 
 
-@pytest.mark.parametrize("L,q,sigma", [(64, 3, 0.5), (97, 7, 0.3), (256, 2, 0.9)])
+@pytest.mark.parametrize("L,q,sigma", [(64, 3, 0.5), (97, 7, 0.3), (256, 2, 0.9), (2, 2, 0.5), (3, 3, 1.0),
+                                     (33, 16, 0.05)])
 def test_energy_by_distance_counts(L, q, sigma):
     """Second route to Eq. 2: E = -(c/2) sum_r J*(r) N_r with N_r the number of
     ordered pairs at periodic offset r holding equal spins, counted by rolling
