@@ -51,6 +51,11 @@ def _load():
     lib.oracle_get_counters.argtypes = [P, P, P]
     lib.oracle_get_stats.argtypes = [P] * 8
     lib.oracle_philox.argtypes = [P, P, P]
+    lib.oracle_set_overrides.argtypes = [P, P, ctypes.c_int]
+    lib.oracle_set_overrides.restype = ctypes.c_int
+    lib.oracle_get_near_log.argtypes = [P, P, ctypes.c_int]
+    lib.oracle_get_near_log.restype = ctypes.c_uint64
+    lib.oracle_get_adopted.argtypes = [P] * 5
     _lib = lib
     return lib
 
@@ -153,6 +158,35 @@ class Oracle:
 
     def set_counters(self, nsweep, nexch):
         _lib.oracle_set_counters(self._h, int(nsweep), int(nexch))
+
+    def set_overrides(self, events):
+        """Decisions to adopt where the oracle itself sees a near tie (the
+        re-synchronisation of two FP64 implementations whose exp and log round
+        differently): rows {kind (0 Metropolis, 1 exchange), slot t (exchange:
+        pair (t, t+1)), sweep n (exchange: index m), attempt within the sweep
+        (exchange: stage), decision (0/1)}.  Replaces the previous table."""
+        ev = np.ascontiguousarray(np.asarray(events, dtype=np.int32).reshape(-1, 5))
+        if _lib.oracle_set_overrides(self._h, ev.ctypes.data if ev.size else None, int(ev.shape[0])) != 0:
+            raise MemoryError("oracle_set_overrides")
+
+    def near_log(self):
+        """Near-tie events seen so far, rows {kind, slot or pair, sweep or
+        exchange index, attempt or stage, own decision, decision taken}, and
+        the total count (the log keeps the first 4096)."""
+        cap = 4096
+        out = np.zeros((cap, 6), np.int32)
+        n = int(_lib.oracle_get_near_log(self._h, out.ctypes.data, cap))
+        return out[: min(n, cap)].copy(), n
+
+    def adopted(self):
+        """Adopted near-tie decisions: per slot (Metropolis) and for the
+        exchange, all of them and those that reversed the oracle's own."""
+        am = np.zeros(self.R, np.uint64)
+        fm = np.zeros(self.R, np.uint64)
+        ae = np.zeros(1, np.uint64)
+        fe = np.zeros(1, np.uint64)
+        _lib.oracle_get_adopted(self._h, am.ctypes.data, fm.ctypes.data, ae.ctypes.data, fe.ctypes.data)
+        return {"metro": am, "metro_reversed": fm, "exch": int(ae[0]), "exch_reversed": int(fe[0])}
 
     def stats(self):
         R = self.R

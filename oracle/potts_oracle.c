@@ -40,8 +40,19 @@
  *
  * A "near tie" is a decision whose margin |beta dE + ln u| (Metropolis) or
  * |D - ln u| (exchange) is below 1e-9: there rounding differences between two
- * correct FP64 implementations may flip the decision.  They are counted and
- * the first sweep at which one happened is recorded per slot.
+ * correct FP64 implementations may flip the decision.  They are counted, the
+ * first sweep at which one happened is recorded per slot, and each is logged
+ * (kind, slot or pair, sweep or exchange index, attempt or stage, the
+ * oracle's own decision, the decision taken).
+ *
+ * Re-synchronisation at near ties (the reading of Eq. 8 and Eq. 9 for two
+ * implementations whose exp and log round differently): the caller may hand
+ * the oracle a table of decisions taken elsewhere, keyed by (kind, slot or
+ * pair, sweep or exchange index, attempt or stage).  At a decision the oracle
+ * itself counts as a near tie, and only there, it adopts the tabled decision
+ * instead of its own.  Adoptions are counted per slot (and for the exchange),
+ * as are those that reversed the oracle's own decision.  Anywhere else the
+ * table is never consulted, so it cannot hide a real disagreement.
  */
 #include <math.h>
 #include <pthread.h>
@@ -54,6 +65,7 @@
 #define ORC_TAG_EXCH 2u
 #define ORC_TAG_SITE 3u
 #define ORC_NEAR_TIE 1e-9
+#define ORC_LOG_CAP 4096 /* near-tie events kept per job (all are counted) */
 
 /* ---- Philox4x32-10, from the published definition (SC'11, Sec. 3) ---- */
 static void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
@@ -105,6 +117,19 @@ typedef struct {
     int64_t* first_near;  /* per slot: first sweep with a Metropolis near tie, or -1 */
     uint64_t near_exch;
     int64_t first_near_exch; /* first exchange index with a near tie, or -1 */
+    /* near-tie log: [ORC_LOG_CAP][6] = {kind (0 Metropolis, 1 exchange), slot t
+       (exchange: pair (t, t+1)), sweep n (exchange: index m), attempt m within
+       the sweep (exchange: stage), own decision, decision taken} */
+    int32_t* log;
+    uint64_t nlog;        /* events seen (the first ORC_LOG_CAP are kept) */
+    pthread_mutex_t log_mu;
+    /* decisions to adopt at near ties: [novr][5] = {kind, t, index, attempt or
+       stage, decision} */
+    int32_t* ovr;
+    int novr;
+    uint64_t* adopted_metro; /* per slot: near-tie decisions taken from the table */
+    uint64_t* flipped_metro; /* per slot: of those, the ones that reversed the oracle's own */
+    uint64_t adopted_exch, flipped_exch;
 } oracle_t;
 
 static double orc_J(const oracle_t* o, int i, int j)
@@ -151,12 +176,36 @@ static void orc_fields_direct(oracle_t* o, int t)
         }
 }
 
+/* the tabled decision for a near tie at (kind, t, index, attempt), or -1 */
+static int orc_override(const oracle_t* o, int kind, int t, uint32_t index, int attempt)
+{
+    for (int i = 0; i < o->novr; ++i) {
+        const int32_t* e = o->ovr + 5 * (size_t)i;
+        if (e[0] == kind && e[1] == t && (uint32_t)e[2] == index && e[3] == attempt) return e[4] ? 1 : 0;
+    }
+    return -1;
+}
+
+/* append one near-tie event (slots may be swept on several threads) */
+static void orc_log(oracle_t* o, int kind, int t, uint32_t index, int attempt, int own, int taken)
+{
+    pthread_mutex_lock(&o->log_mu);
+    if (o->nlog < ORC_LOG_CAP) {
+        int32_t* e = o->log + 6 * (size_t)o->nlog;
+        e[0] = kind; e[1] = t; e[2] = (int32_t)index; e[3] = attempt; e[4] = own; e[5] = taken;
+    }
+    o->nlog++;
+    pthread_mutex_unlock(&o->log_mu);
+}
+
 void oracle_destroy(oracle_t* o)
 {
     if (!o) return;
     free(o->J); free(o->beta); free(o->s); free(o->E); free(o->h);
     free(o->acc_flip); free(o->att_swap); free(o->acc_swap);
     free(o->near_metro); free(o->first_near);
+    free(o->log); free(o->ovr); free(o->adopted_metro); free(o->flipped_metro);
+    pthread_mutex_destroy(&o->log_mu);
     free(o);
 }
 
@@ -179,8 +228,13 @@ oracle_t* oracle_create(int L, int q, int c, const double* J, int R, const doubl
     o->acc_swap = (uint64_t*)calloc(R, sizeof(uint64_t));
     o->near_metro = (uint64_t*)calloc(R, sizeof(uint64_t));
     o->first_near = (int64_t*)malloc(sizeof(int64_t) * R);
+    o->log = (int32_t*)malloc(sizeof(int32_t) * 6 * ORC_LOG_CAP);
+    o->adopted_metro = (uint64_t*)calloc(R, sizeof(uint64_t));
+    o->flipped_metro = (uint64_t*)calloc(R, sizeof(uint64_t));
+    pthread_mutex_init(&o->log_mu, NULL);
     if (!o->J || !o->beta || !o->s || !o->E || (with_fields && !o->h) || !o->acc_flip ||
-        !o->att_swap || !o->acc_swap || !o->near_metro || !o->first_near) {
+        !o->att_swap || !o->acc_swap || !o->near_metro || !o->first_near || !o->log || !o->adopted_metro ||
+        !o->flipped_metro) {
         oracle_destroy(o);
         return NULL;
     }
@@ -236,6 +290,14 @@ static void orc_sweep_slot(oracle_t* o, int t, uint32_t n, int mode)
         if (xarg < 40.0 && fabs(xarg + log(u)) < ORC_NEAR_TIE) {
             o->near_metro[t]++;
             if (o->first_near[t] < 0) o->first_near[t] = (int64_t)n;
+            const int own = accept;
+            const int ov = orc_override(o, 0, t, n, m);
+            if (ov >= 0) {
+                o->adopted_metro[t]++;
+                if (ov != own) o->flipped_metro[t]++;
+                accept = ov;
+            }
+            orc_log(o, 0, t, n, m, own, accept);
         }
         if (!accept) continue;
         s[k] = (uint8_t)b;
@@ -323,6 +385,14 @@ void oracle_exchange(oracle_t* o)
             if (D > -40.0 && fabs(D - log(u)) < ORC_NEAR_TIE) {
                 o->near_exch++;
                 if (o->first_near_exch < 0) o->first_near_exch = (int64_t)m;
+                const int own = accept;
+                const int ov = orc_override(o, 1, t, m, stage);
+                if (ov >= 0) {
+                    o->adopted_exch++;
+                    if (ov != own) o->flipped_exch++;
+                    accept = ov;
+                }
+                orc_log(o, 1, t, m, stage, own, accept);
             }
             o->att_swap[t]++;
             if (accept) {
@@ -367,4 +437,43 @@ void oracle_get_stats(const oracle_t* o, uint64_t* acc_flip, uint64_t* att_swap,
     memcpy(first_near, o->first_near, sizeof(int64_t) * o->R);
     *near_exch = o->near_exch;
     *first_near_exch = o->first_near_exch;
+}
+
+/* Replace the table of decisions to adopt at near ties: n entries of
+   {kind (0 Metropolis, 1 exchange), slot t (exchange: pair (t, t+1)), sweep n
+   (exchange: index m), attempt within the sweep (exchange: stage), decision
+   (0 reject, 1 accept)}.  Returns 0, or -1 if the copy cannot be allocated. */
+int oracle_set_overrides(oracle_t* o, const int32_t* ev, int n)
+{
+    int32_t* copy = NULL;
+    if (n > 0) {
+        copy = (int32_t*)malloc(sizeof(int32_t) * 5 * (size_t)n);
+        if (!copy) return -1;
+        memcpy(copy, ev, sizeof(int32_t) * 5 * (size_t)n);
+    }
+    free(o->ovr);
+    o->ovr = copy;
+    o->novr = n > 0 ? n : 0;
+    return 0;
+}
+
+/* Near-tie events so far (up to cap of them, [cap][6] as in oracle_t.log);
+   returns how many were seen in all. */
+uint64_t oracle_get_near_log(const oracle_t* o, int32_t* out, int cap)
+{
+    uint64_t keep = o->nlog < ORC_LOG_CAP ? o->nlog : ORC_LOG_CAP;
+    if (cap >= 0 && keep > (uint64_t)cap) keep = (uint64_t)cap;
+    if (keep) memcpy(out, o->log, sizeof(int32_t) * 6 * (size_t)keep);
+    return o->nlog;
+}
+
+/* adoptions of tabled decisions: per slot (Metropolis) and for the exchange,
+   all of them and those that reversed the oracle's own decision */
+void oracle_get_adopted(const oracle_t* o, uint64_t* adopted_metro, uint64_t* flipped_metro, uint64_t* adopted_exch,
+                        uint64_t* flipped_exch)
+{
+    memcpy(adopted_metro, o->adopted_metro, sizeof(uint64_t) * o->R);
+    memcpy(flipped_metro, o->flipped_metro, sizeof(uint64_t) * o->R);
+    *adopted_exch = o->adopted_exch;
+    *flipped_exch = o->flipped_exch;
 }
