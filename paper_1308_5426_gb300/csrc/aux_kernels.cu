@@ -3,6 +3,7 @@
 #include <cmath>
 
 #include "measure_body.cuh"
+#include "near_tie.cuh"
 #include "philox.cuh"
 #include "potts_internal.h"
 
@@ -134,7 +135,10 @@ __global__ void __launch_bounds__(kAuxThreads) exchange_kernel(const JobDev* __r
             const int ra = jb.map[t], rb = jb.map[t + 1];
             const double D = (jb.beta[t] - jb.beta[t + 1]) * (jb.E[ra] - jb.E[rb]);
             const bool acc = (D >= 0.0) || (u < exp(D));
-            if (D > -40.0 && fabs(D - log(u)) < 1e-9) ++near;
+            if (D > -40.0 && fabs(D - log(u)) < kNearTie) {  // a near tie: counted and logged
+                ++near;
+                near_tie_log(jb.near_log, jb.near_log_n, 1, t, m, stage, acc);
+            }
             if (acc) {
                 jb.map[t] = rb;
                 jb.map[t + 1] = ra;

@@ -279,7 +279,8 @@ __device__ __forceinline__ void sweep_item(const JobDev* __restrict__ jobs, cons
                                                    cb32, cb64, errd, Jn,
                                                    kMode == 1 ? (const double*)(const void*)J : nullptr, ck, cab,
                                                    mine, dmine, nnear, basefx,
-                                                   kFX ? (const long long*)(const void*)J : nullptr, fxs);
+                                                   kFX ? (const long long*)(const void*)J : nullptr, fxs,
+                                                   NearSink{jp->near_log, jp->near_log_n, t, n});
                 if (mine) {
                     s[k] = (uint8_t)b;
                     if constexpr (!kFP64) dE_acc += (double)((float)c * dmine);

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdint>
 
+#include "near_tie.cuh"
 #include "philox.cuh"
 #include "potts_internal.h"
 
@@ -13,13 +14,18 @@ constexpr unsigned kFullMask = 0xffffffffu;
 constexpr int kNearTable = 64;  // J* in FP32 for distances < 64 (corrections within two blocks)
 enum : int { kReject = 0, kAccept = 1, kUnsure = 2 };
 
-// FP64 rule, evaluated exactly: dE <= 0 or u < exp(-beta dE); near-tie count.
-__device__ __forceinline__ bool decide_fp64_exact(double d, double cb, double u, unsigned long long& near)
+// FP64 rule, evaluated exactly: dE <= 0 or u < exp(-beta dE).  A decision
+// with |beta dE + ln u| < 1e-9 (on either branch) is a near tie: counted, and
+// logged as attempt `attempt` of slot ns.t at sweep ns.n.
+__device__ __forceinline__ bool decide_fp64_exact(double d, double cb, double u, unsigned long long& near,
+                                                  const NearSink& ns, int attempt)
 {
-    if (d <= 0.0) return true;
     const double x = cb * d;  // beta * c * d
-    const bool acc = u < exp(-x);
-    if (fabs(x + log(u)) < 1e-9) ++near;
+    const bool acc = d <= 0.0 || u < exp(-x);
+    if (x < 40.0 && fabs(x + log(u)) < kNearTie) {
+        ++near;
+        near_tie_log(ns.log, ns.count, 0, ns.t, ns.n, attempt, acc);
+    }
     return acc;
 }
 
@@ -83,7 +89,8 @@ __device__ __forceinline__ int decide_block(int lane, int nv, int k, int L, int 
                                             int npend, float cb32, double cb64, float errd, const float* Jn,
                                             const double* J64, int* ck, int* cab, bool& mine, float& dmine,
                                             unsigned long long& nnear, long long basefx = 0,
-                                            const long long* Jfx = nullptr, double fxs = 0.0)
+                                            const long long* Jfx = nullptr, double fxs = 0.0,
+                                            const NearSink& ns = NearSink{nullptr, nullptr, 0, 0u})
 {
     constexpr bool kFP64 = kMode != 0;
     const bool valid = lane < nv;
@@ -169,7 +176,7 @@ __device__ __forceinline__ int decide_block(int lane, int nv, int k, int L, int 
                             if (coef) d64 += (double)coef * J64[k - kf];
                         }
                     }
-                    dec = decide_fp64_exact(d64, cb64, unit53(ux1, ux2), nnear);
+                    dec = decide_fp64_exact(d64, cb64, unit53(ux1, ux2), nnear, ns, k);
                 }
                 acc = __shfl_sync(kFullMask, dec, j);
                 __syncwarp();

@@ -112,7 +112,11 @@ __global__ void __launch_bounds__(kDirThreads) sweep_direct_kernel(const JobDev*
             int st = decide_fp64_filter(d32, cb32, nlu, fabsf(d32) * 1e-6f + 1e-30f);
             if (st == kUnsure) {  // lane 0 applies the rule in FP64 and broadcasts it
                 int acc = 0;
-                if (lane == 0) acc = decide_fp64_exact(d, cb, unit53(ux1, ux2), nnear) ? 1 : 0;
+                if (lane == 0)
+                    acc = decide_fp64_exact(d, cb, unit53(ux1, ux2), nnear,
+                                            NearSink{jp->near_log, jp->near_log_n, t, n0 + (uint32_t)sw}, m)
+                              ? 1
+                              : 0;
                 st = __shfl_sync(kFullMask, acc, 0) ? kAccept : kReject;
             }
             if (st == kAccept) {
