@@ -85,6 +85,7 @@ extern "C" {
 #define POTTS_LR_FX64 2
 
 #define POTTS_LR_MAX_Q 16
+#define POTTS_LR_NEAR_LOG_CAP 256 /* near-tie events kept per job (potts_lr_near_log) */
 
 typedef struct potts_lr potts_lr_t;
 
@@ -172,8 +173,10 @@ int potts_lr_fields_error(potts_lr_t* h, double* max_err);
 int potts_lr_get_state(potts_lr_t* h, void* buf, size_t* len);
 
 /* Restore a checkpoint written by potts_lr_get_state of a handle created with
- * the same L, q, R and precision; ESTATE if it does not match.  Continuing
- * from a restored state reproduces the uninterrupted run bit for bit. */
+ * the same L, q, sigma, temperatures, R, seed, precision and pair factor;
+ * ESTATE if any of them differs (the checkpoint's header records them), or
+ * the size, format version or slot map is wrong.  Continuing from a restored
+ * state reproduces the uninterrupted run bit for bit. */
 int potts_lr_set_state(potts_lr_t* h, const void* buf, size_t len);
 
 /* Spins of every slot, out[t*L + i] in 0..q-1 (host array of R*L bytes). Syncs. */
@@ -191,6 +194,37 @@ int potts_lr_get_energy(potts_lr_t* h, double* E);
  * (entry R-1 is 0); near_ties[2] = {Metropolis, exchange} decisions whose FP64
  * margin |beta dE + ln u| (resp. |D - ln u|) was below 1e-9. Syncs. */
 int potts_lr_stats(potts_lr_t* h, uint64_t* acc_flip, uint64_t* acc_swap, uint64_t* near_ties);
+
+/* Log of the near ties counted by potts_lr_stats, so that a checker whose
+ * exp and log round differently can see where they fell and adopt the
+ * decisions taken here (the re-synchronisation reading of Eq. 8 and Eq. 9).
+ * events: host array of cap rows of 5 int32 {kind (0 = Metropolis, 1 =
+ * exchange), slot t (exchange: pair (t, t+1)), sweep index n (exchange:
+ * exchange index m), attempt within the sweep (the site k in sequential
+ * order; exchange: stage 0 or 1), decision (1 = accepted)}.  The rows are
+ * the first POTTS_LR_NEAR_LOG_CAP near ties since create in the order the
+ * device recorded them (the order between slots of one launch is not
+ * fixed); min(cap, *n, POTTS_LR_NEAR_LOG_CAP) rows are written.  *n = near
+ * ties logged since create (more than the capacity are counted, not kept).
+ * The log is not part of a checkpoint.  Only the FP64 rule logs (FP64 and
+ * FX64 modes, the exchange of any mode).  EINVAL for a NULL handle or n, cap
+ * < 0, or events NULL with cap > 0.  Synchronises. */
+int potts_lr_near_log(potts_lr_t* h, int32_t* events, int cap, int* n);
+
+/* Bounds of the handle's device waits (the paper has no counterpart), in ns:
+ *   rebuild_ns -- each pipeline wait of the FP32 tensor-core rebuild (default
+ *     4e9).  When one expires, the rebuild stops, lets its own copies and
+ *     tensor-core operations finish, frees its tensor memory and returns; the
+ *     fields are then invalid, and the next synchronising call on the handle
+ *     (or on a batch holding it) returns ETIMEOUT.  The next
+ *     potts_lr_fields_recompute under a sufficient bound makes them valid.
+ *   plan_ns -- how long sweep CTAs wait for the other CTAs' first claims
+ *     under the SM placement plan (default 50000).  Expiry only changes which
+ *     SM sweeps which slot, never a result.
+ * Small values exist to test the expiry paths.  They apply to the handle's
+ * own calls and to batches created afterwards (a batch group takes the
+ * smallest plan_ns of its jobs).  Synchronises.  EINVAL for a NULL handle. */
+int potts_lr_set_wait_limits(potts_lr_t* h, uint64_t rebuild_ns, uint64_t plan_ns);
 
 /* Sweep and exchange counts since create. */
 int potts_lr_counters(potts_lr_t* h, uint32_t* nsweep, uint32_t* nexch);
@@ -248,7 +282,7 @@ void potts_lr_batch_destroy(potts_lr_batch_t* b);
  * job order, len = potts_lr_batch_state_size bytes.  All copies are issued on
  * the batch stream with one synchronisation at the end (pinned host memory
  * makes them run at link speed).  potts_lr_batch_set_state checks every job's
- * part (size, L, q, R, precision, slot map) before it changes any device
+ * part (everything potts_lr_set_state checks) before it changes any device
  * memory; a mismatch returns ESTATE and leaves every job as it was.  Errors:
  * EINVAL (NULL), ESTATE (len or a part does not match), ECUDA. */
 int potts_lr_batch_state_size(potts_lr_batch_t* b, size_t* len);
@@ -275,18 +309,33 @@ int potts_lr_batch_set_state(potts_lr_batch_t* b, const void* buf, size_t len);
  * pair_factor not 1 or 2, or R outside [1, 4096] (the scratch size); ECUDA for
  * a runtime error.  The first call on a device looks up the device address of
  * the scratch array (cudaGetSymbolAddress), so make that first call before any
- * stream capture.  Every call writes every scratch entry it later reads, so
+ * stream capture; the first call after a cudaDeviceReset looks it up again
+ * (the address is cached with the device's context).  Every call writes every scratch entry it later reads, so
  * nothing needs clearing between calls; but all calls share the one array, so
  * calls that overlap on the GPU (different streams, or threads) race. */
 int potts_lr_measure_static(const uint32_t* spins, int L, int q, int R, const double* jstar, int pair_factor,
                             double* E, double* M, void* cuda_stream);
 
 /* Measurement utility (the paper has no counterpart): throughput of this
- * GPU's FP64 add pipe (what = 0, adds/s), FP32 add pipe (what = 1, adds/s) or
- * shared memory (what = 2, bytes/s loaded + stored), measured with CUDA
+ * GPU's FP64 add pipe (what = 0, adds/s), FP32 add pipe (what = 1, adds/s),
+ * shared memory (what = 2, bytes/s loaded + stored) or L2 (what = 3, bytes/s
+ * loaded + stored on a 32 MB buffer resident in L2), measured with CUDA
  * events on the current device; the roofline denominators of the sweep
- * kernel.  Synchronous; allocates 16 bytes of device memory for the call. */
+ * kernels.  Synchronous; allocates 16 bytes of device memory for the call
+ * (32 MB for what = 3).  On any failure (ECUDA, ENOMEM) *value is left
+ * untouched. */
 int potts_lr_probe(int what, double* value);
+
+/* Which sweep kernel the handle runs (the paper has no counterpart; it lets a
+ * benchmark label and bound what it timed).  info: host array of n int32
+ * (n >= 1; entries past 7 are not written): [0] kernel (0 = fields in shared
+ * or global memory, 1 = fields in registers, 2 = fields shared by a CTA
+ * cluster, 3 = the direct sweep without fields); [1] fields in shared memory
+ * (0/1); [2] coupling table in shared memory (0/1); [3] register
+ * configuration (1..8, else 0); [4] cluster size (2, 4 or 8, else 0); [5]
+ * threads per CTA; [6] dynamic shared memory per CTA in bytes.  EINVAL for a
+ * NULL handle or info, or n < 1. */
+int potts_lr_sweep_info(potts_lr_t* h, int32_t* info, int n);
 
 #ifdef __cplusplus
 }

@@ -33,11 +33,11 @@ def jtot(L: int, sigma: float) -> float:
 
 
 def probe(what: str) -> float:
-    """Measured throughput of this GPU: "fp64_add", "fp32_add" (adds/s) or
-    "smem" (shared-memory bytes/s) -- roofline denominators."""
+    """Measured throughput of this GPU: "fp64_add", "fp32_add" (adds/s),
+    "smem" or "l2" (bytes/s loaded + stored) -- roofline denominators."""
     lib = _lib.load()
     v = ctypes.c_double()
-    _lib.check(lib.potts_lr_probe({"fp64_add": 0, "fp32_add": 1, "smem": 2}[what], ctypes.byref(v)))
+    _lib.check(lib.potts_lr_probe({"fp64_add": 0, "fp32_add": 1, "smem": 2, "l2": 3}[what], ctypes.byref(v)))
     return v.value
 
 
@@ -178,6 +178,30 @@ class Job:
         _lib.check(self._lib.potts_lr_stats(self._h, _lib._ptr(acc), _lib._ptr(sw), _lib._ptr(near)))
         return {"acc_flip": acc, "acc_swap": sw[: max(self.R - 1, 0)], "near_metro": int(near[0]),
                 "near_exch": int(near[1])}
+
+    def sweep_info(self):
+        """The sweep kernel this job runs (potts_lr_sweep_info)."""
+        v = np.zeros(7, np.int32)
+        _lib.check(self._lib.potts_lr_sweep_info(self._h, _lib._ptr(v), 7))
+        kind = ("memory", "registers", "cluster", "direct")[int(v[0])]
+        return {"kernel": kind, "fields_in_smem": bool(v[1]), "table_in_smem": bool(v[2]),
+                "register_config": int(v[3]), "cluster": int(v[4]), "threads": int(v[5]),
+                "smem_bytes": int(v[6])}
+
+    def set_wait_limits(self, rebuild_ns=4_000_000_000, plan_ns=50_000):
+        """Bounds of the device waits (potts_lr_set_wait_limits); small values
+        make them expire (the tests of the failure paths)."""
+        _lib.check(self._lib.potts_lr_set_wait_limits(self._h, ctypes.c_uint64(int(rebuild_ns)),
+                                                      ctypes.c_uint64(int(plan_ns))))
+
+    def near_log(self):
+        """Near ties so far (potts_lr_near_log): rows {kind (0 Metropolis, 1
+        exchange), slot or pair, sweep or exchange index, attempt or stage,
+        decision}, and the number logged since create."""
+        out = np.zeros((_lib.NEAR_LOG_CAP, 5), np.int32)
+        n = ctypes.c_int()
+        _lib.check(self._lib.potts_lr_near_log(self._h, _lib._ptr(out), _lib.NEAR_LOG_CAP, ctypes.byref(n)))
+        return out[: min(n.value, _lib.NEAR_LOG_CAP)].copy(), n.value
 
     def counters(self):
         a, b = ctypes.c_uint32(), ctypes.c_uint32()

@@ -13,6 +13,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libpotts_lr.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE = 0, 1, 2, 3, 4, 5
+NEAR_LOG_CAP = 256  # POTTS_LR_NEAR_LOG_CAP
 FP64, FP32, FX64 = 0, 1, 2
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "fx64": FX64}
 
@@ -26,7 +27,8 @@ EXPORTS = [
     "potts_lr_batch_create", "potts_lr_batch_run", "potts_lr_batch_sync", "potts_lr_batch_destroy",
     "potts_lr_batch_sweep", "potts_lr_batch_exchange", "potts_lr_batch_measure",
     "potts_lr_batch_measure_device", "potts_lr_batch_state_size", "potts_lr_batch_get_state",
-    "potts_lr_batch_set_state", "potts_lr_probe", "potts_lr_measure_static",
+    "potts_lr_batch_set_state", "potts_lr_probe", "potts_lr_measure_static", "potts_lr_near_log",
+    "potts_lr_set_wait_limits", "potts_lr_sweep_info",
 ]
 
 
@@ -84,6 +86,9 @@ def load(path: str = LIB_PATH):
         "potts_lr_batch_set_state": [P, P, SZ],
         "potts_lr_probe": [I, P],
         "potts_lr_measure_static": [P, I, I, I, P, I, P, P, P],
+        "potts_lr_near_log": [P, P, I, P],
+        "potts_lr_set_wait_limits": [P, U64, U64],
+        "potts_lr_sweep_info": [P, P, I],
     }
     for name, args in sig.items():
         f = getattr(lib, name)

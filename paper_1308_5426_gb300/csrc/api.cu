@@ -43,16 +43,35 @@ int cuda_fail(cudaError_t e, const char* where)
 constexpr size_t kSmemBudget = 220 * 1024;  // dynamic shared memory a sweep CTA may take
 constexpr size_t kClusterFieldBytes = 88 * 1024;  // FP32 fields above this go to a cluster (see create)
 constexpr uint32_t kStateMagic = 0x31524c50u; // "PLR1"
-constexpr uint32_t kStateVersion = 3;          // header + the job's checkpoint block
+constexpr uint32_t kStateVersion = 4;          // header + the job's checkpoint block
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Checkpoint header: what a restored state must share with the handle for
+// the run to continue as the uninterrupted run would (72 bytes).
 struct StateHeader {
     uint32_t magic, version;
     int32_t L, q, R, precision, c, Lpad;
     uint64_t seed;
     uint32_t nsweep, nexch;
+    uint64_t sigma_bits;  // bit pattern of sigma (the couplings, Eq. 4-6)
+    uint64_t temps_hash;  // FNV-1a of the bit patterns of the R inverse temperatures
+    int32_t fx_bits;      // FX64 mode: F of the field grid 2^-F (0 otherwise)
+    int32_t reserved;
 };
+static_assert(sizeof(StateHeader) == 72, "checkpoint header layout");
+
+// FNV-1a (64-bit) over the bytes of n doubles
+uint64_t fnv1a(const double* v, size_t n)
+{
+    uint64_t hsh = 0xcbf29ce484222325ull;
+    const unsigned char* p = (const unsigned char*)v;
+    for (size_t i = 0; i < n * sizeof(double); ++i) {
+        hsh ^= p[i];
+        hsh *= 0x100000001b3ull;
+    }
+    return hsh;
+}
 
 }  // namespace
 
@@ -60,6 +79,8 @@ struct potts_lr {
     int L, q, R, W, Lpad, precision, K, c;
     double sigma, jtot;
     uint64_t seed;
+    int fx_bits;                  // FX64 mode: F of the field grid (0 otherwise)
+    uint64_t temps_hash;          // fnv1a of the inverse temperatures (checkpoint check)
     cudaStream_t stream;
     bool own_stream;
     void* arena;
@@ -348,6 +369,8 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
     if (h->precision == POTTS_LR_FP32) tc_hank_table(J, split.data(), h->Lpad, hank);
     std::vector<double> beta(R);
     for (int t = 0; t < R; ++t) beta[t] = 1.0 / temps[t];
+    h->fx_bits = fx_bits;
+    h->temps_hash = fnv1a(beta.data(), (size_t)R);
     // first FP32 rebuild interval: short for long chains with few states (the
     // drift grows with the field updates per element, ~L/q per sweep); the
     // device doubles it while the measured drift stays small
@@ -399,6 +422,7 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
     const bool tc = h->precision == POTTS_LR_FP32;  // tensor-core rebuild operands
     const size_t o_hank = take(tc ? tc_hank_bytes(L) : 0), o_xoh = take(tc ? tc_onehot_bytes(L, q, R) : 0);
     const size_t o_status = take(4);
+    const size_t o_nlog = take((size_t)kNearLogCap * sizeof(int4)), o_nlogn = take(4);
     std::vector<int4> tiles;
     h->tc_tn = tc_tile_width(tc_tile_count(L, q, R, 64), tc_tile_count(L, q, R, 128), device_sm_count());
     if (h->precision == POTTS_LR_FP32) tc_tiles(0, L, q, R, h->tc_tn, tiles);
@@ -444,6 +468,8 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
     j.acc_flip = (unsigned long long*)(base + o_accf);
     j.acc_swap = (unsigned long long*)(base + o_accs);
     j.near = (unsigned long long*)(base + o_near);
+    j.near_log = (int4*)(base + o_nlog);
+    j.near_log_n = (unsigned*)(base + o_nlogn);
     j.meas_E = (double*)(base + o_mE);
     j.meas_M = (double*)(base + o_mM);
     j.meas_part = (double*)(base + o_mpart);
@@ -456,6 +482,7 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
     j.NG = tc_ng(q, R);
     h->onehot_blocks = tc_onehot_blocks(L, q, R);
     j.status = (int*)(base + o_status);
+    j.tc_wait_ns = kTcWaitNs;
     j.sched = (int*)(base + o_sched);
     h->dtiles = (int4*)(base + o_tiles);
     h->ntiles = (int)tiles.size();
@@ -680,6 +707,9 @@ static int state_out_enqueue(potts_lr_t* h, char* p, cudaStream_t st)
     hd.seed = h->seed;
     hd.nsweep = h->nsweep;
     hd.nexch = h->nexch;
+    std::memcpy(&hd.sigma_bits, &h->sigma, 8);
+    hd.temps_hash = h->temps_hash;
+    hd.fx_bits = h->fx_bits;
     std::memcpy(p, &hd, sizeof(hd));
     PLR_CUDA(cudaMemcpyAsync(p + sizeof(hd), (const char*)h->arena + h->state_off, h->state_len,
                              cudaMemcpyDeviceToHost, st));
@@ -692,9 +722,19 @@ static int state_in_check(const potts_lr_t* h, const char* p, size_t len)
     if (len != state_bytes(h)) return fail(POTTS_LR_ESTATE, "checkpoint size %zu does not match %zu", len, state_bytes(h));
     StateHeader hd;
     std::memcpy(&hd, p, sizeof(hd));
-    if (hd.magic != kStateMagic || hd.version != kStateVersion || hd.L != h->L || hd.q != h->q || hd.R != h->R ||
-        hd.precision != h->precision || hd.Lpad != h->Lpad)
+    if (hd.magic != kStateMagic || hd.version != kStateVersion)
+        return fail(POTTS_LR_ESTATE, "not a checkpoint of this format (version %u, expected %u)", hd.version,
+                    kStateVersion);
+    if (hd.L != h->L || hd.q != h->q || hd.R != h->R || hd.precision != h->precision || hd.Lpad != h->Lpad)
         return fail(POTTS_LR_ESTATE, "checkpoint does not match this job's L, q, R or precision");
+    uint64_t sb;
+    std::memcpy(&sb, &h->sigma, 8);
+    if (hd.sigma_bits != sb || hd.fx_bits != h->fx_bits)
+        return fail(POTTS_LR_ESTATE, "checkpoint was made with other couplings (sigma or the FX64 grid differ)");
+    if (hd.seed != h->seed) return fail(POTTS_LR_ESTATE, "checkpoint was made with another seed");
+    if (hd.c != h->c) return fail(POTTS_LR_ESTATE, "checkpoint was made with another pair factor c");
+    if (hd.temps_hash != h->temps_hash)
+        return fail(POTTS_LR_ESTATE, "checkpoint was made with another temperature grid");
     const size_t R = h->R;
     std::vector<int> map(R);
     std::memcpy(map.data(), p + sizeof(hd), R * 4);
@@ -799,6 +839,53 @@ int potts_lr_stats(potts_lr_t* h, uint64_t* acc_flip, uint64_t* acc_swap, uint64
     if (acc_swap) PLR_CUDA(cudaMemcpyAsync(acc_swap, h->hj.acc_swap, b, cudaMemcpyDeviceToHost, h->stream));
     if (near_ties) PLR_CUDA(cudaMemcpyAsync(near_ties, h->hj.near, 16, cudaMemcpyDeviceToHost, h->stream));
     PLR_CUDA(cudaStreamSynchronize(h->stream));
+    return POTTS_LR_OK;
+}
+
+int potts_lr_sweep_info(potts_lr_t* h, int32_t* info, int n)
+{
+    if (!h || !info || n < 1) return fail(POTTS_LR_EINVAL, "bad argument");
+    const JobDev& j = h->hj;
+    const int kind = h->direct ? 3 : j.cl ? 2 : j.rf ? 1 : 0;
+    // threads per CTA of each kernel: register configurations 1-3 run 7 update
+    // warps, 4-8 run 15, plus the decision warp; the direct sweep one warp
+    const int threads = kind == 3 ? 32 : kind == 2 ? 512 : kind == 1 ? (j.rf <= 3 ? 256 : 512)
+                                                                      : (j.h_smem ? 256 : 512);
+    const int32_t v[7] = {kind, kind == 0 ? j.h_smem : 0, kind == 0 ? j.j_smem : 0, j.rf, j.cl, threads,
+                          (int32_t)h->sweep_smem};
+    for (int i = 0; i < n && i < 7; ++i) info[i] = v[i];
+    return POTTS_LR_OK;
+}
+
+int potts_lr_set_wait_limits(potts_lr_t* h, uint64_t rebuild_ns, uint64_t plan_ns)
+{
+    if (!h) return fail(POTTS_LR_EINVAL, "handle is NULL");
+    h->hj.tc_wait_ns = rebuild_ns;
+    h->sched.wait_ns = plan_ns;
+    PLR_CUDA(cudaMemcpyAsync(h->dj, &h->hj, sizeof(JobDev), cudaMemcpyHostToDevice, h->stream));
+    PLR_CUDA(cudaStreamSynchronize(h->stream));
+    return POTTS_LR_OK;
+}
+
+int potts_lr_near_log(potts_lr_t* h, int32_t* events, int cap, int* n)
+{
+    if (!h || !n || cap < 0 || (cap > 0 && !events)) return fail(POTTS_LR_EINVAL, "bad argument");
+    std::vector<int4> log(kNearLogCap);
+    unsigned cnt = 0;
+    PLR_CUDA(cudaMemcpyAsync(log.data(), h->hj.near_log, log.size() * sizeof(int4), cudaMemcpyDeviceToHost,
+                             h->stream));
+    PLR_CUDA(cudaMemcpyAsync(&cnt, h->hj.near_log_n, 4, cudaMemcpyDeviceToHost, h->stream));
+    PLR_CUDA(cudaStreamSynchronize(h->stream));
+    const int keep = std::min<int>(std::min<unsigned>(cnt, (unsigned)kNearLogCap), cap);
+    for (int i = 0; i < keep; ++i) {
+        int32_t* e = events + 5 * (size_t)i;
+        e[0] = log[i].x & 1;         // kind
+        e[1] = log[i].y;             // slot or pair
+        e[2] = log[i].z;             // sweep or exchange index
+        e[3] = log[i].w;             // attempt or stage
+        e[4] = (log[i].x >> 1) & 1;  // decision
+    }
+    *n = (int)std::min<unsigned>(cnt, 0x7fffffffu);
     return POTTS_LR_OK;
 }
 
@@ -942,6 +1029,7 @@ int potts_lr_batch_create(potts_lr_t* const* jobs, int n, void* cuda_stream, pot
         g.nwork = (int)kv.second.size();
         g.smem = smem[kv.first];
         sweep_sched_carve((char*)b->arena + osch[kv.first], g.nwork, nsm, &g.sched);
+        for (const int2& w : kv.second) g.sched.wait_ns = std::min(g.sched.wait_ns, jobs[w.x]->sched.wait_ns);
         g.stream = nullptr;
         g.done = nullptr;
         b->groups.push_back(g);

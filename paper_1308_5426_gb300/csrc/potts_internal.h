@@ -15,6 +15,10 @@ constexpr int kMaxQ = 16;           // largest q (4-bit packed spins)
 constexpr int kMaxL = 65536;        // largest L (16-bit positions in the direct rebuild)
 constexpr int kChunk = 128;         // K sites per chunk of the tensor-core rebuild
 constexpr int kMeasMaxParts = 32;   // largest split of one slot's measurement over CTAs
+constexpr int kNearLogCap = 256;    // near-tie events logged per job (all are counted)
+// default bounds of the device waits (potts_lr_set_wait_limits)
+constexpr unsigned long long kTcWaitNs = 4000000000ull;  // each pipeline wait of the tensor-core rebuild: 4 s
+constexpr unsigned long long kSchedWaitNs = 50000;       // sweep CTAs waiting for the others' first claims
 // precision modes (JobDev::precision, the C ABI's POTTS_LR_FP64 / FP32 / FX64)
 constexpr int kPrecFP64 = 0;        // FP64 fields
 constexpr int kPrecFP32 = 1;        // FP32 fields, tensor-core rebuilds
@@ -46,6 +50,9 @@ struct JobDev {
     unsigned long long* acc_flip;  // per slot
     unsigned long long* acc_swap;  // per pair (t, t+1), R entries
     unsigned long long* near;      // [2]: Metropolis, exchange near ties
+    int4* near_log;                // [kNearLogCap]: {kind | decision << 1, slot or pair, sweep or exchange
+                                   // index, attempt or stage} of the first near ties (near_tie.cuh)
+    unsigned* near_log_n;          // near ties logged since create (the log keeps the first kNearLogCap)
     double* meas_E;       // per slot, written by the measure kernel
     double* meas_M;
     double* meas_part;    // [slot][kMeasMaxParts]: the measure kernel's partial energy sums
@@ -59,6 +66,7 @@ struct JobDev {
     int hank_cores;                // core matrices per part of Jhank: Lc / 4 - 1
     int NG;                        // 8-row groups of the B operand: q R rounded up to 128, / 8
     int* status;                   // 0 ok; 1 a bounded device wait expired
+    unsigned long long tc_wait_ns; // bound of each pipeline wait of the tensor-core rebuild (kTcWaitNs)
     int* sched;                    // FP32 rebuild schedule: [0] current interval k, [1] sweep of the next rebuild
     unsigned long long* drift_bits;  // max |h_before - h_rebuilt| / Jtot of the last rebuild (double bits)
 };
@@ -91,6 +99,7 @@ struct SweepSched {
     int* claim;   // [n] 0 until an item is taken
     int* ctr;     // [nsm + 2]: arrivals per SM, next list position, CTAs past their claim
     int n, nsm, occ;
+    unsigned long long wait_ns;  // longest wait for the other CTAs' first claims (kSchedWaitNs)
 };
 size_t sweep_sched_bytes(int n, int nsm);
 // carve a SweepSched for n items out of device memory at base (sweep_sched_bytes long)

@@ -108,8 +108,15 @@ def test_entry_point_argument_checks_without_gpu(lib):
                                          None)
         assert rc == _lib.EINVAL, bad
     v = ctypes.c_double()
-    assert lib.potts_lr_probe(3, ctypes.byref(v)) == _lib.EINVAL
+    assert lib.potts_lr_probe(4, ctypes.byref(v)) == _lib.EINVAL
     assert lib.potts_lr_probe(0, None) == _lib.EINVAL
+    # the near-tie log, the wait limits and the sweep description of a NULL handle
+    k = ctypes.c_int()
+    ev = np.zeros((4, 5), np.int32)
+    assert lib.potts_lr_near_log(None, _lib._ptr(ev), 4, ctypes.byref(k)) == _lib.EINVAL
+    assert lib.potts_lr_set_wait_limits(None, 0, 0) == _lib.EINVAL
+    info = np.zeros(7, np.int32)
+    assert lib.potts_lr_sweep_info(None, _lib._ptr(info), 7) == _lib.EINVAL
 
 
 @pytest.mark.parametrize("L", [2, 3, 64, 1000, 1024, 4096, 16384, 65536])
