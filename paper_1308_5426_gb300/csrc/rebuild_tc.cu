@@ -39,9 +39,11 @@
 // B: core matrix (row group g, K group kc) at byte (16 g + kc) 128; leading
 // byte offset 128, stride byte offset 2048; K-step s starts at byte 256 s.
 //
-// Every wait is bounded (a timer): a wait that expires raises a shared abort
-// flag that ends the other roles' loops, the job's status word is set, and the
-// CTA still drains its copies and MMAs before it frees the tensor memory.
+// Every wait is bounded (a timer): a pipeline wait that expires (after the
+// job's tc_wait_ns, 4 s unless set otherwise) raises a shared abort flag that
+// ends the other roles' loops, the job's status word is set, and the CTA
+// still drains its own copies and MMAs (waits bounded by 4 s, which such
+// waits never approach) before it frees the tensor memory.
 #include <cstdint>
 #include <vector>
 
@@ -59,7 +61,7 @@ constexpr int kHank = kTileM / 8 + kChunk / 8 - 1;  // distinct core matrices of
 constexpr int kTileBytes = kHank * 128;            // 3968 B per A tile of one part
 constexpr int kTmemCols = 512;       // all of the SM's tensor memory: accumulators of TN columns each
 constexpr int kOnehotThreads = 256;
-constexpr unsigned long long kWaitNs = 4000000000ull;  // bounded waits: 4 s
+constexpr unsigned long long kDrainWaitNs = kTcWaitNs;  // the waits for the CTA's own copies and MMAs at exit
 constexpr size_t kTcMinSmem = 120 * 1024;   // forces one CTA per SM (owner of all 512 columns)
 
 // per tile width TN (64 or 128 output columns): accumulators, B tile, stage
@@ -103,9 +105,10 @@ __device__ __forceinline__ unsigned long long global_ns()
 }
 
 // Wait for the phase of the given parity to complete; false if the abort
-// flag is raised meanwhile (abort may be null: no early exit) or the time
-// limit passes (which raises the flag).  sleep_ns: back-off between polls.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort, uint32_t sleep_ns = 0)
+// flag is raised meanwhile (abort may be null: no early exit) or limit_ns
+// passes (which raises the flag).  sleep_ns: back-off between polls.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort, uint32_t sleep_ns = 0,
+                                          unsigned long long limit_ns = kDrainWaitNs)
 {
     unsigned long long t0 = 0;
     for (uint32_t it = 0;; ++it) {
@@ -119,15 +122,15 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
             : "memory");
         if (done) return true;
         if (abort && *abort) return false;
-        if (sleep_ns) __nanosleep(sleep_ns);
-        if ((it & 255u) == 0) {
-            const unsigned long long t = global_ns();
-            if (it == 0) t0 = t;
-            else if (t - t0 > kWaitNs) {
-                if (abort) *abort = 1;
-                return false;
-            }
+        // the clock is read at every poll: a try_wait may itself suspend the
+        // thread for a while, so polls are few and a read is cheap beside one
+        const unsigned long long t = global_ns();
+        if (it == 0) t0 = t;
+        else if (t - t0 > limit_ns) {
+            if (abort) *abort = 1;
+            return false;
         }
+        if (sleep_ns) __nanosleep(sleep_ns);
     }
 }
 
@@ -270,7 +273,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* 
                 const size_t xchunk = (size_t)jb.NG * 2048;
                 for (int t = 0; t < nchunks; ++t) {
                     const uint32_t b = issued % kStages;
-                    if (issued >= kStages && !mbar_wait(smem_u32(empty + b), ((issued / kStages) - 1) & 1u, abort)) {
+                    if (issued >= kStages &&
+                        !mbar_wait(smem_u32(empty + b), ((issued / kStages) - 1) & 1u, abort, 0, jb.tc_wait_ns)) {
                         failed_job = tile.x;
                         break;
                     }
@@ -299,14 +303,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* 
                 if (!tile_live(jb, cond)) continue;
                 const int nchunks = (jb.L + kChunk - 1) / kChunk;
                 // the accumulators of the previous tile have been read
-                if (ntile > 0 && !mbar_wait(smem_u32(tempty), (ntile - 1) & 1u, abort)) {
+                if (ntile > 0 && !mbar_wait(smem_u32(tempty), (ntile - 1) & 1u, abort, 0, jb.tc_wait_ns)) {
                     failed_job = tile.x;
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 for (int t = 0; t < nchunks; ++t) {
                     const uint32_t b = used % kStages;
-                    if (!mbar_wait(smem_u32(full + b), (used / kStages) & 1u, abort)) {
+                    if (!mbar_wait(smem_u32(full + b), (used / kStages) & 1u, abort, 0, jb.tc_wait_ns)) {
                         failed_job = tile.x;
                         break;
                     }
@@ -381,7 +385,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* 
             // polls compete with the copies and MMAs for shared memory); then
             // every lane observes the completed phase itself
             bool got = true;
-            if (lane == 0) got = mbar_wait(smem_u32(tfull), ntile & 1u, abort, 256);
+            if (lane == 0) got = mbar_wait(smem_u32(tfull), ntile & 1u, abort, 256, jb.tc_wait_ns);
             if (!__shfl_sync(0xffffffffu, got, 0)) {
                 failed_job = tile.x;
                 break;

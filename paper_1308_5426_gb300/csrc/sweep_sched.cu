@@ -83,6 +83,7 @@ void sweep_sched_carve(char* base, int n, int nsm, SweepSched* s)
     s->n = n;
     s->nsm = nsm;
     s->occ = 0;  // set per launch from the kernel's occupancy
+    s->wait_ns = kSchedWaitNs;
 }
 
 int device_sm_count()

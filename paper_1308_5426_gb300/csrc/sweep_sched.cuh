@@ -7,8 +7,6 @@
 
 namespace plr {
 
-constexpr unsigned long long kSchedWaitNs = 50000;  // longest wait for the other CTAs' first claims
-
 __device__ __forceinline__ unsigned sched_smid()
 {
     unsigned r;
@@ -43,7 +41,7 @@ __device__ __forceinline__ int sched_claim_home(const SweepSched& s)
 
 // Later claims (one thread per CTA): the next unclaimed item of the ordered
 // list, or -1 when none is left.  Before its first such claim a CTA waits,
-// for at most kSchedWaitNs, until every CTA of the grid has made its first
+// for at most s.wait_ns, until every CTA of the grid has made its first
 // claim, so that no item is taken from the SM it was dealt to; the wait only
 // shapes placement (every item is claimed once whatever happens), so its
 // expiry is not an error.
@@ -53,7 +51,7 @@ __device__ __forceinline__ int sched_claim_next(const SweepSched& s, bool& waite
         waited = true;
         const unsigned long long t0 = sched_clock_ns();
         const volatile int* arrived = s.ctr + s.nsm + 1;
-        while (*arrived < (int)gridDim.x && sched_clock_ns() - t0 < kSchedWaitNs) __nanosleep(256);
+        while (*arrived < (int)gridDim.x && sched_clock_ns() - t0 < s.wait_ns) __nanosleep(256);
     }
     for (;;) {
         const int p = atomicAdd(&s.ctr[s.nsm], 1);

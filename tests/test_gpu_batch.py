@@ -122,20 +122,21 @@ def test_batch_checkpoint_resume(plr):
         for u, v in zip(x, y):
             np.testing.assert_array_equal(u, v)
 
-    # a corrupt slot map in the last job's part (the map follows the 48-byte
+    # a corrupt slot map in the last job's part (the map follows the 72-byte
     # header: magic, version, L, q, R, precision, c, Lpad, seed, nsweep,
-    # nexch): refused, nothing changes
+    # nexch, sigma bits, temperature hash, FX64 grid, reserved): refused,
+    # nothing changes
     bad = bytearray(state)
     off = len(state) - len(jobs[-1].get_state())  # the last part starts here
     before = snapshot()
     import struct
     from paper_1308_5426_gb300 import _lib
-    bad[off + 48:off + 56] = struct.pack("<ii", 0, 0)  # slots 0 and 1 -> replica 0 twice
+    bad[off + 72:off + 80] = struct.pack("<ii", 0, 0)  # slots 0 and 1 -> replica 0 twice
     with pytest.raises(plr.PottsError) as e:
         b.set_state(bytes(bad))
     assert e.value.code == _lib.ESTATE
     bad = bytearray(state)
-    bad[off + 4:off + 8] = struct.pack("<I", 2)  # an older format version
+    bad[off + 4:off + 8] = struct.pack("<I", 3)  # an older format version
     with pytest.raises(plr.PottsError):
         b.set_state(bytes(bad))
     after = snapshot()
