@@ -16,8 +16,12 @@
 // exits.  In host code its name is only a host-side stand-in, not a device
 // address, so the entry point asks the runtime for the device address once
 // per device (cudaGetSymbolAddress, with that device current) and hands that
-// pointer to the kernel.
+// pointer to the kernel.  The address is cached together with the device's
+// current context: after a cudaDeviceReset the runtime loads the module into
+// a new context, and the first call there looks the address up again.
 #include <mutex>
+
+#include <cuda.h>
 
 #include "../../include/potts_lr.h"
 #include "measure_body.cuh"
@@ -34,6 +38,26 @@ static __device__ __align__(256) double g_measure_scratch[2 * kStaticMeasureMaxR
 
 std::mutex g_scratch_mu;
 double* g_scratch_ptr[kMaxDevices] = {};
+CUcontext g_scratch_ctx[kMaxDevices] = {};
+
+// the calling thread's current context (driver entry point found through the
+// runtime, so the library needs no link-time dependency on the driver)
+CUcontext current_context()
+{
+    using Fn = CUresult (*)(CUcontext*);
+    static Fn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (Fn)p;
+    });
+    CUcontext c = nullptr;
+    if (fn) fn(&c);
+    return c;
+}
 
 __global__ void __launch_bounds__(kAuxThreads) measure_static_kernel(const uint32_t* __restrict__ spins, int L,
                                                                      int q, int W, int c,
@@ -64,14 +88,17 @@ extern "C" int potts_lr_measure_static(const uint32_t* spins, int L, int q, int 
         return POTTS_LR_EINVAL;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return POTTS_LR_ECUDA;
+    const CUcontext ctx = current_context();  // null before the runtime first used the device
     double* scratch = nullptr;
     {
-        // once per device, with that device current: the device address of the array
+        // once per device (and context), with that device current: the
+        // device address of the array
         std::lock_guard<std::mutex> lock(g_scratch_mu);
-        if (!g_scratch_ptr[dev]) {
+        if (!g_scratch_ptr[dev] || g_scratch_ctx[dev] != ctx) {
             void* p = nullptr;
             if (cudaGetSymbolAddress(&p, g_measure_scratch) != cudaSuccess || !p) return POTTS_LR_ECUDA;
             g_scratch_ptr[dev] = (double*)p;
+            g_scratch_ctx[dev] = current_context();  // the context the lookup ran in
         }
         scratch = g_scratch_ptr[dev];
     }

@@ -1,5 +1,5 @@
-// Throughput probes for roofline denominators: FP64 add, FP32 add and
-// shared-memory bandwidth of this GPU, measured with CUDA events on a private
+// Throughput probes for roofline denominators: FP64 add, FP32 add, shared-
+// memory and L2 bandwidth of this GPU, measured with CUDA events on a private
 // stream.  Each probe kernel runs long independent dependency chains at full
 // occupancy so that the pipe (not latency) is the limit.
 #include <cstring>
@@ -55,6 +55,23 @@ __global__ void __launch_bounds__(kProbeThreads) smem_probe(float* out, int iter
     if (acc == 123456.0f) out[0] = acc;
 }
 
+// L2 bandwidth: each CTA reads and rewrites its own slice of a buffer that
+// stays resident in L2 (far below its 129 MB), 16 bytes per thread access
+__global__ void __launch_bounds__(kProbeThreads) l2_probe(float4* buf, size_t per_cta, int iters)
+{
+    float4* p = buf + (size_t)blockIdx.x * per_cta;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int it = 0; it < iters; ++it) {
+        for (size_t i = threadIdx.x; i < per_cta; i += kProbeThreads) {
+            float4 v = __ldcg(p + i);
+            acc.x += v.x;
+            v.x += 1.0f;
+            __stcg(p + i, v);
+        }
+    }
+    if (acc.x == 123456.0f) buf[0] = acc;
+}
+
 }  // namespace
 }  // namespace plr
 
@@ -62,7 +79,7 @@ using namespace plr;
 
 extern "C" int potts_lr_probe(int what, double* value)
 {
-    if (!value || what < 0 || what > 2) return POTTS_LR_EINVAL;
+    if (!value || what < 0 || what > 3) return POTTS_LR_EINVAL;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return POTTS_LR_ECUDA;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return POTTS_LR_ECUDA;
@@ -71,28 +88,42 @@ extern "C" int potts_lr_probe(int what, double* value)
     void* out = nullptr;
     cudaEvent_t e0, e1;
     int rc = POTTS_LR_OK;
-    if (cudaMalloc(&out, 16) != cudaSuccess) {
+    const int blocks = sms * 8;  // 2048 threads per SM
+    const size_t l2_per_cta = ((size_t)32 << 20) / 16 / (size_t)blocks;  // float4s per CTA of a 32 MB buffer
+    if (cudaMalloc(&out, what == 3 ? l2_per_cta * blocks * 16 : 16) != cudaSuccess) {
         cudaStreamDestroy(st);
         return POTTS_LR_ENOMEM;
     }
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    const int blocks = sms * 8;  // 2048 threads per SM
+    bool ok = cudaEventCreate(&e0) == cudaSuccess;
+    if (ok && cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        ok = false;
+    }
+    if (!ok) {
+        cudaFree(out);
+        cudaStreamDestroy(st);
+        return POTTS_LR_ECUDA;
+    }
     const int smem_iters = 1 << 16;
+    const int l2_iters = 256;
+    if (what == 3 && cudaMemsetAsync(out, 0, l2_per_cta * blocks * 16, st) != cudaSuccess) ok = false;
     double work = 0.0;
-    for (int rep = 0; rep < 2; ++rep) {  // first pass warms up
-        cudaEventRecord(e0, st);
+    for (int rep = 0; rep < 2 && ok; ++rep) {  // first pass warms up
+        ok = cudaEventRecord(e0, st) == cudaSuccess;
         if (what == 0) add_probe<double><<<blocks, kProbeThreads, 0, st>>>((double*)out, 1.0);
         else if (what == 1) add_probe<float><<<blocks, kProbeThreads, 0, st>>>((float*)out, 1.0f);
-        else smem_probe<<<blocks, kProbeThreads, 0, st>>>((float*)out, smem_iters);
-        cudaEventRecord(e1, st);
+        else if (what == 2) smem_probe<<<blocks, kProbeThreads, 0, st>>>((float*)out, smem_iters);
+        else l2_probe<<<blocks, kProbeThreads, 0, st>>>((float4*)out, l2_per_cta, l2_iters);
+        ok = ok && cudaGetLastError() == cudaSuccess && cudaEventRecord(e1, st) == cudaSuccess;
     }
-    if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) rc = POTTS_LR_ECUDA;
+    ok = cudaStreamSynchronize(st) == cudaSuccess && ok;
     float ms = 0.0f;
-    cudaEventElapsedTime(&ms, e0, e1);
+    ok = ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms > 0.0f;
     if (what <= 1) work = (double)blocks * kProbeThreads * kProbeIters * 16.0;  // adds
-    else work = (double)blocks * kProbeThreads * smem_iters * 4.0 * 2.0 * 4.0; // bytes (load + store)
-    *value = ms > 0.0f ? work / (ms * 1e-3) : 0.0;
+    else if (what == 2) work = (double)blocks * kProbeThreads * smem_iters * 4.0 * 2.0 * 4.0;  // bytes (load + store)
+    else work = (double)blocks * (double)l2_per_cta * l2_iters * 16.0 * 2.0;                 // bytes (load + store)
+    if (ok) *value = work / (ms * 1e-3);  // left untouched on any failure
+    else rc = POTTS_LR_ECUDA;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(out);
