@@ -7,7 +7,16 @@ energy and magnetisation measured every 10 sweeps.  One step = 10 x (one sweep
 of every slot + one exchange step) + one measurement, over all 8 chains.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload chains|precision]
+                  [--workload chains|precision|batching|serving|paper]
+
+Beside the main line (the eight chains in FP64), the default run adds one key
+per workload of the method's contract, each timed with CUDA events on its own
+stream: the precision job (L=4096 q=8 R=128) in FP32, FP64 and FX64 with a
+roofline for each sweep kernel and the FP32-vs-FP64 accuracy contract; the
+256 ragged jobs as one graph-captured batch; the serving trace (24 requests x
+5000 sweeps under a binding field-memory budget) beside the plain FP64
+per-job path on the same shapes; and the paper's benchmark protocol at two
+chain lengths against one host core.
 
 --impl reference times the CPU oracle (plain C, FP64, local-field mode) on
 the host cores on a bounded sample of the same workload.
@@ -40,9 +49,13 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="chains", choices=["chains", "precision", "batching", "serving", "paper"])
-    ap.add_argument("--serve-jobs", type=int, default=32)
-    ap.add_argument("--serve-sweeps", type=int, default=100)
+    ap.add_argument("--serve-jobs", type=int, default=24)
+    ap.add_argument("--serve-sweeps", type=int, default=5000)
+    ap.add_argument("--serve-budget-mib", type=float, default=64.0)
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--no-batching", action="store_true")
+    ap.add_argument("--no-paper", action="store_true")
     ap.add_argument("--precision", default=None, choices=[None, "fp64", "fp32", "fx64"])
     ap.add_argument("--no-fp32-compare", action="store_true")
     ap.add_argument("--no-fx64-compare", action="store_true")
@@ -202,51 +215,75 @@ def profiled_traffic():
     return None
 
 
-def rf_fits_shape(L, q):
-    """Whether the automatic FP32 sweep of an (L, q) chain keeps its fields in
-    registers (the library's register configurations)."""
-    for maxL, maxq in ((224, 16), (448, 16), (1120, 16), (2400, 8), (4320, 8), (7680, 5), (12480, 3), (16800, 2)):
-        if L <= maxL and q <= maxq:
-            return True
-    return False
+# shared-memory (or L2) bytes of one FX64 field update (one element of one
+# accepted flip): the two 8-byte field words read and written, the 8-byte
+# coupling read
+FX64_BYTES_PER_UPDATE = 5 * 8
+
+KERNEL_NAMES = {"memory": "sweep_kernel", "registers": "sweep_rf_kernel", "cluster": "sweep_cluster_kernel",
+                "direct": "sweep_direct_kernel"}
 
 
-# shared-memory bytes of one FX64 field update (one element of one accepted
-# flip): the two 8-byte field words read and written, the 8-byte coupling read
-FX64_SMEM_BYTES_PER_UPDATE = 5 * 8
+def kernel_label(info, prec):
+    """Name of the sweep kernel a job ran, from the library's own report
+    (potts_lr_sweep_info), with where its fields and table live."""
+    k = info["kernel"]
+    if k == "memory":
+        where = "fields %s, table %s" % ("in shared memory" if info["fields_in_smem"] else "in global memory",
+                                         "in shared memory" if info["table_in_smem"] else "in global memory")
+        return "sweep_kernel<%s> (%s)" % ({"fp64": "double", "fp32": "float", "fx64": "long long"}[prec], where)
+    if k == "registers":
+        return "sweep_rf_kernel (FP32 fields in registers, configuration %d)" % info["register_config"]
+    if k == "cluster":
+        return "sweep_cluster_kernel (FP32 fields shared by a %d-CTA cluster)" % info["cluster"]
+    return "sweep_direct_kernel (no fields)"
 
 
-def fx64_fields_in_smem(L, q):
-    """Whether the FX64 sweep kernel keeps a slot's fields and coupling table
-    in shared memory: the library's carve-up (table of Lpad + 4 words, q Lpad
-    field words, spins, flip lists, near table, reduction scratch) within its
-    220 KB budget."""
-    lpad = (L + 31) // 32 * 32
-    b = (lpad + 4) * 8 + q * lpad * 8 + lpad + 4 * 32 * 4 + 64 * 4 + 32 * 8 + 16
-    return (b + 15) // 16 * 16 <= 220 * 1024
-
-
-def fx64_smem_roofline(plr, res, specs):
-    """Shared-memory traffic of the FX64 sweep kernel's field updates (A L
-    element updates per attempt, 40 bytes each) over its average launch time,
-    against the measured shared-memory probe.  Where the fields sit in global
-    memory the same bytes go to L2 and no shared-memory roofline applies."""
+def sweep_roofline(plr, res, specs, sm_max_mhz, nsms):
+    """Roofline entry of the sweep kernel of a timed_device run.  Work per
+    attempt: A * 2L field additions (FP64 and FP32: against the add pipe's
+    unit-count peak and its measured probe) or A * L element updates of 40
+    bytes (FX64: against the measured shared-memory probe where the fields
+    sit in shared memory, the measured L2 probe where they sit in global
+    memory).  A = the measured acceptance; achieved = the work of one launch
+    over the average sweep launch time (CUDA events on the launching stream)."""
+    info = res["info"]
+    prec = specs[0].precision
+    A = res["acceptance"]
     att_launch = sum(s.L * s.R for s in specs)
+    upd_launch = sum(s.L * s.R * s.L for s in specs) * A  # element updates per launch (per state row pair)
     sweep_s = float(np.mean(res["sweep_ms"])) / 1e3
-    A, L = res["acceptance"], specs[0].L
-    achieved = att_launch * A * L * FX64_SMEM_BYTES_PER_UPDATE / sweep_s
-    work = ("A*L element updates per attempt, %d bytes each, A=%.4f measured; %d attempts per launch"
-            % (FX64_SMEM_BYTES_PER_UPDATE, A, att_launch))
-    if not all(fx64_fields_in_smem(s.L, s.q) for s in specs):
-        return {"bound": None, "achieved_update_bytes_gbs": achieved / 1e9, "traffic": None,
-                "kernel": "sweep_kernel<long long> (FX64 fields in global memory)", "work": work,
-                "note": "fields in global memory: the updates run against L2; no shared-memory roofline",
+    kernel = kernel_label(info, prec)
+    if prec == "fx64":
+        where = "smem" if info["fields_in_smem"] else "l2"
+        peak = plr.probe(where)
+        achieved = upd_launch * FX64_BYTES_PER_UPDATE / sweep_s
+        roof = {"bound": where, "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "kernel": kernel,
+                "work": "A*L element updates per attempt, %d bytes each, A=%.4f measured; %d attempts per launch"
+                        % (FX64_BYTES_PER_UPDATE, A, att_launch),
+                "peak_source": "measured %s probe (potts_lr_probe)" % ("shared-memory" if where == "smem" else "L2"),
                 "sweep_ms_avg": sweep_s * 1e3}
-    peak = plr.probe("smem")
-    return {"bound": "smem", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": None,
-            "kernel": "sweep_kernel<long long> (FX64 fields and table in shared memory)", "work": work,
-            "peak_source": "measured shared-memory probe (potts_lr_probe)", "sweep_ms_avg": sweep_s * 1e3}
+    else:
+        kind = "fp32" if prec == "fp32" else "fp64"
+        peak = alu_peak(kind, sm_max_mhz)
+        achieved = 2.0 * upd_launch / sweep_s
+        measured = plr.probe(kind + "_add")
+        roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_measured_probe": measured / 1e12, "frac_of_measured_probe": achieved / measured,
+                "kernel": kernel,
+                "work": "A*2L %s adds per attempt, A=%.4f measured; %d attempts per launch" % (prec, A, att_launch),
+                "peak_source": "unit counts x max SM clock (2 FP64 / 128 FP32 add lanes per SM per clock, 152 SMs)",
+                "sweep_ms_avg": sweep_s * 1e3}
+    nslots = sum(s.R for s in specs)
+    if nslots < nsms and info["kernel"] != "cluster":  # fewer slots than SMs: also against the SMs they occupy
+        roof["frac_of_occupied_sms"] = roof["frac"] * nsms / nslots
+        roof["occupied_sms"] = nslots
+    if prec == "fp32":
+        roof["sweep_ms_note"] = ("the timed sweep includes the conditional rebuild launches that follow every FP32 "
+                                 "sweep (they exit at once unless a rebuild is due)")
+    return roof
 
 
 def alu_peak(kind, sm_max_mhz):
@@ -372,7 +409,7 @@ def timed_device(plr, torch, specs, steps, warmup, dev, with_events=True, varian
     step_ms = sum(a.elapsed_time(b) for a, b in step_ev)
     sweep_ms = [a.elapsed_time(b) for a, b in sweep_ev]
     out = {"step_ms": step_ms, "att_step": att_step, "acceptance": (acc1 - acc0) / (steps * att_step),
-           "sweep_ms": sweep_ms, "steps": steps}
+           "sweep_ms": sweep_ms, "steps": steps, "info": jobs[0].sweep_info()}
     batch.close()
     for j in jobs:
         j.close()
@@ -417,12 +454,50 @@ def timed_e2e(plr, torch, specs, steps, warmup, dev):
             "d2h_bytes_per_step": d2h}
 
 
-def serving_run(plr, torch, dev, njobs, sweeps, fp64_sample=8, fp64_sweeps=10):
+def per_job_rates(plr, torch, dev, reqs, precision, min_seconds=0.25, max_sweeps=200):
+    """Each request's shape as a plain job of the given precision, alone on the
+    GPU (the per-job path), from its random start: one sweep + exchange of
+    warm-up, then as many timed sweeps + exchanges as take about min_seconds
+    (CUDA events on the job's stream, at least two).  Returns the attempts a
+    request asks for, the time the per-job path needs for all of them at its
+    sampled rate, and the samples."""
+    st = torch.cuda.Stream(device=dev)
+    total_att, total_s, rows = 0, 0.0, []
+    for r in reqs:
+        j = plr.Job(r.L, r.q, r.sigma, r.temps, r.seed, precision=precision, stream=st.cuda_stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        j.sweep(1)
+        j.exchange()
+        e1.record(st)
+        e1.synchronize()
+        first = max(e0.elapsed_time(e1) / 1e3, 1e-6)
+        n = max(2, min(max_sweeps, int(min_seconds / first)))
+        e0.record(st)
+        for _ in range(n):
+            j.sweep(1)
+            j.exchange()
+        e1.record(st)
+        e1.synchronize()
+        dt = e0.elapsed_time(e1) / 1e3
+        rate = n * r.L * r.R / dt
+        rows.append({"L": r.L, "q": r.q, "sigma": round(r.sigma, 4), "sampled_sweeps": n, "attempts_per_s": rate,
+                     "kernel": kernel_label(j.sweep_info(), precision)})
+        total_att += r.attempts
+        total_s += r.attempts / rate
+        j.close()
+    return total_att, total_s, rows
+
+
+def serving_run(plr, torch, dev, njobs, sweeps, budget_bytes):
     """The serving trace (Poisson arrivals at 50 jobs/s; q in {3,5,8}, sigma in
     U[0.1,1], L in {512..16384}, R=64, FP32 fields, K=100) cut to its first
-    njobs requests with `sweeps` sweeps each, served with continuous batching on
-    the wall clock; then the same requests' shapes run as plain FP64 jobs, one at
-    a time, for fp64_sweeps sweeps each (the per-job FP64 path)."""
+    njobs requests, each with its stated `sweeps`, served with continuous
+    batching on the wall clock under a field-memory budget (L q R 4 bytes per
+    job) small enough that admission binds.  Then the same requests, every one
+    of them, on the plain FP64 per-job path (and the exact FX64 one): each
+    shape alone on the GPU, its rate sampled, and the time the whole request
+    would take at that rate -- equal work on both sides of the ratio."""
     from paper_1308_5426_gb300 import workloads
     from paper_1308_5426_gb300.serve import GpuEngine, Request, Server
 
@@ -435,52 +510,60 @@ def serving_run(plr, torch, dev, njobs, sweeps, fp64_sample=8, fp64_sweeps=10):
 
     class Engine(GpuEngine):
         max_err = 0.0
+        peak_used = 0
 
         def destroy(self, job):
             Engine.max_err = max(Engine.max_err, job.fields_error())
             job.close()
 
-    free, _ = torch.cuda.mem_get_info(dev)
-    budget = int(0.5 * free)
     st = torch.cuda.Stream(device=dev)
-    srv = Server(Engine(stream=st.cuda_stream), budget_bytes=budget, chunk=10)
+    srv = Server(Engine(stream=st.cuda_stream), budget_bytes=budget_bytes, chunk=10)
+    max_concurrent = [0]
+    orig_admit = srv._admit
+
+    def admit(now):
+        ok = orig_admit(now)
+        max_concurrent[0] = max(max_concurrent[0], len(srv.active))
+        Engine.peak_used = max(Engine.peak_used, srv.used)
+        return ok
+    srv._admit = admit
     t0 = time.perf_counter()
     srv.run(reqs, idle_sleep=1e-4)
     torch.cuda.synchronize(dev)
     wall = time.perf_counter() - t0
     summ = srv.summary(wall_seconds=wall)
-    # plain FP64 per-job path on the same shapes
-    att64, t64 = 0, 0.0
-    for r in reqs[:fp64_sample]:
-        j = plr.Job(r.L, r.q, r.sigma, r.temps, r.seed, precision="fp64")
-        j.sync()
-        a = time.perf_counter()
-        for _ in range(fp64_sweeps):
-            j.sweep(1)
-            j.exchange()
-        j.sync()
-        t64 += time.perf_counter() - a
-        att64 += r.L * r.R * fp64_sweeps
-        j.close()
-    fp64_rate = att64 / t64
+    waited = [r.admitted - r.arrival for r in srv.results.values() if r.admitted is not None]
+    att64, t64, rows64 = per_job_rates(plr, torch, dev, reqs, "fp64")
+    attx, tx, rowsx = per_job_rates(plr, torch, dev, reqs, "fx64")
+    served = summ.get("attempts_per_s") or 0.0
     return {"jobs": len(reqs), "sweeps_per_job": sweeps,
-            "trace": "first %d requests of the 500-request Poisson(50/s) trace, seed 5; %d sweeps each "
-                     "instead of 5000" % (len(reqs), sweeps),
-            "budget_bytes": budget, "wall_s": wall, "attempts": summ["attempts"],
-            "attempts_per_s": summ.get("attempts_per_s"), "p50_latency_s": summ.get("p50_s"),
-            "p99_latency_s": summ.get("p99_s"), "done": summ["done"],
+            "trace": "first %d requests of the 500-request Poisson(50/s) trace, seed 5, each with its stated "
+                     "%d sweeps" % (len(reqs), sweeps),
+            "budget_bytes": budget_bytes, "total_footprint_bytes": sum(r.footprint for r in reqs),
+            "peak_admitted_bytes": Engine.peak_used, "max_concurrent_jobs": max_concurrent[0],
+            "max_queue_wait_s": max(waited) if waited else None,
+            "wall_s": wall, "attempts": summ["attempts"], "attempts_per_s": served,
+            "attempts_per_busy_s": summ.get("attempts_per_busy_s"),
+            "p50_latency_s": summ.get("p50_s"), "p99_latency_s": summ.get("p99_s"), "done": summ["done"],
             "max_field_error_rel_jtot": Engine.max_err,
-            "fp64_per_job_attempts_per_s": fp64_rate,
-            "fp64_per_job_sample": "first %d requests' shapes as FP64 jobs, one at a time, %d sweeps each"
-                                   % (min(fp64_sample, len(reqs)), fp64_sweeps),
-            "served_fp32_over_fp64_per_job": (summ.get("attempts_per_s") or 0.0) / fp64_rate}
+            "fp64_per_job_attempts_per_s": att64 / t64,
+            "fp64_per_job": "every request's shape as a plain FP64 job alone on the GPU, rate sampled over >= 0.25 s "
+                            "after one warm-up sweep; the full %d sweeps of all %d requests would take %.0f s at "
+                            "those rates" % (sweeps, len(reqs), t64),
+            "fp64_per_job_samples": rows64,
+            "fx64_per_job_attempts_per_s": attx / tx, "fx64_per_job_samples": rowsx,
+            "served_fp32_over_fp64_per_job": served / (att64 / t64),
+            "served_fp32_over_fx64_per_job": served / (attx / tx)}
 
 
-def batching_run(plr, torch, dev, steps, warmup):
+def batching_run(plr, torch, dev, steps, warmup, sm_max_mhz=None):
     """The 256 ragged jobs (L in {256..8192}, q in 2..10, sigma in U[0.1,1],
     R in {32,64,128}, FP32, K=100) created together and stepped as one
     graph-captured batch; each step = one sweep of every slot of every job +
-    one exchange step per job (+ the rebuilds that fall due)."""
+    one exchange step per job (+ the rebuilds that fall due).  The roofline
+    is that of the whole step: the FP32 field additions of every accepted flip
+    (2L per flip, counted from each job's own acceptance counters) over the
+    step time, against the FP32 add pipe's unit-count peak."""
     from paper_1308_5426_gb300 import workloads
     specs = workloads.batching_jobs()
     st = torch.cuda.Stream(device=dev)
@@ -488,26 +571,107 @@ def batching_run(plr, torch, dev, steps, warmup):
     b = plr.Batch(jobs, stream=st.cuda_stream)
     b.run(warmup, max(1, warmup))
     b.sync()
+    acc0 = [int(j.stats()["acc_flip"].sum()) for j in jobs]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(st)
     b.run(steps, min(10, steps))
     e1.record(st)
     e1.synchronize()
     ms = e0.elapsed_time(e1)
+    acc1 = [int(j.stats()["acc_flip"].sum()) for j in jobs]
     att = steps * sum(s.L * s.R for s in specs)
+    adds = sum(2.0 * s.L * (a1 - a0) for s, a0, a1 in zip(specs, acc0, acc1))
+    kinds = {}
+    for j in jobs:
+        k = j.sweep_info()["kernel"]
+        kinds[k] = kinds.get(k, 0) + 1
     b.close()
     for j in jobs:
         j.close()
+    peak = alu_peak("fp32", sm_max_mhz)
+    achieved = adds / (ms / 1e3)
     return {"jobs": len(specs), "slots": sum(s.R for s in specs), "steps": steps, "ms": ms,
-            "attempts_per_s": att / (ms / 1e3)}
+            "attempts_per_s": att / (ms / 1e3), "unit": "attempts/s",
+            "acceptance": sum(a1 - a0 for a0, a1 in zip(acc0, acc1)) / att, "sweep_kernels": kinds,
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "the whole batch step (every sweep kernel, rebuilds, exchanges)",
+                         "work": "2L FP32 adds per accepted flip, summed over the jobs' own counters",
+                         "peak_source": "unit counts x max SM clock (128 FP32 add lanes per SM per clock, 152 SMs)"}}
 
 
-def paper_run(plr, torch, dev, seconds_per_case=2.0):
+def precision_legs(plr, torch, dev, steps, warmup, sm_max_mhz, nsms):
+    """The precision job (L=4096 q=8 sigma=0.2 R=128, T/Jtot geometric
+    0.02-0.5, seed 1) in FP32 (split-BF16 tensor-core rebuilds, K=100), plain
+    FP64 and FX64 fields: each timed alone (step = 10 sweeps + exchanges + one
+    measurement), with the roofline of its sweep kernel."""
+    from paper_1308_5426_gb300 import workloads
+    out = {}
+    for prec in ("fp32", "fp64", "fx64"):
+        spec = workloads.precision_job(prec)
+        r = timed_device(plr, torch, [spec], steps, warmup, dev)
+        out["precision_" + prec] = {"value": r["steps"] * r["att_step"] / (r["step_ms"] / 1e3),
+                                    "unit": "attempts/s", "acceptance": r["acceptance"],
+                                    "ms_per_step": r["step_ms"] / r["steps"],
+                                    "roofline": sweep_roofline(plr, r, [spec], sm_max_mhz, nsms)}
+    return out
+
+
+def precision_accuracy(plr, torch, dev, warm=500, prod=2000, nbins=20, check_every=10):
+    """The precision contract on the precision job, same seed and call
+    sequence in FP32 (K=100) and FP64: the FP32 field drift (max |h32 - h64| /
+    Jtot, h64 the FP64 direct sums of the same spins) at a check every 10
+    sweeps over the whole run, and after `warm` sweeps the difference of <E>/L
+    and <M> per slot over `prod` sweeps (measured every sweep on the device,
+    binned in `nbins` bins) in units of the combined binned standard error."""
+    import math
+    from paper_1308_5426_gb300 import workloads
+    data, drift = {}, []
+    for prec in ("fp32", "fp64"):
+        spec = workloads.precision_job(prec)
+        st = torch.cuda.Stream(device=dev)
+        j = make_jobs(plr, [spec], st.cuda_stream)[0]
+        Eb = torch.zeros((prod, spec.R), dtype=torch.float64, device=dev)
+        Mb = torch.zeros((prod, spec.R), dtype=torch.float64, device=dev)
+        for n in range(warm + prod):
+            j.sweep(1)
+            j.exchange()
+            if n >= warm:
+                j.measure_device(Eb[n - warm].data_ptr(), Mb[n - warm].data_ptr())
+            if prec == "fp32" and (n + 1) % check_every == 0:
+                drift.append(j.fields_error())
+        j.sync()
+        data[prec] = ((Eb / spec.L).cpu().numpy(), Mb.cpu().numpy())
+        j.close()
+    out = {"protocol": "L=4096 q=8 sigma=0.2 R=128, seed 1, FP32 (K=100) vs FP64; %d warm-up + %d measured "
+                       "sweeps (each followed by an exchange), %d bins; drift checked every %d sweeps"
+                       % (warm, prod, nbins, check_every),
+           "max_field_drift_rel_jtot": max(drift), "drift_checks": len(drift)}
+    for k, name in ((0, "E_per_site"), (1, "M")):
+        stats = []
+        for prec in ("fp32", "fp64"):
+            x = data[prec][k]
+            b = x[: (x.shape[0] // nbins) * nbins].reshape(nbins, -1, x.shape[1]).mean(axis=1)
+            stats.append((b.mean(axis=0), b.std(axis=0, ddof=1) / math.sqrt(nbins)))
+        (m32, s32), (m64, s64) = stats
+        se = np.hypot(s32, s64)
+        diff = m32 - m64
+        frozen = se <= 1e-12 * np.maximum(np.abs(m64), 1.0)
+        z = np.where(frozen, 0.0, diff / np.where(frozen, 1.0, se))
+        out[name] = {"max_abs_fp32_minus_fp64": float(np.abs(diff).max()),
+                     "max_abs_diff_over_se": float(np.abs(z).max()),
+                     "slots_beyond_3_se": int((np.abs(diff) >= 3 * se + 1e-12).sum()),
+                     "frozen_slots_equal": bool(np.all(diff[frozen] == 0)), "frozen_slots": int(frozen.sum())}
+    return out
+
+
+def paper_run(plr, torch, dev, seconds_per_case=2.0, Ls=None, scan=True):
     """The paper's benchmark (Sec. 5.2, Fig. 4) and replica scan (Fig. 5) on
     this GPU, FP32 and FP64, against the oracle on one host core.  Each GPU
     case runs the protocol's sweeps from random spins (cut to about
     seconds_per_case); the oracle runs 8 of the 400 temperatures (every 50th)
-    from random spins for as many sweeps as fit in about seconds_per_case."""
+    from random spins for as many sweeps as fit in about seconds_per_case.
+    Ls: the chain lengths to run (default all nine); scan: the replica scan."""
     import oracle
     from paper_1308_5426_gb300 import workloads
 
@@ -548,12 +712,18 @@ def paper_run(plr, torch, dev, seconds_per_case=2.0):
 
     table = []
     for s in workloads.paper_benchmark_jobs():
+        if Ls is not None and s.L not in Ls:
+            continue
         g32, n32 = gpu_rate(s, 400, "fp32", s.sweeps)
         g64, n64 = gpu_rate(s, 400, "fp64", s.sweeps)
         c1, nc = cpu_rate(s)
         table.append({"L": s.L, "R": 400, "protocol_sweeps": s.sweeps, "gpu_fp32": g32, "gpu_fp32_sweeps": n32,
                       "gpu_fp64": g64, "gpu_fp64_sweeps": n64, "oracle_1core": c1, "oracle_sweeps": nc,
                       "speedup_fp32_vs_1core": g32 / c1, "speedup_fp64_vs_1core": g64 / c1})
+    if not scan:
+        return {"fig4_table": table,
+                "oracle_sample": "8 of the 400 temperatures (every 50th), one thread, FP64 local-field mode, "
+                                 "from random spins"}
     s1024 = [s for s in workloads.paper_benchmark_jobs() if s.L == 1024][0]
     c1024 = [row["oracle_1core"] for row in table if row["L"] == 1024][0]
     scan = []
@@ -611,7 +781,8 @@ def main():
             r = batching_run(plr, torch, dev, args.steps, args.warmup)
             value, ms_step = r["attempts_per_s"], r["ms"] / args.steps
         else:
-            r = serving_run(plr, torch, dev, args.serve_jobs, args.serve_sweeps)
+            r = serving_run(plr, torch, dev, args.serve_jobs, args.serve_sweeps,
+                            int(args.serve_budget_mib * 2 ** 20))
             value, ms_step = r["attempts_per_s"], 1e3 * r["wall_s"]
         ck = clocks.stop()
         if rank == 0:
@@ -634,35 +805,18 @@ def main():
     # roofline of the sweep kernel (the dominant kernel)
     prec = specs[0].precision
     A = res["acceptance"]
-    L = specs[0].L
-    att_launch = sum(s.L * s.R for s in specs)
-    sweep_avg_s = float(np.mean(res["sweep_ms"])) / 1e3
-    flops_launch = att_launch * A * 2 * L  # the rank-1 field updates: 2L adds per accepted flip
-    peak_adds = alu_peak("fp32" if prec == "fp32" else "fp64", ck.get("sm_max_mhz"))
-    achieved = flops_launch / sweep_avg_s
-    traffic = profiled_traffic() if (args.workload == "chains" and prec == "fp64") else None
-    measured = plr.probe("fp32_add" if prec == "fp32" else "fp64_add")
-    roof = fx64_smem_roofline(plr, res, specs) if prec == "fx64" else {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_adds / 1e12, "unit": "TFLOP/s",
-            "frac": achieved / peak_adds, "traffic": traffic,
-            "peak_measured_probe": measured / 1e12, "frac_of_measured_probe": achieved / measured,
-            "kernel": ("sweep_kernel<double> (fields in shared memory)" if prec == "fp64" else
-                       "sweep_rf_kernel (FP32 fields in registers)" if rf_fits_shape(L, specs[0].q) else
-                       "sweep_kernel<float> (FP32 fields in shared or global memory)"),
-            "work": "A*2L %s adds per attempt, A=%.4f measured; %d attempts per launch" % (prec, A, att_launch),
-            "peak_source": "unit counts x max SM clock (2 FP64 / 128 FP32 add lanes per SM per clock, 152 SMs)",
-            "sweep_ms_avg": sweep_avg_s * 1e3}
     nsms = torch.cuda.get_device_properties(dev).multi_processor_count
-    if att_launch // L < nsms and prec != "fx64":  # fewer slots than SMs: also against the SMs they occupy
-        occ = (att_launch // L) / nsms
-        roof["frac_of_occupied_sms"] = achieved / (peak_adds * occ)
-        roof["occupied_sms"] = att_launch // L
+    roof = sweep_roofline(plr, res, specs, ck.get("sm_max_mhz"), nsms)
+    if args.workload == "chains" and prec == "fp64":
+        roof["traffic"] = profiled_traffic()
 
     extra = {}
     if args.workload == "chains" and not args.no_fp32_compare and prec == "fp64":
         specs32, _ = workload_specs(args.workload, rank, "fp32")
-        r32 = timed_device(plr, torch, specs32, max(3, args.steps // 3), args.warmup, dev, with_events=False)
+        r32 = timed_device(plr, torch, specs32, max(3, args.steps // 3), args.warmup, dev)
         extra["fp32_same_workload"] = {"value": world * r32["steps"] * r32["att_step"] / (r32["step_ms"] / 1e3),
-                                       "unit": "attempts/s", "acceptance": r32["acceptance"]}
+                                       "unit": "attempts/s", "acceptance": r32["acceptance"],
+                                       "roofline": sweep_roofline(plr, r32, specs32, ck.get("sm_max_mhz"), nsms)}
     if args.workload == "chains" and not args.no_fx64_compare and prec == "fp64":
         # the same chains with 64-bit fixed-point fields: exact integer updates,
         # the same FP64 decisions
@@ -670,7 +824,7 @@ def main():
         rx = timed_device(plr, torch, specsx, max(3, args.steps // 3), args.warmup, dev)
         extra["fx64_same_workload"] = {
             "value": world * rx["steps"] * rx["att_step"] / (rx["step_ms"] / 1e3), "unit": "attempts/s",
-            "acceptance": rx["acceptance"], "roofline": fx64_smem_roofline(plr, rx, specsx)}
+            "acceptance": rx["acceptance"], "roofline": sweep_roofline(plr, rx, specsx, ck.get("sm_max_mhz"), nsms)}
     if args.workload == "chains" and not args.no_direct_compare and prec == "fp64":
         # the paper's scheme on the same workload: every proposal sums its O(L)
         # interaction (no fields), FP64
@@ -687,8 +841,20 @@ def main():
             "acceptance": rr["acceptance"],
             "kernel": "sweep_direct_kernel with random site order (attempts at Philox-drawn sites)"}
 
-    if args.workload == "chains" and not args.no_serving and world == 1:
-        extra["serving"] = serving_run(plr, torch, dev, args.serve_jobs, args.serve_sweeps)
+    if args.workload == "chains" and world == 1:
+        # the other workloads of the contract, each timed on its own stream
+        if not args.no_precision:
+            extra.update(precision_legs(plr, torch, dev, max(3, args.steps // 4), max(3, args.warmup),
+                                        ck.get("sm_max_mhz"), nsms))
+            extra["precision_config3"] = precision_accuracy(plr, torch, dev)
+        if not args.no_batching:
+            extra["batching_256"] = batching_run(plr, torch, dev, max(5, args.steps), max(3, args.warmup),
+                                                 ck.get("sm_max_mhz"))
+        if not args.no_serving:
+            extra["serving"] = serving_run(plr, torch, dev, args.serve_jobs, args.serve_sweeps,
+                                           int(args.serve_budget_mib * 2 ** 20))
+        if not args.no_paper:
+            extra["paper_protocol"] = paper_run(plr, torch, dev, seconds_per_case=1.0, Ls=(1024, 4096), scan=False)
 
     e2e = timed_e2e(plr, torch, specs, max(3, args.steps // 3), 1, dev)
     if world > 1:  # every rank runs the same amount of work: the slowest rank's rate, times the ranks

@@ -1,8 +1,9 @@
-"""Host arithmetic of bench.py's FX64 roofline entry (no GPU): the algorithmic
-shared-memory bytes of the field updates over the measured launch time, against
-a probe value, and the residency rule that decides whether that roofline
-applies (the library keeps FX64 fields and table in shared memory while they
-fit its 220 KB budget)."""
+"""Host arithmetic of bench.py's roofline entries (no GPU): the algorithmic
+work of one sweep launch over its measured duration, against the right
+denominator for the kernel the library reports it ran (potts_lr_sweep_info):
+FP64 or FP32 adds against the add pipe, FX64 update bytes against shared
+memory where the fields sit there and against L2 where they sit in global
+memory."""
 import os
 import sys
 
@@ -16,32 +17,65 @@ from paper_1308_5426_gb300 import workloads  # noqa: E402
 
 
 class FakeLib:
+    def __init__(self):
+        self.asked = []
+
     def probe(self, what):
-        assert what == "smem"
-        return 4.0e13
+        self.asked.append(what)
+        return {"smem": 4.0e13, "l2": 2.0e13, "fp64_add": 5.0e11, "fp32_add": 3.9e13}[what]
 
 
-def test_fx64_roofline_on_the_chain_workload():
+def _info(kernel="memory", hs=True, js=True, rf=0, cl=0):
+    return {"kernel": kernel, "fields_in_smem": hs, "table_in_smem": js, "register_config": rf, "cluster": cl,
+            "threads": 256, "smem_bytes": 0}
+
+
+def test_fx64_roofline_with_fields_in_shared_memory():
     specs = workloads.chains_jobs()
-    res = {"sweep_ms": [0.5, 0.5], "acceptance": 0.25}
-    r = bench.fx64_smem_roofline(FakeLib(), res, specs)
+    for s in specs:
+        s.precision = "fx64"
+    lib = FakeLib()
+    res = {"sweep_ms": [0.5, 0.5], "acceptance": 0.25, "info": _info()}
+    r = bench.sweep_roofline(lib, res, specs, 2070.0, 152)
     att = 8 * 1024 * 64
     want = att * 0.25 * 1024 * 40 / 0.5e-3
+    assert lib.asked == ["smem"]
     assert r["bound"] == "smem" and r["unit"] == "GB/s"
     assert r["achieved"] == pytest.approx(want / 1e9)
     assert r["peak"] == pytest.approx(40000.0)
     assert r["frac"] == pytest.approx(want / 4.0e13)
     assert r["sweep_ms_avg"] == pytest.approx(0.5)
+    assert "shared memory" in r["kernel"] and "long long" in r["kernel"]
 
 
-def test_fx64_residency_rule():
-    # L = 1024, q = 5: 8.2 KB of table + 40 KB of fields: shared memory
-    assert bench.fx64_fields_in_smem(1024, 5)
-    # L = 4096, q = 8: 256 KB of fields: global memory
-    assert not bench.fx64_fields_in_smem(4096, 8)
-    # the boundary: q Lpad 8 + (Lpad + 4) 8 + the rest within 220 KB
-    assert bench.fx64_fields_in_smem(2048, 12)
-    assert not bench.fx64_fields_in_smem(2048, 13)
+def test_fx64_roofline_with_fields_in_global_memory_uses_l2():
     s = workloads.precision_job("fx64")
-    r = bench.fx64_smem_roofline(FakeLib(), {"sweep_ms": [4.0], "acceptance": 0.1}, [s])
-    assert r["bound"] is None and "global" in r["kernel"]
+    lib = FakeLib()
+    res = {"sweep_ms": [4.0], "acceptance": 0.1, "info": _info(hs=False, js=True)}
+    r = bench.sweep_roofline(lib, res, [s], 2070.0, 152)
+    want = 4096 * 128 * 0.1 * 4096 * 40 / 4e-3
+    assert lib.asked == ["l2"] and r["bound"] == "l2"
+    assert r["achieved"] == pytest.approx(want / 1e9)
+    assert r["frac"] == pytest.approx(want / 2.0e13)
+    assert "global memory" in r["kernel"]
+    # 128 slots on 152 SMs: also against the occupied SMs
+    assert r["occupied_sms"] == 128 and r["frac_of_occupied_sms"] == pytest.approx(r["frac"] * 152 / 128)
+
+
+@pytest.mark.parametrize("prec,lanes", [("fp64", 2), ("fp32", 128)])
+def test_alu_roofline(prec, lanes):
+    specs = workloads.chains_jobs()
+    for s in specs:
+        s.precision = prec
+    lib = FakeLib()
+    info = _info("registers", rf=3) if prec == "fp32" else _info()
+    res = {"sweep_ms": [0.6], "acceptance": 0.2, "info": info}
+    r = bench.sweep_roofline(lib, res, specs, 2070.0, 152)
+    adds = 8 * 1024 * 64 * 0.2 * 2 * 1024
+    peak = 152 * lanes * 2070e6
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert r["achieved"] == pytest.approx(adds / 0.6e-3 / 1e12)
+    assert r["peak"] == pytest.approx(peak / 1e12)
+    assert r["frac"] == pytest.approx(adds / 0.6e-3 / peak)
+    assert "frac_of_occupied_sms" not in r  # 512 slots fill the SMs
+    assert ("registers" in r["kernel"]) == (prec == "fp32")
