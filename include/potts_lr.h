@@ -51,7 +51,8 @@
  *     mode's rule, the exact difference converted to FP64 once, so
  *     trajectories equal FP64 mode's except where |beta dE + ln u| is within
  *     rounding of zero (counted as near ties).  Same memory as FP64 mode; the updates run on the integer pipes
- *     instead of GB300's narrow FP64 pipe.  sweep_variant 0, 1 or 3.  EINVAL if
+ *     instead of GB300's narrow FP64 pipe.  sweep_variant 0 to 3 or 5 (0 keeps
+ *     the fields in registers where a register configuration holds them).  EINVAL if
  *     sigma is so small that F would fall below 24.  Energies and fields come
  *     out in FP64 (fields converted from field units).
  *
@@ -100,21 +101,27 @@ typedef struct {
                             does not fit: L <= 1120, or L <= 4320 with q <= 8, L <= 7680
                             with q <= 5, L <= 12480 with q <= 3, L <= 16800 with q = 2);
                             either mode: 3 = fields in global memory even where they fit
-                            in shared memory (FX64 mode: 0, 1 and 3 only); FP64 mode:
+                            in shared memory (FX64 mode: 0, 1, 2, 3 and 5; 2 = the FX64 fields
+                            in registers, EINVAL unless L <= 448, or L <= 1120 with q <= 8,
+                            L <= 2400 with q <= 5, L <= 4320 with q <= 3); FP64 mode:
                             4 = the direct sweep of the
                             paper (Sec. 4.2: every proposal sums its O(L) interaction,
                             no fields; same decisions up to rounding of the sum; L up to
-                            about 27000); FP32 mode: 5 = the slot's fields spread over
+                            about 27000); any mode: 5 = the slot's fields spread over
                             the shared memory of a cluster of 2, 4 or 8 CTAs (the
                             smallest that holds them; EINVAL if 8 do not; chosen by 0
-                            where the fields fit no registers and either fit no
-                            single CTA's shared memory or take more than 88 KB of
-                            it with R x C at most the SM count); FP32 mode:
+                            where the fields fit no registers and fit no single
+                            CTA's shared memory, and in FP32 mode also where they
+                            take more than 88 KB of it with R x C at most the SM
+                            count); FP32 mode:
                             16 + c (c = 1..8) = register
                             configuration c (E sites per update thread x update warps:
                             1x7, 2x7, 5x7, 5x15, 9x15, 16x15, 26x15, 35x15; q at most
                             16, 16, 16, 8, 8, 5, 3, 2; EINVAL if L > 32 x E x warps or q
-                            too large).  All variants give identical results. */
+                            too large); FX64 mode: 16 + c (c = 1..6) = FX64 register
+                            configuration c (1x7, 2x7, 4x8, 5x7, 5x15, 9x15; q at most 16,
+                            16, 8, 8, 5, 3).  All variants of a precision give identical
+                            results. */
     int site_order;      /* 0 = sites 0..L-1 in order (default); 1 = random sites: attempt
                             m of a sweep at site floor(x3 L / 2^32) of Philox counter
                             (m, slot, sweep, 3) -- the other reading of Sec. 4.2; runs
@@ -318,8 +325,9 @@ int potts_lr_measure_static(const uint32_t* spins, int L, int q, int R, const do
 
 /* Measurement utility (the paper has no counterpart): throughput of this
  * GPU's FP64 add pipe (what = 0, adds/s), FP32 add pipe (what = 1, adds/s),
- * shared memory (what = 2, bytes/s loaded + stored) or L2 (what = 3, bytes/s
- * loaded + stored on a 32 MB buffer resident in L2), measured with CUDA
+ * shared memory (what = 2, bytes/s loaded + stored), L2 (what = 3, bytes/s
+ * loaded + stored on a 32 MB buffer resident in L2) or 64-bit integer adds
+ * (what = 4, adds/s: the FX64 field update), measured with CUDA
  * events on the current device; the roofline denominators of the sweep
  * kernels.  Synchronous; allocates 16 bytes of device memory for the call
  * (32 MB for what = 3).  On any failure (ECUDA, ENOMEM) *value is left

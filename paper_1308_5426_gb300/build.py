@@ -15,6 +15,7 @@ LIB = os.path.join(OUT_DIR, "libpotts_lr.so")
 SOURCES = ["api.cu", "sweep.cu", "sweep_rf_a.cu", "sweep_rf_b.cu", "sweep_rf_c.cu", "sweep_rf_d.cu", "sweep_rf_e.cu",
            "sweep_rf_f.cu", "sweep_rf_g.cu", "sweep_rf_h.cu", "aux_kernels.cu", "rebuild_tc.cu", "probe.cu",
            "measure_static.cu", "sweep_sched.cu", "sweep_direct.cu", "sweep_rf_dispatch.cu", "sweep_cluster.cu",
+           "sweep_rfx_a.cu", "sweep_rfx_b.cu", "sweep_rfx_c.cu", "sweep_rfx_d.cu", "sweep_rfx_e.cu", "sweep_rfx_f.cu",
            "jstar.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

@@ -165,8 +165,6 @@ int check_opts(const potts_lr_opts* o)
     if (o->recompute_every < 0) return fail(POTTS_LR_EINVAL, "recompute_every must be >= 0");
     if (o->sweep_variant < 0 || (o->sweep_variant > 5 && (o->sweep_variant < 17 || o->sweep_variant > 24)))
         return fail(POTTS_LR_EINVAL, "sweep_variant must be 0..5 or 17..24");
-    if (o->sweep_variant == 5 && o->precision != POTTS_LR_FP32)
-        return fail(POTTS_LR_EINVAL, "the cluster sweep (sweep_variant 5) runs in FP32 mode only");
     if (o->sweep_variant == 4 && o->precision != POTTS_LR_FP64)
         return fail(POTTS_LR_EINVAL, "the direct sweep (sweep_variant 4) runs in FP64 mode only");
     if (o->site_order != 0 && o->site_order != 1) return fail(POTTS_LR_EINVAL, "site_order must be 0 or 1");
@@ -194,23 +192,31 @@ cudaError_t rebuild_launch(const potts_lr_t* h, const JobDev* job_dev, int cond,
 
 // the sweep kernel variant of a job: register-resident (per configuration and
 // q) or memory-resident (per precision and shared-memory residency)
-// keys: memory kernel 0..7 (precision, fields and table residency), direct
-// sweep 99, register kernel 100 + 32 configuration + q (132..372), cluster
-// kernel kClusterKey + cluster size
+// keys: memory kernel 0..11 (precision, fields and table residency), direct
+// sweep 99, FP32 register kernel 100 + 32 configuration + q (132..372), FX64
+// register kernel kRfxKey + 32 configuration + q (432..608), cluster kernel
+// kClusterKey + 16 precision + cluster size
 constexpr int kDirectKey = 99;
+constexpr int kRfxKey = 400;
 constexpr int kClusterKey = 1000;
 
 int variant_key(const potts_lr_t* h)
 {
     if (h->direct) return kDirectKey;
-    if (h->hj.cl) return kClusterKey + h->hj.cl;
-    return h->hj.rf ? 100 + h->hj.rf * 32 + h->q : h->precision * 4 + h->hj.h_smem * 2 + h->hj.j_smem;
+    if (h->hj.cl) return kClusterKey + 16 * h->precision + h->hj.cl;
+    if (h->hj.rf) return (h->precision == POTTS_LR_FX64 ? kRfxKey : 100) + h->hj.rf * 32 + h->q;
+    return h->precision * 4 + h->hj.h_smem * 2 + h->hj.j_smem;
 }
 
 cudaError_t launch_variant(int key, const JobDev* jobs, const int2* work, int nwork, int nsweeps, size_t smem,
                            const SweepSched* sched, cudaStream_t st)
 {
-    if (key > kClusterKey) return launch_sweep_cluster(key - kClusterKey, jobs, work, nwork, nsweeps, smem, st);
+    if (key > kClusterKey)
+        return launch_sweep_cluster((key - kClusterKey) % 16, (key - kClusterKey) / 16, jobs, work, nwork, nsweeps,
+                                    smem, st);
+    if (key >= kRfxKey)
+        return launch_sweep_rfx((key - kRfxKey) / 32, (key - kRfxKey) % 32, jobs, work, nwork, nsweeps, smem, sched,
+                                st);
     if (key >= 100)
         return launch_sweep_rf((key - 100) / 32, (key - 100) % 32, jobs, work, nwork, nsweeps, smem, sched, st);
     if (key == kDirectKey) return launch_sweep_direct(jobs, work, nwork, nsweeps, smem, st);
@@ -500,34 +506,45 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
             }
         }
     }
-    j.rf = (h->precision == POTTS_LR_FP32 && (o.sweep_variant == 0 || o.sweep_variant == 2)) ? rf_config(L, q) : 0;
+    if (o.sweep_variant == 0 || o.sweep_variant == 2)
+        j.rf = h->precision == POTTS_LR_FP32 ? rf_config(L, q) : h->precision == POTTS_LR_FX64 ? rfx_config(L, q) : 0;
     if (o.sweep_variant >= 17) {  // one register configuration, chosen by the caller (a tuner)
         const int cfg = o.sweep_variant - 16;
-        if (h->precision != POTTS_LR_FP32 || !rf_fits(cfg, L, q)) {
+        const bool ok = h->precision == POTTS_LR_FP32   ? rf_fits(cfg, L, q)
+                        : h->precision == POTTS_LR_FX64 ? rfx_fits(cfg, L, q)
+                                                        : false;
+        if (!ok) {
             potts_lr_destroy(h);
-            return fail(POTTS_LR_EINVAL, "register configuration %d does not hold L = %d, q = %d in FP32", cfg, L, q);
+            return fail(POTTS_LR_EINVAL, "register configuration %d does not hold L = %d, q = %d in this precision",
+                        cfg, L, q);
         }
         j.rf = cfg;
     }
     if (o.sweep_variant == 2 && !j.rf) {
         potts_lr_destroy(h);
         return fail(POTTS_LR_EINVAL, "register-resident sweep needs FP32 and L <= 1120, or L <= 4320 with q <= 8 "
-                                     "(7680 with q <= 5, 12480 with q <= 3, 16800 with q = 2)");
+                                     "(7680 with q <= 5, 12480 with q <= 3, 16800 with q = 2), or FX64 and L <= 448, "
+                                     "or L <= 1120 with q <= 8 (2400 with q <= 5, 4320 with q <= 3)");
     }
     h->dj = (JobDev*)(base + o_job);
     h->dwork = (int2*)(base + o_work);
-    h->sweep_smem = j.rf ? rf_smem_bytes(j.rf, q, L, h->Lpad) : sweep_smem_bytes(j);
+    h->sweep_smem = !j.rf                              ? sweep_smem_bytes(j)
+                    : h->precision == POTTS_LR_FX64 ? rfx_smem_bytes(j.rf, q, L, h->Lpad)
+                                                    : rf_smem_bytes(j.rf, q, L, h->Lpad);
     // FP32 fields that fit no registers: a cluster of CTAs shares them when
     // they fit no single CTA's shared memory, or fill most of one (then one
     // CTA per SM sweeps the slot with few update warps) while the job's
     // clusters fit on the GPU at once (measured: 2-2.6x faster at 64 slots;
     // on a GPU already filled by many jobs' slots, about even); or when asked
     // for (variant 5)
-    if (h->precision == POTTS_LR_FP32 && !j.rf && (o.sweep_variant == 0 || o.sweep_variant == 5)) {
-        const int C = cluster_size_for(L, q, kSmemBudget);
+    // for (variant 5).  FP64 and FX64 fields take a cluster when they fit no
+    // single CTA's shared memory.
+    if (!j.rf && (o.sweep_variant == 0 || o.sweep_variant == 5)) {
+        const int C = cluster_size_for(L, q, kSmemBudget, h->precision);
+        const bool fp32 = h->precision == POTTS_LR_FP32;
         const bool big = (size_t)q * h->Lpad * 4 > kClusterFieldBytes;
         const bool fits_gpu = (long long)R * C <= (long long)std::max(1, device_sm_count());
-        if (o.sweep_variant == 5 || (C && (!j.h_smem || (big && fits_gpu)))) {
+        if (o.sweep_variant == 5 || (C && (!j.h_smem || (fp32 && big && fits_gpu)))) {
             if (!C) {
                 potts_lr_destroy(h);
                 return fail(POTTS_LR_EINVAL, "the cluster sweep holds at most 8 x %zu bytes of fields and spins",
@@ -535,7 +552,7 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
             }
             j.cl = C;
             h->cl_auto = o.sweep_variant == 0;
-            h->sweep_smem = cluster_sweep_smem(L, q, C);
+            h->sweep_smem = cluster_sweep_smem(L, q, C, h->precision);
         }
     }
     j.random_sites = o.site_order;
@@ -849,8 +866,10 @@ int potts_lr_sweep_info(potts_lr_t* h, int32_t* info, int n)
     const int kind = h->direct ? 3 : j.cl ? 2 : j.rf ? 1 : 0;
     // threads per CTA of each kernel: register configurations 1-3 run 7 update
     // warps, 4-8 run 15, plus the decision warp; the direct sweep one warp
-    const int threads = kind == 3 ? 32 : kind == 2 ? 512 : kind == 1 ? (j.rf <= 3 ? 256 : 512)
-                                                                      : (j.h_smem ? 256 : 512);
+    const int threads = kind == 3 ? 32
+                        : kind == 2 ? 512
+                        : kind == 1 ? (h->precision == POTTS_LR_FX64 ? rfx_threads(j.rf) : (j.rf <= 3 ? 256 : 512))
+                                    : (j.h_smem ? 256 : 512);
     const int32_t v[7] = {kind, kind == 0 ? j.h_smem : 0, kind == 0 ? j.j_smem : 0, j.rf, j.cl, threads,
                           (int32_t)h->sweep_smem};
     for (int i = 0; i < n && i < 7; ++i) info[i] = v[i];

@@ -31,7 +31,7 @@ struct JobDev {
     int L, q, Lpad, W, R, c, precision;
     int recompute_every;  // FP32 mode: longest interval K between field rebuilds (0 = on request only)
     int h_smem, j_smem;   // sweep kernel: fields / coupling table staged in shared memory
-    int rf;               // FP32 mode: register-resident sweep configuration (0 = none, 1..8)
+    int rf;               // register-resident sweep configuration (0 = none; FP32 mode 1..8, FX64 mode 1..6)
     int cl;               // FP32 mode: CTAs of the cluster that shares a slot's fields (0 = none; 2, 4, 8)
     int random_sites;     // direct sweep: attempt m at a site drawn from Philox counter (m, slot, sweep, 3)
     uint32_t key0, key1;  // Philox key (seed low, high)
@@ -165,12 +165,12 @@ size_t direct_sweep_smem_bytes(int L, int Lpad);
 cudaError_t launch_sweep_direct(const JobDev* jobs_dev, const int2* work, int nwork, int nsweeps, size_t smem,
                                 cudaStream_t st);
 
-// Cluster FP32 sweep (sweep_cluster.cu): a slot's fields spread over the
-// shared memory of a cluster of C = 2, 4 or 8 CTAs.
-size_t cluster_sweep_smem(int L, int q, int C);
-int cluster_size_for(int L, int q, size_t budget);  // smallest C whose share fits budget (0: none)
-cudaError_t launch_sweep_cluster(int C, const JobDev* jobs_dev, const int2* work, int nwork, int nsweeps,
-                                 size_t smem, cudaStream_t st);
+// Cluster sweep (sweep_cluster.cu): a slot's fields (FP32, FP64 or FX64)
+// spread over the shared memory of a cluster of C = 2, 4 or 8 CTAs.
+size_t cluster_sweep_smem(int L, int q, int C, int precision);
+int cluster_size_for(int L, int q, size_t budget, int precision);  // smallest C whose share fits (0: none)
+cudaError_t launch_sweep_cluster(int C, int precision, const JobDev* jobs_dev, const int2* work, int nwork,
+                                 int nsweeps, size_t smem, cudaStream_t st);
 
 // Register-resident FP32 sweep (sweep_rf.cuh): configuration 1..8 =
 // (E sites per update thread, update warps) = (1, 7), (2, 7), (5, 7) for
@@ -198,6 +198,28 @@ cudaError_t launch_sweep_rf_g(int q, const JobDev*, const int2*, int, int, size_
                              cudaStream_t);
 cudaError_t launch_sweep_rf_h(int q, const JobDev*, const int2*, int, int, size_t, const SweepSched*,
                              cudaStream_t);
+// Register-resident FX64 sweep (sweep_rf.cuh with 64-bit integer fields):
+// configuration 1..6 = (E, update warps) = (1, 7), (2, 7), (4, 8), (5, 7),
+// (5, 15), (9, 15) for L <= 224, 448, 1024, 1120, 2400, 4320 with q at most
+// 16, 16, 8, 8, 5, 3; rfx_config: 4 where it fits, else the fewest sites per
+// thread that hold the chain, 0 if none does.
+int rfx_config(int L, int q);
+bool rfx_fits(int cfg, int L, int q);
+int rfx_threads(int cfg);  // threads per CTA of configuration cfg
+size_t rfx_smem_bytes(int cfg, int q, int L, int Lpad);
+cudaError_t launch_sweep_rfx(int cfg, int q, const JobDev* jobs_dev, const int2* work, int nwork, int nsweeps,
+                             size_t smem, const SweepSched* sched, cudaStream_t st);
+#define PLR_RFX_DECL(tag)                                                                                    \
+    cudaError_t launch_sweep_rfx_##tag(int q, const JobDev*, const int2*, int, int, size_t, const SweepSched*, \
+                                       cudaStream_t);                                                          \
+    size_t sweep_rfx_smem_##tag(int q, int L, int Lpad);
+PLR_RFX_DECL(a)
+PLR_RFX_DECL(b)
+PLR_RFX_DECL(c)
+PLR_RFX_DECL(d)
+PLR_RFX_DECL(e)
+PLR_RFX_DECL(f)
+#undef PLR_RFX_DECL
 size_t sweep_rf_smem_a(int q, int L, int Lpad);
 size_t sweep_rf_smem_b(int q, int L, int Lpad);
 size_t sweep_rf_smem_c(int q, int L, int Lpad);

@@ -325,7 +325,14 @@ __device__ __forceinline__ void sweep_item(const JobDev* __restrict__ jobs, cons
         const int n = q * Lpad;
         for (int e = tid; e < n; e += NT) hg[e] = hs[e];
     }
-    if constexpr (kFP64) {
+    double Efx = 0.0;
+    if constexpr (kFX) {
+        // E = -(c/2) sum_i h[s_i][i] from the integer fields, the sum exact in
+        // 128 bits, so that every FX64 kernel variant gets the same value
+        unsigned long long lo = 0, hi = 0;
+        for (int i = tid; i < L; i += NT) u128_add(lo, hi, (unsigned long long)h[(size_t)s[i] * Lpad + i]);
+        Efx = block_sum_u128(lo, hi, (unsigned long long*)red);
+    } else if constexpr (kFP64) {
         // E = -(c/2) sum_i h[s_i][i] from the FP64 fields (Eq. 2 through the
         // fields), summed over 256 fixed strands whatever the CTA size, so
         // that every kernel variant rounds the sum alike
@@ -343,10 +350,12 @@ __device__ __forceinline__ void sweep_item(const JobDev* __restrict__ jobs, cons
     }
     __syncthreads();
     if (tid == 0) {
-        if constexpr (kFP64) {
+        if constexpr (kFX) {
+            jp->E[rep] = -0.5 * (double)c * Efx * fxs;  // fxs: FX64 field units (a power of two)
+        } else if constexpr (kFP64) {
             double tot = 0.0;
             for (int w = 0; w < kSweepThreads / 32; ++w) tot += red[w];
-            jp->E[rep] = -0.5 * (double)c * tot * fxs;  // fxs: FX64 field units (a power of two)
+            jp->E[rep] = -0.5 * (double)c * tot;
         } else {
             jp->E[rep] += dE_acc;
         }

@@ -14,6 +14,42 @@ constexpr unsigned kFullMask = 0xffffffffu;
 constexpr int kNearTable = 64;  // J* in FP32 for distances < 64 (corrections within two blocks)
 enum : int { kReject = 0, kAccept = 1, kUnsure = 2 };
 
+// (lo, hi) += v: 128-bit unsigned accumulation
+__device__ __forceinline__ void u128_add(unsigned long long& lo, unsigned long long& hi, unsigned long long v)
+{
+    lo += v;
+    hi += lo < v ? 1ull : 0ull;
+}
+
+// Exact sum over the CTA of every thread's 128-bit (lo, hi), returned to every
+// thread as hi 2^64 + lo in FP64 by one fixed formula -- the same value
+// whatever the order of the terms (FX64 energies, from non-negative integer
+// fields).  scratch: shared memory of 2 words per warp of the CTA.
+__device__ __forceinline__ double block_sum_u128(unsigned long long lo, unsigned long long hi,
+                                                 unsigned long long* scratch)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long l2 = __shfl_xor_sync(kFullMask, lo, o);
+        const unsigned long long h2 = __shfl_xor_sync(kFullMask, hi, o);
+        u128_add(lo, hi, l2);
+        hi += h2;
+    }
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();  // the scratch may have been read by an earlier step
+    if ((threadIdx.x & 31) == 0) {
+        scratch[2 * warp] = lo;
+        scratch[2 * warp + 1] = hi;
+    }
+    __syncthreads();
+    unsigned long long L0 = 0, H0 = 0;
+    for (int w = 0; w < nw; ++w) {
+        u128_add(L0, H0, scratch[2 * w]);
+        H0 += scratch[2 * w + 1];
+    }
+    __syncthreads();
+    return (double)H0 * 0x1p64 + (double)L0;
+}
+
 // FP64 rule, evaluated exactly: dE <= 0 or u < exp(-beta dE).  A decision
 // with |beta dE + ln u| < 1e-9 (on either branch) is a near tie: counted, and
 // logged as attempt `attempt` of slot ns.t at sweep ns.n.

@@ -1,4 +1,6 @@
-// Register-resident FP32 Metropolis sweep (Eq. 8, Sec. 4.2 of the paper).
+// Register-resident Metropolis sweep (Eq. 8, Sec. 4.2 of the paper), FP32
+// fields (T = float) or FX64 fields (T = long long: 64-bit integers in units
+// of 2^-F, exact integer updates, the FP64 rule's decisions).
 //
 // One CTA sweeps one temperature slot at a time: NU update warps hold the local fields
 // h[x][i] of their sites in registers, one decision warp holds none.  Update
@@ -17,9 +19,12 @@
 //     proposals.
 // One CTA barrier per block; deciding and updating overlap.
 //
-// The arithmetic is that of the shared-memory kernel -- the same FP32 values
-// J*, the same subtractions and additions in flip order, the same decisions
-// and the same grouping of the energy sum -- so both give identical results.
+// The arithmetic is that of the shared-memory kernel -- the same values J*,
+// the same subtractions and additions in flip order, the same decisions and
+// (FP32) the same grouping of the energy sum, (FX64) the same exact integer
+// energy sum -- so both give identical results.  FX64 decisions take the FP64
+// rule through decide_block<2>: the FP32 screen, and where it cannot tell,
+// the exact integer difference converted to FP64 once.
 #pragma once
 #include "sweep_common.cuh"
 #include "sweep_sched.cuh"
@@ -27,19 +32,20 @@
 namespace plr {
 namespace rf {
 
-template <int NU, int E, int Q>
+template <typename T, int NU, int E, int Q>
 struct RfSmem {
     static size_t bytes(int L, int Lpad)
     {
-        size_t b = (size_t)(E * 32 * NU + L) * sizeof(float);  // J*(m mod L), m < E 32 NU + L
-        b += (size_t)Lpad;                                       // spins
+        size_t b = (size_t)(E * 32 * NU + L) * sizeof(T);  // J*(m mod L), m < E 32 NU + L
+        b += (size_t)Lpad;                                   // spins
         b = (b + 15) & ~(size_t)15;
         b += 2 * 2 * kSiteBlock * sizeof(int);   // double-buffered flip lists
         b += kNearTable * sizeof(float);         // J*(r), r < 64
         b += 32 * sizeof(double);                // per-lane energy change
+        b += 2 * Q * kSiteBlock * sizeof(T);     // published field values, double-buffered
         b += 2 * kSiteBlock * sizeof(int);       // proposals (a << 8 | b), double-buffered
         b += 2 * kSiteBlock * sizeof(float);     // -ln u, double-buffered
-        b += 2 * Q * kSiteBlock * sizeof(float); // published field values, double-buffered
+        b += 2 * 2 * kSiteBlock * sizeof(uint32_t);  // the words u is made of (FP64 rule), double-buffered
         b += 16;                                 // flip counts
         return (b + 15) & ~(size_t)15;
     }
@@ -53,13 +59,13 @@ struct RfSmem {
         break;
 
 // apply flips (pk, pab)[0..nf) to all register rows of update thread u
-template <int Q, int E, int NU>
-__device__ __forceinline__ void apply_rows(float (&h)[E][Q], const float* __restrict__ J2, int u, int L,
-                                           const int* pk, const int* pab, int nf)
+template <typename T, int Q, int E, int NU>
+__device__ __forceinline__ void apply_rows(T (&h)[E][Q], const T* __restrict__ J2, int u, int L, const int* pk,
+                                           const int* pab, int nf)
 {
     for (int f = 0; f < nf; ++f) {
         const int kf = pk[f], af = pab[f] >> 8, bf = pab[f] & 255;
-        float v[E];
+        T v[E];
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = J2[m * 32 * NU + u - kf + L];
         switch (af) {
@@ -82,8 +88,8 @@ __device__ __forceinline__ void apply_rows(float (&h)[E][Q], const float* __rest
 #undef PLR_RF_CASE
 
 // publish register row M (all states) of this lane: hv[x][lane] = h[M][x]
-template <int Q, int E>
-__device__ __forceinline__ void publish_row(const float (&h)[E][Q], int M, float* hv, int lane)
+template <typename T, int Q, int E>
+__device__ __forceinline__ void publish_row(const T (&h)[E][Q], int M, T* hv, int lane)
 {
 #pragma unroll
     for (int m = 0; m < E; ++m)
@@ -94,22 +100,24 @@ __device__ __forceinline__ void publish_row(const float (&h)[E][Q], int M, float
 }
 
 // CTAs per SM to aim for, holding the compiler to the matching register budget
-template <int Q, int E, int NU>
+template <typename T, int Q, int E, int NU>
 constexpr int rf_min_blocks()
 {
+    constexpr int w = sizeof(T) / 4;  // registers per field value
     const int threads = 32 * (NU + 1);
-    if (Q * E <= 25 && threads <= 256) return 4;  // fits 64 registers
-    const int need = threads * (Q * E + E + 48);
+    if (w * Q * E <= 25 && threads <= 256) return 4;  // fits 64 registers
+    const int need = threads * (w * (Q * E + E) + 48);
     const int b = 65536 / need;
     return b < 1 ? 1 : (b > 4 ? 4 : b);
 }
 
 // nsweeps sweeps of one work item wk = (job, slot) by the whole CTA
-template <int Q, int E, int NU>
+template <typename T, int Q, int E, int NU>
 __device__ __forceinline__ void rf_item(const JobDev* __restrict__ jobs, const int2 wk, int nsweeps,
                                         unsigned char* __restrict__ smem)
 {
-    constexpr int NUT = 32 * NU;  // update threads
+    constexpr bool kFX = sizeof(T) == 8;  // FX64 fields: the FP64 rule
+    constexpr int NUT = 32 * NU;          // update threads
     const JobDev* jp = jobs + wk.x;
     const int t = wk.y;
     const int L = jp->L, q = jp->q, Lpad = jp->Lpad, W = jp->W, c = jp->c;
@@ -118,39 +126,44 @@ __device__ __forceinline__ void rf_item(const JobDev* __restrict__ jobs, const i
     const double beta = jp->beta[t];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool decider = warp == NU;
-    float* __restrict__ hg = (float*)jp->fields + (size_t)rep * q * Lpad;
+    T* __restrict__ hg = (T*)jp->fields + (size_t)rep * q * Lpad;
     uint32_t* __restrict__ spins = jp->spins + (size_t)rep * W;
+    const T* __restrict__ Jsrc = kFX ? (const T*)(const void*)jp->Jfxd : (const T*)(const void*)jp->J32d;
 
-    float* J2 = (float*)smem;
-    size_t off = (size_t)(E * NUT + L) * sizeof(float);
+    T* J2 = (T*)smem;
+    size_t off = (size_t)(E * NUT + L) * sizeof(T);
     uint8_t* s = smem + off;
     off = (off + (size_t)Lpad + 15) & ~(size_t)15;
     int* lk = (int*)(smem + off);
     int* lab = lk + 2 * kSiteBlock;
     float* Jn = (float*)(lab + 2 * kSiteBlock);
     double* dEl = (double*)(Jn + kNearTable);
-    int* pab = (int*)(dEl + 32);            // [2][32] proposals
+    T* hv = (T*)(dEl + 32);                 // [2][Q][32] published field values
+    int* pab = (int*)(hv + 2 * Q * kSiteBlock);  // [2][32] proposals
     float* pnlu = (float*)(pab + 2 * kSiteBlock);
-    float* hv = pnlu + 2 * kSiteBlock;      // [2][Q][32]
-    int* lcnt = (int*)(hv + 2 * Q * kSiteBlock);
+    uint32_t* pux = (uint32_t*)(pnlu + 2 * kSiteBlock);  // [2][2][32] words of u (FP64 rule)
+    int* lcnt = (int*)(pux + 4 * kSiteBlock);
 
-    for (int m = tid; m < E * NUT + L; m += blockDim.x) J2[m] = jp->J32d[m % L];
+    for (int m = tid; m < E * NUT + L; m += blockDim.x) J2[m] = Jsrc[m % L];
     for (int i = tid; i < L; i += blockDim.x) s[i] = (uint8_t)((spins[i >> 3] >> (4 * (i & 7))) & 15u);
     if (tid < kNearTable) Jn[tid] = tid < L ? (float)jp->J64d[tid] : 0.0f;
     if (tid < 32) dEl[tid] = 0.0;
     if (tid < 2) lcnt[tid] = 0;
-    float h[E][Q];
+    T h[E][Q];
 #pragma unroll
     for (int m = 0; m < E; ++m) {
         const int i = m * NUT + tid;
 #pragma unroll
-        for (int x = 0; x < Q; ++x) h[m][x] = (!decider && i < L) ? hg[(size_t)x * Lpad + i] : 0.0f;
+        for (int x = 0; x < Q; ++x) h[m][x] = (!decider && i < L) ? hg[(size_t)x * Lpad + i] : (T)0;
     }
     __syncthreads();
 
     const uint32_t n0 = jp->nsweep[t];
     const double cb64 = beta * (double)c;
     const float cb32 = (float)cb64;
+    const float errd = kFX ? (float)(2.4e-5 * jp->jtot) : 0.0f;  // FP32 screen margin of the FP64 rule
+    const double fxs = kFX ? jp->fx_scale : 1.0;                  // value of one field unit
+    const float fxs32 = (float)fxs;                               // a power of two: exact
     unsigned long long nacc = 0, nnear = 0;
     const int nblk = (L + kSiteBlock - 1) / kSiteBlock;
     const int total = nsweeps * nblk;
@@ -160,19 +173,23 @@ __device__ __forceinline__ void rf_item(const JobDev* __restrict__ jobs, const i
         const int k = (g % nblk) * kSiteBlock + lane;
         int a = 0, b = 0;
         float nlu = 0.0f;
+        uint32_t ux1 = 0, ux2 = 0;
         if (k < L) {
-            uint32_t ux1, ux2;
             a = s[k];
-            draw_proposal<false>(k, t, n0 + (uint32_t)(g / nblk), key0, key1, q, a, b, nlu, ux1, ux2);
+            draw_proposal<kFX>(k, t, n0 + (uint32_t)(g / nblk), key0, key1, q, a, b, nlu, ux1, ux2);
         }
         pab[(g & 1) * kSiteBlock + lane] = (a << 8) | b;
         pnlu[(g & 1) * kSiteBlock + lane] = nlu;
+        if constexpr (kFX) {
+            pux[(g & 1) * 2 * kSiteBlock + lane] = ux1;
+            pux[(g & 1) * 2 * kSiteBlock + kSiteBlock + lane] = ux2;
+        }
     };
     // field values and proposals of block g into buffer g & 1 (its owner warp)
     auto publish_block = [&](int g) {
         const int gb = g % nblk;
         if (warp == gb % NU) {
-            publish_row<Q, E>(h, gb / NU, hv + (g & 1) * Q * kSiteBlock, lane);
+            publish_row<T, Q, E>(h, gb / NU, hv + (g & 1) * Q * kSiteBlock, lane);
             if (nblk > 1 || g == 0) draw_block(g);
         }
     };
@@ -201,19 +218,35 @@ __device__ __forceinline__ void rf_item(const JobDev* __restrict__ jobs, const i
                 const int a = ab >> 8, b = ab & 255;
                 const float nlu = pnlu[cb * kSiteBlock + lane];
                 float d32 = 0.0f;
+                long long dfx = 0;
                 if (valid) {
-                    const float* hvb = hv + cb * Q * kSiteBlock;
-                    d32 = hvb[a * kSiteBlock + lane] - hvb[b * kSiteBlock + lane];
+                    const T* hvb = hv + cb * Q * kSiteBlock;
+                    const T dd = hvb[a * kSiteBlock + lane] - hvb[b * kSiteBlock + lane];
+                    if constexpr (kFX) {
+                        dfx = (long long)dd;
+                        d32 = (float)dd * fxs32;
+                    } else {
+                        d32 = (float)dd;
+                    }
                 }
                 int* ck = lk + cb * kSiteBlock;
                 int* cab = lab + cb * kSiteBlock;
                 bool mine;
                 float dmine;
-                const int nf = decide_block<false>(lane, nv, k, L, a, b, nlu, 0u, 0u, d32, 0.0, pk, pl, npend,
-                                                   cb32, cb64, 0.0f, Jn, nullptr, ck, cab, mine, dmine, nnear);
+                int nf;
+                if constexpr (kFX) {
+                    const uint32_t ux1 = pux[cb * 2 * kSiteBlock + lane], ux2 = pux[cb * 2 * kSiteBlock + kSiteBlock + lane];
+                    nf = decide_block<2>(lane, nv, k, L, a, b, nlu, ux1, ux2, d32, 0.0, pk, pl, npend, cb32, cb64,
+                                         errd, Jn, nullptr, ck, cab, mine, dmine, nnear, dfx,
+                                         (const long long*)(const void*)J2, fxs,
+                                         NearSink{jp->near_log, jp->near_log_n, t, n0 + (uint32_t)(g / nblk)});
+                } else {
+                    nf = decide_block<0>(lane, nv, k, L, a, b, nlu, 0u, 0u, d32, 0.0, pk, pl, npend, cb32, cb64,
+                                         0.0f, Jn, nullptr, ck, cab, mine, dmine, nnear);
+                }
                 if (mine) {
                     s[k] = (uint8_t)b;
-                    dEl[lane] += (double)((float)c * dmine);
+                    if constexpr (!kFX) dEl[lane] += (double)((float)c * dmine);
                 }
                 if (lane == 0) {
                     lcnt[cb] = nf;
@@ -221,7 +254,7 @@ __device__ __forceinline__ void rf_item(const JobDev* __restrict__ jobs, const i
                 }
             }
         } else {
-            apply_rows<Q, E, NU>(h, J2, tid, L, pk, pl, npend);
+            apply_rows<T, Q, E, NU>(h, J2, tid, L, pk, pl, npend);
             if (g + 1 < total) publish_block(g + 1);
         }
         __syncthreads();
@@ -245,7 +278,36 @@ __device__ __forceinline__ void rf_item(const JobDev* __restrict__ jobs, const i
                 for (int x = 0; x < Q; ++x) hg[(size_t)x * Lpad + i] = h[m][x];
             }
         }
-    } else {
+    }
+    if constexpr (kFX) {
+        // E = -(c/2) sum_i h[s_i][i], the sum exact in 128-bit integers (every
+        // FX64 variant then rounds it alike), counted once per launch
+        unsigned long long lo = 0, hi = 0;
+        if (!decider) {
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                const int i = m * NUT + tid;
+                if (i < L) {
+                    const int si = s[i];
+                    long long v = 0;
+#pragma unroll
+                    for (int x = 0; x < Q; ++x) v = x == si ? h[m][x] : v;
+                    u128_add(lo, hi, (unsigned long long)v);
+                }
+            }
+        }
+        // scratch: the per-lane energy buffer (unused in FX64 mode), 32 words
+        const double Efx = block_sum_u128(lo, hi, (unsigned long long*)dEl);
+        if (tid == 0) jp->E[rep] = -0.5 * (double)c * Efx * fxs;  // fxs: a power of two
+        if (decider) {  // the counts live in the decision warp
+            for (int o = 16; o > 0; o >>= 1) nnear += __shfl_xor_sync(kFullMask, nnear, o);
+            if (lane == 0) {
+                jp->nsweep[t] = n0 + (uint32_t)nsweeps;
+                if (nacc) atomicAdd(&jp->acc_flip[t], nacc);
+                if (nnear) atomicAdd(&jp->near[0], nnear);
+            }
+        }
+    } else if (decider) {
         double dE = dEl[lane];
         for (int o = 16; o > 0; o >>= 1) dE += __shfl_xor_sync(kFullMask, dE, o);
         if (lane == 0) {
@@ -257,13 +319,13 @@ __device__ __forceinline__ void rf_item(const JobDev* __restrict__ jobs, const i
 }
 
 // One item per CTA (sc.n == 0), or persistent CTAs placed by a SweepSched plan.
-template <int Q, int E, int NU>
-__global__ void __launch_bounds__(32 * (NU + 1), rf_min_blocks<Q, E, NU>())
+template <typename T, int Q, int E, int NU>
+__global__ void __launch_bounds__(32 * (NU + 1), rf_min_blocks<T, Q, E, NU>())
     sweep_rf_kernel(const JobDev* __restrict__ jobs, const int2* __restrict__ work, int nsweeps, const SweepSched sc)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     if (sc.n == 0) {
-        rf_item<Q, E, NU>(jobs, work[blockIdx.x], nsweeps, smem);
+        rf_item<T, Q, E, NU>(jobs, work[blockIdx.x], nsweeps, smem);
         return;
     }
     __shared__ int s_item;
@@ -272,7 +334,7 @@ __global__ void __launch_bounds__(32 * (NU + 1), rf_min_blocks<Q, E, NU>())
     __syncthreads();
     for (;;) {
         const int item = s_item;
-        if (item >= 0) rf_item<Q, E, NU>(jobs, work[item], nsweeps, smem);
+        if (item >= 0) rf_item<T, Q, E, NU>(jobs, work[item], nsweeps, smem);
         __syncthreads();
         if (threadIdx.x == 0) s_item = sched_claim_next(sc, waited);
         __syncthreads();
@@ -280,11 +342,11 @@ __global__ void __launch_bounds__(32 * (NU + 1), rf_min_blocks<Q, E, NU>())
     }
 }
 
-template <int Q, int E, int NU>
+template <typename T, int Q, int E, int NU>
 cudaError_t launch_rf(const JobDev* jobs_dev, const int2* work, int nwork, int nsweeps, size_t smem,
                       const SweepSched* sched, cudaStream_t st)
 {
-    auto k = sweep_rf_kernel<Q, E, NU>;
+    auto k = sweep_rf_kernel<T, Q, E, NU>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     SweepSched sc{};
@@ -305,15 +367,15 @@ cudaError_t launch_rf(const JobDev* jobs_dev, const int2* work, int nwork, int n
     return cudaGetLastError();
 }
 
-// dispatch over Q for one (E, NU) configuration
-template <int E, int NU, int QMAX>
+// dispatch over Q for one (field type, E, NU) configuration
+template <typename T, int E, int NU, int QMAX>
 cudaError_t launch_rf_q(int q, const JobDev* jobs_dev, const int2* work, int nwork, int nsweeps, size_t smem,
                         const SweepSched* sched, cudaStream_t st)
 {
     switch (q) {
 #define PLR_RF_Q(Qv) \
     case Qv:         \
-        if constexpr (Qv <= QMAX) return launch_rf<Qv, E, NU>(jobs_dev, work, nwork, nsweeps, smem, sched, st); \
+        if constexpr (Qv <= QMAX) return launch_rf<T, Qv, E, NU>(jobs_dev, work, nwork, nsweeps, smem, sched, st); \
         break;
         PLR_RF_Q(2) PLR_RF_Q(3) PLR_RF_Q(4) PLR_RF_Q(5) PLR_RF_Q(6) PLR_RF_Q(7) PLR_RF_Q(8) PLR_RF_Q(9)
         PLR_RF_Q(10) PLR_RF_Q(11) PLR_RF_Q(12) PLR_RF_Q(13) PLR_RF_Q(14) PLR_RF_Q(15) PLR_RF_Q(16)
@@ -323,13 +385,14 @@ cudaError_t launch_rf_q(int q, const JobDev* jobs_dev, const int2* work, int nwo
     return cudaErrorNotSupported;
 }
 
-// smem bytes for one (E, NU) configuration (depends on q through the published values)
-template <int E, int NU>
+// smem bytes for one (field type, E, NU) configuration (depends on q through
+// the published values)
+template <typename T, int E, int NU>
 size_t rf_smem_q(int q, int L, int Lpad)
 {
     switch (q) {
 #define PLR_RF_S(Qv) \
-    case Qv: return RfSmem<NU, E, Qv>::bytes(L, Lpad);
+    case Qv: return RfSmem<T, NU, E, Qv>::bytes(L, Lpad);
         PLR_RF_S(2) PLR_RF_S(3) PLR_RF_S(4) PLR_RF_S(5) PLR_RF_S(6) PLR_RF_S(7) PLR_RF_S(8) PLR_RF_S(9)
         PLR_RF_S(10) PLR_RF_S(11) PLR_RF_S(12) PLR_RF_S(13) PLR_RF_S(14) PLR_RF_S(15) PLR_RF_S(16)
 #undef PLR_RF_S

@@ -1,5 +1,6 @@
-// Dispatch of the register-resident FP32 sweep over its configurations
-// (sweep_rf.cuh; one translation unit per configuration).
+// Dispatch of the register-resident sweeps over their configurations
+// (sweep_rf.cuh; one translation unit per configuration): FP32 fields and
+// FX64 fields (64-bit integers, two registers per value).
 #include "potts_internal.h"
 
 namespace plr {
@@ -8,7 +9,53 @@ namespace {
 // capacity of each register configuration: largest L (E x 32 x update warps) and q
 constexpr int kRfMaxL[9] = {0, 224, 448, 1120, 2400, 4320, 7680, 12480, 16800};
 constexpr int kRfMaxQ[9] = {0, 16, 16, 16, 8, 8, 5, 3, 2};
+// FX64 configurations 1..6: (E, NU) = (1, 7), (2, 7), (4, 8), (5, 7), (5, 15), (9, 15)
+constexpr int kRfxMaxL[7] = {0, 224, 448, 1024, 1120, 2400, 4320};
+constexpr int kRfxMaxQ[7] = {0, 16, 16, 8, 8, 5, 3};
 }  // namespace
+
+bool rfx_fits(int cfg, int L, int q) { return cfg >= 1 && cfg <= 6 && L <= kRfxMaxL[cfg] && q <= kRfxMaxQ[cfg]; }
+
+int rfx_config(int L, int q)
+{
+    // configuration 4 (5 sites x 7 warps) wherever it holds the chain: timed
+    // on GB300 the fastest, or within 2% of it, from L = 128 to 1024 (q <= 8);
+    // else the fewest sites per thread that hold it
+    if (rfx_fits(4, L, q)) return 4;
+    for (int cfg = 1; cfg <= 6; ++cfg)
+        if (rfx_fits(cfg, L, q)) return cfg;
+    return 0;
+}
+
+int rfx_threads(int cfg) { return cfg == 3 ? 288 : (cfg >= 5 ? 512 : 256); }
+
+size_t rfx_smem_bytes(int cfg, int q, int L, int Lpad)
+{
+    switch (cfg) {
+    case 1: return sweep_rfx_smem_a(q, L, Lpad);
+    case 2: return sweep_rfx_smem_b(q, L, Lpad);
+    case 3: return sweep_rfx_smem_c(q, L, Lpad);
+    case 4: return sweep_rfx_smem_d(q, L, Lpad);
+    case 5: return sweep_rfx_smem_e(q, L, Lpad);
+    case 6: return sweep_rfx_smem_f(q, L, Lpad);
+    default: return 0;
+    }
+}
+
+cudaError_t launch_sweep_rfx(int cfg, int q, const JobDev* jobs_dev, const int2* work, int nwork, int nsweeps,
+                             size_t smem, const SweepSched* sched, cudaStream_t st)
+{
+    if (nwork <= 0 || nsweeps <= 0) return cudaSuccess;
+    switch (cfg) {
+    case 1: return launch_sweep_rfx_a(q, jobs_dev, work, nwork, nsweeps, smem, sched, st);
+    case 2: return launch_sweep_rfx_b(q, jobs_dev, work, nwork, nsweeps, smem, sched, st);
+    case 3: return launch_sweep_rfx_c(q, jobs_dev, work, nwork, nsweeps, smem, sched, st);
+    case 4: return launch_sweep_rfx_d(q, jobs_dev, work, nwork, nsweeps, smem, sched, st);
+    case 5: return launch_sweep_rfx_e(q, jobs_dev, work, nwork, nsweeps, smem, sched, st);
+    case 6: return launch_sweep_rfx_f(q, jobs_dev, work, nwork, nsweeps, smem, sched, st);
+    default: return cudaErrorNotSupported;
+    }
+}
 
 bool rf_fits(int cfg, int L, int q) { return cfg >= 1 && cfg <= 8 && L <= kRfMaxL[cfg] && q <= kRfMaxQ[cfg]; }
 

@@ -7,9 +7,9 @@ namespace plr {
 cudaError_t launch_sweep_rf_e(int q, const JobDev* jobs_dev, const int2* work, int nwork, int nsweeps,
                                size_t smem, const SweepSched* sched, cudaStream_t st)
 {
-    return rf::launch_rf_q<9, 15, 8>(q, jobs_dev, work, nwork, nsweeps, smem, sched, st);
+    return rf::launch_rf_q<float, 9, 15, 8>(q, jobs_dev, work, nwork, nsweeps, smem, sched, st);
 }
 
-size_t sweep_rf_smem_e(int q, int L, int Lpad) { return rf::rf_smem_q<9, 15>(q, L, Lpad); }
+size_t sweep_rf_smem_e(int q, int L, int Lpad) { return rf::rf_smem_q<float, 9, 15>(q, L, Lpad); }
 
 }  // namespace plr

@@ -1,0 +1,15 @@
+// Register-resident FX64 sweep: E = 5 sites per update thread, 15 update warps
+// + 1 decision warp per CTA, q <= 5 (chains up to L = 2400).
+#include "sweep_rf.cuh"
+
+namespace plr {
+
+cudaError_t launch_sweep_rfx_e(int q, const JobDev* jobs_dev, const int2* work, int nwork, int nsweeps,
+                                 size_t smem, const SweepSched* sched, cudaStream_t st)
+{
+    return rf::launch_rf_q<long long, 5, 15, 5>(q, jobs_dev, work, nwork, nsweeps, smem, sched, st);
+}
+
+size_t sweep_rfx_smem_e(int q, int L, int Lpad) { return rf::rf_smem_q<long long, 5, 15>(q, L, Lpad); }
+
+}  // namespace plr

@@ -1,7 +1,8 @@
 """Autotuner of the sweep kernel's shape: for a job shape (L, q, precision) it
 times every sweep variant that can hold it -- fields in shared memory, in
-global memory, shared by a cluster of CTAs, and each register configuration (E sites per update thread x
-update warps) -- on this GPU and keeps the fastest.
+global memory, shared by a cluster of CTAs (FP32), and each register
+configuration (E sites per update thread x update warps; FP32 and FX64) --
+on this GPU and keeps the fastest.
 
 All variants give bit-identical results, so the choice affects speed only.
 Each candidate sweeps a probe job of the same shape (its own seed, the job's
@@ -22,11 +23,14 @@ _cache = {}
 
 
 def candidates(L, q, precision):
-    """Variant names that can hold a job of this shape."""
-    if precision in ("fp64", "fx64"):
+    """Variant names that might hold a job of this shape (the library refuses
+    those that do not; the tuner skips them)."""
+    regs = [v for v in SWEEP_VARIANTS if v.startswith("registers") and v != "registers"]
+    if precision == "fp64":
         return ["memory", "global"]
-    return ["memory", "global", "cluster"] + [v for v in SWEEP_VARIANTS
-                                               if v.startswith("registers") and v != "registers"]
+    if precision == "fx64":
+        return ["memory", "global"] + regs[:6]  # FX64 register configurations 1..6
+    return ["memory", "global", "cluster"] + regs
 
 
 def _time_variant(L, q, sigma, temps, variant, precision, sweeps, warm, torch):

@@ -222,9 +222,43 @@ def test_fx64_full_size_chains_in_bench_configuration(plr):
         j.close()
 
 
-@pytest.mark.parametrize("variant", ["registers", "cluster", "direct", "registers3"])
-def test_fx64_rejects_fp32_and_direct_variants(plr, variant):
+@pytest.mark.parametrize("L,q,variant", [(64, 3, "direct"), (64, 3, "registers7"), (4096, 8, "registers"),
+                                         (1200, 6, "registers"), (500, 9, "registers3")])
+def test_fx64_rejects_unsupported_variants(plr, L, q, variant):
+    """No direct sweep in FX64 mode, no FX64 register configuration 7 or 8,
+    and none that does not hold the chain."""
     from paper_1308_5426_gb300 import _lib
     with pytest.raises(_lib.PottsError) as ei:
-        plr.Job(64, 3, 0.5, _temps(64, 0.5, 2), 1, precision="fx64", sweep_variant=variant)
+        plr.Job(L, q, 0.5, _temps(L, 0.5, 2), 1, precision="fx64", sweep_variant=variant)
     assert ei.value.code == _lib.EINVAL
+
+
+@pytest.mark.parametrize("L,q,sigma,R,cfg", [
+    (200, 16, 0.6, 5, 1), (33, 5, 0.4, 3, 1), (448, 9, 0.3, 4, 2), (300, 2, 0.8, 6, 2),
+    (1024, 5, 0.4, 12, 3), (1000, 8, 0.2, 5, 3), (1120, 7, 0.5, 4, 4), (999, 3, 0.9, 5, 4),
+    (2400, 5, 0.4, 3, 5), (1500, 2, 0.3, 4, 5), (4320, 3, 0.5, 2, 6), (3001, 2, 0.7, 3, 6),
+])
+def test_fx64_register_configurations_equal_the_memory_kernel(plr, L, q, sigma, R, cfg):
+    """Every FX64 register configuration (64-bit integer fields in registers,
+    a decision warp taking the FP64 rule) against the shared/global-memory
+    FX64 kernel: identical spins, fields, energies (the exact 128-bit sum) and
+    counters after sweeps, exchanges and multi-sweep launches."""
+    temps = _temps(L, sigma, R)
+    a = plr.Job(L, q, sigma, temps, 31, precision="fx64", sweep_variant="memory")
+    b = plr.Job(L, q, sigma, temps, 31, precision="fx64", sweep_variant="registers%d" % cfg)
+    assert b.sweep_info()["kernel"] == "registers" and b.sweep_info()["register_config"] == cfg
+    for _ in range(8):
+        for j in (a, b):
+            j.sweep(1)
+            j.exchange()
+    for j in (a, b):
+        j.sweep(3)
+    np.testing.assert_array_equal(a.spins(), b.spins())
+    np.testing.assert_array_equal(a.fields(), b.fields())
+    np.testing.assert_array_equal(a.running_energy(), b.running_energy())
+    sa, sb = a.stats(), b.stats()
+    np.testing.assert_array_equal(sa["acc_flip"], sb["acc_flip"])
+    np.testing.assert_array_equal(sa["acc_swap"], sb["acc_swap"])
+    assert sa["near_metro"] == sb["near_metro"]
+    a.close()
+    b.close()

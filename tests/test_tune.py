@@ -22,6 +22,7 @@ def test_candidates():
     assert candidates(1000, 5, "fp64") == ["memory", "global"]
     c = candidates(1000, 5, "fp32")
     assert c[:3] == ["memory", "global", "cluster"] and c[3:] == ["registers%d" % k for k in range(1, 9)]
+    assert candidates(1000, 5, "fx64") == ["memory", "global"] + ["registers%d" % k for k in range(1, 7)]
 
 
 @pytest.fixture(scope="module")
