@@ -60,10 +60,10 @@ def test_option_checks_without_gpu(lib):
     import ctypes
     from paper_1308_5426_gb300 import _lib
     T = np.ones(4)
-    bad = [dict(precision=3), dict(precision=-1), dict(precision=_lib.FX64, sweep_variant=5),
+    bad = [dict(precision=3), dict(precision=-1),
            dict(precision=_lib.FX64, sweep_variant=4), dict(precision=_lib.FX64, site_order=1),
-           dict(precision=_lib.FP64, sweep_variant=5), dict(precision=_lib.FP32, sweep_variant=4),
-           dict(pair_factor=3), dict(sweep_variant=6)]
+           dict(precision=_lib.FP32, sweep_variant=4), dict(precision=_lib.FP32, site_order=1),
+           dict(pair_factor=3), dict(sweep_variant=6), dict(sweep_variant=25)]
     for kw in bad:
         o = _lib.Opts()
         assert lib.potts_lr_default_opts(ctypes.byref(o)) == _lib.OK
@@ -108,7 +108,7 @@ def test_entry_point_argument_checks_without_gpu(lib):
                                          None)
         assert rc == _lib.EINVAL, bad
     v = ctypes.c_double()
-    assert lib.potts_lr_probe(4, ctypes.byref(v)) == _lib.EINVAL
+    assert lib.potts_lr_probe(5, ctypes.byref(v)) == _lib.EINVAL
     assert lib.potts_lr_probe(0, None) == _lib.EINVAL
     # the near-tie log, the wait limits and the sweep description of a NULL handle
     k = ctypes.c_int()

@@ -164,20 +164,29 @@ def test_shared_and_global_field_residency_agree(plr, precision, L, q, sigma, R)
         np.testing.assert_array_equal(jobs[0].running_energy(), j.running_energy())
 
 
-@pytest.mark.parametrize("L,q,sigma,R,rounds", [
-    (2048, 5, 0.4, 3, 12),    # asked for explicitly: two CTAs, 32 blocks each
-    (10000, 7, 0.5, 3, 6),    # automatic, two CTAs, ragged last block
-    (16384, 12, 0.6, 2, 4),   # four CTAs
-    (24000, 16, 0.3, 2, 2),   # eight CTAs
+@pytest.mark.parametrize("precision,L,q,sigma,R,rounds", [
+    ("fp32", 2048, 5, 0.4, 3, 12),    # asked for explicitly: two CTAs, 32 blocks each
+    ("fp32", 10000, 7, 0.5, 3, 6),    # automatic, two CTAs, ragged last block
+    ("fp32", 16384, 12, 0.6, 2, 4),   # four CTAs
+    ("fp32", 24000, 16, 0.3, 2, 2),   # eight CTAs
+    ("fp64", 2048, 5, 0.4, 3, 10),    # FP64 fields: asked for, two CTAs
+    ("fp64", 4096, 8, 0.2, 3, 4),     # the precision shape: two CTAs
+    ("fp64", 10000, 7, 0.5, 2, 3),    # four CTAs, ragged last block
+    ("fp64", 16384, 8, 0.3, 2, 2),    # eight CTAs
+    ("fx64", 4096, 8, 0.2, 3, 4),     # FX64 fields: two CTAs
+    ("fx64", 9000, 11, 0.6, 2, 3),    # eight CTAs, ragged
+    ("fx64", 16384, 5, 0.4, 2, 2),    # four CTAs
 ])
-def test_cluster_sweep_equals_global_sweep(plr, L, q, sigma, R, rounds):
+def test_cluster_sweep_equals_global_sweep(plr, precision, L, q, sigma, R, rounds):
     """A slot's fields spread over the shared memory of a CTA cluster run the
     same arithmetic as the single-CTA sweep with the fields in global memory:
     spins, fields, running energies and counters agree bit for bit after
-    sweeps, exchanges and tensor-core rebuilds."""
+    sweeps, exchanges and (FP32) tensor-core rebuilds -- in FP32, FP64 (the
+    energy summed in the single-CTA kernel's order) and FX64 (exact)."""
     temps = workloads.geometric_ratios(R, 0.05, 1.0) * oracle.jtot(L, sigma)
-    a = plr.Job(L, q, sigma, temps, 23, precision="fp32", recompute_every=3, sweep_variant="global")
-    b = plr.Job(L, q, sigma, temps, 23, precision="fp32", recompute_every=3, sweep_variant="cluster")
+    a = plr.Job(L, q, sigma, temps, 23, precision=precision, recompute_every=3, sweep_variant="global")
+    b = plr.Job(L, q, sigma, temps, 23, precision=precision, recompute_every=3, sweep_variant="cluster")
+    assert b.sweep_info()["kernel"] == "cluster"
     for _ in range(rounds):
         for j in (a, b):
             j.sweep(1)
@@ -192,9 +201,10 @@ def test_cluster_sweep_equals_global_sweep(plr, L, q, sigma, R, rounds):
     b.close()
 
 
-def test_cluster_sweep_rejects_fp64_and_oversize(plr):
+@pytest.mark.parametrize("precision,L,q", [("fp32", 65536, 16), ("fp64", 32768, 16), ("fx64", 65536, 4)])
+def test_cluster_sweep_rejects_oversize(plr, precision, L, q):
+    """Fields beyond eight CTAs' shared memory (4 MB of FP32, 4 MB and 2 MB of
+    8-byte words per slot) are refused."""
     temps = np.linspace(1.0, 2.0, 2)
     with pytest.raises(plr.PottsError):
-        plr.Job(1024, 5, 0.5, temps, 1, precision="fp64", sweep_variant="cluster")
-    with pytest.raises(plr.PottsError):  # 4 MB of fields per slot: more than eight CTAs hold
-        plr.Job(65536, 16, 0.5, temps, 1, precision="fp32", sweep_variant="cluster")
+        plr.Job(L, q, 0.5, temps, 1, precision=precision, sweep_variant="cluster")
