@@ -224,6 +224,10 @@ KERNEL_NAMES = {"memory": "sweep_kernel", "registers": "sweep_rf_kernel", "clust
                 "direct": "sweep_direct_kernel"}
 
 
+FIELD_TYPE = {"fp64": "double", "fp32": "float", "fx64": "long long"}
+FIELD_NAME = {"fp64": "FP64", "fp32": "FP32", "fx64": "FX64"}
+
+
 def kernel_label(info, prec):
     """Name of the sweep kernel a job ran, from the library's own report
     (potts_lr_sweep_info), with where its fields and table live."""
@@ -231,22 +235,26 @@ def kernel_label(info, prec):
     if k == "memory":
         where = "fields %s, table %s" % ("in shared memory" if info["fields_in_smem"] else "in global memory",
                                          "in shared memory" if info["table_in_smem"] else "in global memory")
-        return "sweep_kernel<%s> (%s)" % ({"fp64": "double", "fp32": "float", "fx64": "long long"}[prec], where)
+        return "sweep_kernel<%s> (%s)" % (FIELD_TYPE[prec], where)
     if k == "registers":
-        return "sweep_rf_kernel (FP32 fields in registers, configuration %d)" % info["register_config"]
+        return "sweep_rf_kernel<%s> (%s fields in registers, configuration %d)" % (
+            FIELD_TYPE[prec], FIELD_NAME[prec], info["register_config"])
     if k == "cluster":
-        return "sweep_cluster_kernel (FP32 fields shared by a %d-CTA cluster)" % info["cluster"]
+        return "sweep_cluster_kernel<%s> (%s fields shared by a %d-CTA cluster)" % (
+            FIELD_TYPE[prec], FIELD_NAME[prec], info["cluster"])
     return "sweep_direct_kernel (no fields)"
 
 
 def sweep_roofline(plr, res, specs, sm_max_mhz, nsms):
     """Roofline entry of the sweep kernel of a timed_device run.  Work per
     attempt: A * 2L field additions (FP64 and FP32: against the add pipe's
-    unit-count peak and its measured probe) or A * L element updates of 40
-    bytes (FX64: against the measured shared-memory probe where the fields
-    sit in shared memory, the measured L2 probe where they sit in global
-    memory).  A = the measured acceptance; achieved = the work of one launch
-    over the average sweep launch time (CUDA events on the launching stream)."""
+    unit-count peak and its measured probe); FX64: A * L element updates of
+    40 bytes against the measured shared-memory probe where the fields sit in
+    shared memory (one CTA or a cluster), the measured L2 probe where they
+    sit in global memory, and for fields in registers A * 2L 64-bit integer
+    adds against the measured integer-add probe.  A = the measured
+    acceptance; achieved = the work of one launch over the average sweep
+    launch time (CUDA events on the launching stream)."""
     info = res["info"]
     prec = specs[0].precision
     A = res["acceptance"]
@@ -254,8 +262,16 @@ def sweep_roofline(plr, res, specs, sm_max_mhz, nsms):
     upd_launch = sum(s.L * s.R * s.L for s in specs) * A  # element updates per launch (per state row pair)
     sweep_s = float(np.mean(res["sweep_ms"])) / 1e3
     kernel = kernel_label(info, prec)
-    if prec == "fx64":
-        where = "smem" if info["fields_in_smem"] else "l2"
+    if prec == "fx64" and info["kernel"] == "registers":
+        peak = plr.probe("i64_add")
+        achieved = 2.0 * upd_launch / sweep_s
+        roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tadd/s",
+                "frac": achieved / peak, "traffic": None, "kernel": kernel,
+                "work": "A*2L 64-bit integer adds per attempt (two field words per element), A=%.4f measured; "
+                        "%d attempts per launch" % (A, att_launch),
+                "peak_source": "measured 64-bit integer add probe (potts_lr_probe)", "sweep_ms_avg": sweep_s * 1e3}
+    elif prec == "fx64":
+        where = "smem" if (info["fields_in_smem"] or info["kernel"] == "cluster") else "l2"
         peak = plr.probe(where)
         achieved = upd_launch * FX64_BYTES_PER_UPDATE / sweep_s
         roof = {"bound": where, "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "GB/s",

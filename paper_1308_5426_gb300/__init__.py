@@ -33,11 +33,13 @@ def jtot(L: int, sigma: float) -> float:
 
 
 def probe(what: str) -> float:
-    """Measured throughput of this GPU: "fp64_add", "fp32_add" (adds/s),
-    "smem" or "l2" (bytes/s loaded + stored) -- roofline denominators."""
+    """Measured throughput of this GPU: "fp64_add", "fp32_add", "i64_add"
+    (adds/s), "smem" or "l2" (bytes/s loaded + stored) -- roofline
+    denominators."""
     lib = _lib.load()
     v = ctypes.c_double()
-    _lib.check(lib.potts_lr_probe({"fp64_add": 0, "fp32_add": 1, "smem": 2, "l2": 3}[what], ctypes.byref(v)))
+    _lib.check(lib.potts_lr_probe({"fp64_add": 0, "fp32_add": 1, "smem": 2, "l2": 3, "i64_add": 4}[what],
+                                  ctypes.byref(v)))
     return v.value
 
 

@@ -55,6 +55,27 @@ __global__ void __launch_bounds__(kProbeThreads) smem_probe(float* out, int iter
     if (acc == 123456.0f) out[0] = acc;
 }
 
+// 64-bit integer adds (the FX64 field update): 8 independent chains per
+// thread, two adds each per iteration
+__global__ void __launch_bounds__(kProbeThreads) i64_probe(long long* out, long long seed)
+{
+    long long a[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) a[c] = seed * (long long)(threadIdx.x + c);
+    const long long d0 = seed * 3, d1 = seed * -5;
+    for (int it = 0; it < kProbeIters; ++it) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            a[c] += d0;
+            a[c] += d1;
+        }
+    }
+    long long s = 0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) s += a[c];
+    if (s == 123456789ll) out[0] = s;  // keeps the chains alive
+}
+
 // L2 bandwidth: each CTA reads and rewrites its own slice of a buffer that
 // stays resident in L2 (far below its 129 MB), 16 bytes per thread access
 __global__ void __launch_bounds__(kProbeThreads) l2_probe(float4* buf, size_t per_cta, int iters)
@@ -79,7 +100,7 @@ using namespace plr;
 
 extern "C" int potts_lr_probe(int what, double* value)
 {
-    if (!value || what < 0 || what > 3) return POTTS_LR_EINVAL;
+    if (!value || what < 0 || what > 4) return POTTS_LR_EINVAL;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return POTTS_LR_ECUDA;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return POTTS_LR_ECUDA;
@@ -113,13 +134,14 @@ extern "C" int potts_lr_probe(int what, double* value)
         if (what == 0) add_probe<double><<<blocks, kProbeThreads, 0, st>>>((double*)out, 1.0);
         else if (what == 1) add_probe<float><<<blocks, kProbeThreads, 0, st>>>((float*)out, 1.0f);
         else if (what == 2) smem_probe<<<blocks, kProbeThreads, 0, st>>>((float*)out, smem_iters);
+        else if (what == 4) i64_probe<<<blocks, kProbeThreads, 0, st>>>((long long*)out, 1ll);
         else l2_probe<<<blocks, kProbeThreads, 0, st>>>((float4*)out, l2_per_cta, l2_iters);
         ok = ok && cudaGetLastError() == cudaSuccess && cudaEventRecord(e1, st) == cudaSuccess;
     }
     ok = cudaStreamSynchronize(st) == cudaSuccess && ok;
     float ms = 0.0f;
     ok = ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms > 0.0f;
-    if (what <= 1) work = (double)blocks * kProbeThreads * kProbeIters * 16.0;  // adds
+    if (what <= 1 || what == 4) work = (double)blocks * kProbeThreads * kProbeIters * 16.0;  // adds
     else if (what == 2) work = (double)blocks * kProbeThreads * smem_iters * 4.0 * 2.0 * 4.0;  // bytes (load + store)
     else work = (double)blocks * (double)l2_per_cta * l2_iters * 16.0 * 2.0;                 // bytes (load + store)
     if (ok) *value = work / (ms * 1e-3);  // left untouched on any failure

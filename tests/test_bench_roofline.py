@@ -22,7 +22,7 @@ class FakeLib:
 
     def probe(self, what):
         self.asked.append(what)
-        return {"smem": 4.0e13, "l2": 2.0e13, "fp64_add": 5.0e11, "fp32_add": 3.9e13}[what]
+        return {"smem": 4.0e13, "l2": 2.0e13, "fp64_add": 5.0e11, "fp32_add": 3.9e13, "i64_add": 1.0e13}[what]
 
 
 def _info(kernel="memory", hs=True, js=True, rf=0, cl=0):
@@ -79,3 +79,25 @@ def test_alu_roofline(prec, lanes):
     assert r["frac"] == pytest.approx(adds / 0.6e-3 / peak)
     assert "frac_of_occupied_sms" not in r  # 512 slots fill the SMs
     assert ("registers" in r["kernel"]) == (prec == "fp32")
+
+
+def test_fx64_register_and_cluster_kernels():
+    """FX64 fields in registers: 64-bit integer adds against the integer-add
+    probe; FX64 fields shared by a cluster: shared-memory bytes."""
+    specs = workloads.chains_jobs()
+    for s in specs:
+        s.precision = "fx64"
+    lib = FakeLib()
+    res = {"sweep_ms": [0.4], "acceptance": 0.2, "info": _info("registers", hs=False, js=False, rf=4)}
+    r = bench.sweep_roofline(lib, res, specs, 2070.0, 152)
+    adds = 8 * 1024 * 64 * 0.2 * 2 * 1024
+    assert lib.asked == ["i64_add"] and r["bound"] == "alu"
+    assert r["frac"] == pytest.approx(adds / 0.4e-3 / 1.0e13)
+    assert "FX64 fields in registers" in r["kernel"]
+    s = workloads.precision_job("fx64")
+    lib = FakeLib()
+    res = {"sweep_ms": [2.0], "acceptance": 0.14, "info": _info("cluster", hs=False, js=False, cl=2)}
+    r = bench.sweep_roofline(lib, res, [s], 2070.0, 152)
+    assert lib.asked == ["smem"] and r["bound"] == "smem"
+    assert "FX64 fields shared by a 2-CTA cluster" in r["kernel"]
+    assert "frac_of_occupied_sms" not in r
