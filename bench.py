@@ -188,7 +188,7 @@ def peaks():
     return p
 
 
-SWEEP_SOURCES = ["sweep.cu", "sweep_common.cuh", "sweep_sched.cuh", "philox.cuh", "potts_internal.h"]
+SWEEP_SOURCES = ["sweep.cu", "sweep_common.cuh", "near_tie.cuh", "sweep_sched.cuh", "philox.cuh", "potts_internal.h"]
 SWEEP_PROFILE = os.path.join(ROOT, "profiles", "sweep_fp64_chains_L1024_q5.md")
 
 

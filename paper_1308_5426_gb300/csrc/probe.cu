@@ -56,7 +56,8 @@ __global__ void __launch_bounds__(kProbeThreads) smem_probe(float* out, int iter
 }
 
 // 64-bit integer adds (the FX64 field update): 8 independent chains per
-// thread, two adds each per iteration
+// thread, two adds each per iteration, written as PTX adds so that the
+// compiler cannot fold the (associative) integer chains into one multiply
 __global__ void __launch_bounds__(kProbeThreads) i64_probe(long long* out, long long seed)
 {
     long long a[8];
@@ -66,8 +67,8 @@ __global__ void __launch_bounds__(kProbeThreads) i64_probe(long long* out, long 
     for (int it = 0; it < kProbeIters; ++it) {
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-            a[c] += d0;
-            a[c] += d1;
+            asm volatile("add.s64 %0, %0, %1;" : "+l"(a[c]) : "l"(d0));
+            asm volatile("add.s64 %0, %0, %1;" : "+l"(a[c]) : "l"(d1));
         }
     }
     long long s = 0;

@@ -5,8 +5,11 @@
 cases:
   chains_fp64   8 chains L=1024 q=5 R=64, FP64 fields (shared-memory sweep kernel), 4 sweeps
   chains_fp32   the same chains in FP32 (register-resident sweep kernel), 4 sweeps
-  chains_fx64   the same chains with 64-bit fixed-point fields (shared-memory sweep kernel), 4 sweeps
+  chains_fx64   the same chains with 64-bit fixed-point fields (register-resident sweep kernel), 4 sweeps
+  chains_fx64_memory  the same FX64 chains with the fields in shared memory, 4 sweeps
   precision_fp32  L=4096 q=8 R=128, FP32 (register-resident sweep), 3 sweeps
+  precision_fp64  L=4096 q=8 R=128, FP64 fields shared by two-CTA clusters, 3 sweeps
+  precision_fx64  L=4096 q=8 R=128, FX64 fields shared by two-CTA clusters, 3 sweeps
   rebuild_fp32  L=4096 q=8 R=128, FP32: 3 tensor-core field rebuilds + measurements
   long_fp32     one job L=16384 q=5 R=64, FP32, fields in global memory (memory kernel), 3 sweeps
   long_fp32_cluster  the same job with its fields shared by a two-CTA cluster, 3 sweeps
@@ -21,10 +24,14 @@ def main(argv):
     from paper_1308_5426_gb300 import workloads
 
     case = argv[1] if len(argv) > 1 else ""
+    variant = "auto"
     if case in ("chains_fp64", "chains_fp32", "chains_fx64"):
         specs, prec, nsw = workloads.chains_jobs(), case[-4:], 4
-    elif case == "precision_fp32":
-        specs, prec, nsw = [workloads.precision_job("fp32")], "fp32", 3
+    elif case == "chains_fx64_memory":
+        specs, prec, nsw, variant = workloads.chains_jobs(), "fx64", 4, "memory"
+    elif case in ("precision_fp32", "precision_fp64", "precision_fx64"):
+        prec = case[-4:]
+        specs, nsw = [workloads.precision_job(prec)], 3
     elif case in ("long_fp32", "long_fp32_cluster"):
         from paper_1308_5426_gb300.workloads import geometric_ratios
         L, q = 16384, 5
@@ -51,7 +58,7 @@ def main(argv):
         print(__doc__)
         return 2
     jobs = [plr.Job(s.L, s.q, s.sigma, s.ratios * plr.jtot(s.L, s.sigma), s.seed, precision=prec,
-                    recompute_every=0) for s in specs]
+                    recompute_every=0, sweep_variant=variant) for s in specs]
     b = plr.Batch(jobs)
     for _ in range(nsw):
         b.sweep(1)
