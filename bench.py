@@ -505,6 +505,38 @@ def per_job_rates(plr, torch, dev, reqs, precision, min_seconds=0.25, max_sweeps
     return total_att, total_s, rows
 
 
+def rebuild_shares(plr, torch, dev, reqs, min_L=4096):
+    """Share of the FP32 step time spent in the tensor-core rebuilds and
+    energy re-anchors, per served shape with L >= min_L: the same job alone,
+    20 sweeps + exchanges timed (CUDA events) after its schedule settled,
+    with the adaptive rebuild (K = 100) and with none (K = 0)."""
+    out = []
+    for L, q, sigma in sorted({(r.L, r.q, r.sigma) for r in reqs if r.L >= min_L}):
+        ms = {}
+        for K in (0, 100):
+            st = torch.cuda.Stream(device=dev)
+            temps = [r for r in reqs if (r.L, r.q, r.sigma) == (L, q, sigma)][0].temps
+            j = plr.Job(L, q, sigma, temps, 5, precision="fp32", recompute_every=K, stream=st.cuda_stream)
+            for _ in range(60 if L >= 16384 else 150):
+                j.sweep(1)
+                j.exchange()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for _ in range(20):
+                j.sweep(1)
+                j.exchange()
+            e1.record(st)
+            e1.synchronize()
+            ms[K] = e0.elapsed_time(e1) / 20
+            if K:
+                info = j.rebuild_info()
+            j.close()
+        out.append({"L": L, "q": q, "sigma": round(sigma, 4), "ms_per_step_no_rebuild": ms[0],
+                    "ms_per_step_adaptive": ms[100], "rebuild_share": 1.0 - ms[0] / ms[100],
+                    "settled_interval": info["interval"], "last_drift": info["last_drift"]})
+    return out
+
+
 def serving_run(plr, torch, dev, njobs, sweeps, budget_bytes):
     """The serving trace (Poisson arrivals at 50 jobs/s; q in {3,5,8}, sigma in
     U[0.1,1], L in {512..16384}, R=64, FP32 fields, K=100) cut to its first
@@ -524,12 +556,17 @@ def serving_run(plr, torch, dev, njobs, sweeps, budget_bytes):
         reqs.append(Request(rid=i, L=sp.L, q=sp.q, sigma=sp.sigma, temps=temps, seed=sp.seed, sweeps=sweeps,
                             recompute_every=100, arrival=sp.arrival))
 
+    rebuilds = {}
+
     class Engine(GpuEngine):
+        """The library's engine, recording each finished job's field error and
+        rebuild schedule."""
         max_err = 0.0
         peak_used = 0
 
         def destroy(self, job):
             Engine.max_err = max(Engine.max_err, job.fields_error())
+            rebuilds.setdefault((job.L, job.q), []).append(job.rebuild_info())
             job.close()
 
     st = torch.cuda.Stream(device=dev)
@@ -549,6 +586,7 @@ def serving_run(plr, torch, dev, njobs, sweeps, budget_bytes):
     wall = time.perf_counter() - t0
     summ = srv.summary(wall_seconds=wall)
     waited = [r.admitted - r.arrival for r in srv.results.values() if r.admitted is not None]
+    shares = rebuild_shares(plr, torch, dev, reqs)
     att64, t64, rows64 = per_job_rates(plr, torch, dev, reqs, "fp64")
     attx, tx, rowsx = per_job_rates(plr, torch, dev, reqs, "fx64")
     served = summ.get("attempts_per_s") or 0.0
@@ -562,6 +600,10 @@ def serving_run(plr, torch, dev, njobs, sweeps, budget_bytes):
             "attempts_per_busy_s": summ.get("attempts_per_busy_s"),
             "p50_latency_s": summ.get("p50_s"), "p99_latency_s": summ.get("p99_s"), "done": summ["done"],
             "max_field_error_rel_jtot": Engine.max_err,
+            "rebuild_by_shape": [{"L": L, "q": q, "settled_interval": [r["interval"] for r in v],
+                                  "rebuilds_per_job": [r["rebuilds"] for r in v]}
+                                 for (L, q), v in sorted(rebuilds.items())],
+            "rebuild_share_by_shape": shares,
             "fp64_per_job_attempts_per_s": att64 / t64,
             "fp64_per_job": "every request's shape as a plain FP64 job alone on the GPU, rate sampled over >= 0.25 s "
                             "after one warm-up sweep; the full %d sweeps of all %d requests would take %.0f s at "

@@ -233,6 +233,21 @@ int potts_lr_near_log(potts_lr_t* h, int32_t* events, int cap, int* n);
  * smallest plan_ns of its jobs).  Synchronises.  EINVAL for a NULL handle. */
 int potts_lr_set_wait_limits(potts_lr_t* h, uint64_t rebuild_ns, uint64_t plan_ns);
 
+/* FP32 mode: how many BF16 parts of J* the tensor-core rebuild multiplies
+ * (the paper has no counterpart): 3 (hi + mid + lo, the default,
+ * representation error about 2^-25 of each coupling) or 2 (hi + mid, about
+ * 2^-17, two thirds of the tensor-core work).  Applies to the handle's own
+ * rebuilds and to batches created afterwards.  EINVAL for a NULL handle, a
+ * job not in FP32 mode, or parts other than 2 and 3.  Synchronises. */
+int potts_lr_set_rebuild_split(potts_lr_t* h, int parts);
+
+/* FP32 mode's rebuild schedule (any argument may be NULL): *interval = the
+ * current interval between rebuilds in sweeps (it halves or doubles with the
+ * measured drift, up to recompute_every), *rebuilds = automatic rebuilds done
+ * since create (0 in the other modes), *last_drift = max |h_fp32 -
+ * h_rebuilt| / Jtot measured by the last of them.  Synchronises. */
+int potts_lr_rebuild_info(potts_lr_t* h, int32_t* interval, uint32_t* rebuilds, double* last_drift);
+
 /* Sweep and exchange counts since create. */
 int potts_lr_counters(potts_lr_t* h, uint32_t* nsweep, uint32_t* nexch);
 

@@ -190,6 +190,17 @@ class Job:
                 "register_config": int(v[3]), "cluster": int(v[4]), "threads": int(v[5]),
                 "smem_bytes": int(v[6])}
 
+    def set_rebuild_split(self, parts):
+        """FP32: BF16 parts of J* in the tensor-core rebuild, 3 (default) or 2."""
+        _lib.check(self._lib.potts_lr_set_rebuild_split(self._h, int(parts)))
+
+    def rebuild_info(self):
+        """FP32 rebuild schedule: current interval (sweeps), automatic rebuilds
+        done, drift of the last one (/ Jtot)."""
+        k, n, d = ctypes.c_int32(), ctypes.c_uint32(), ctypes.c_double()
+        _lib.check(self._lib.potts_lr_rebuild_info(self._h, ctypes.byref(k), ctypes.byref(n), ctypes.byref(d)))
+        return {"interval": k.value, "rebuilds": n.value, "last_drift": d.value}
+
     def set_wait_limits(self, rebuild_ns=4_000_000_000, plan_ns=50_000):
         """Bounds of the device waits (potts_lr_set_wait_limits); small values
         make them expire (the tests of the failure paths)."""

@@ -28,7 +28,7 @@ EXPORTS = [
     "potts_lr_batch_sweep", "potts_lr_batch_exchange", "potts_lr_batch_measure",
     "potts_lr_batch_measure_device", "potts_lr_batch_state_size", "potts_lr_batch_get_state",
     "potts_lr_batch_set_state", "potts_lr_probe", "potts_lr_measure_static", "potts_lr_near_log",
-    "potts_lr_set_wait_limits", "potts_lr_sweep_info",
+    "potts_lr_set_wait_limits", "potts_lr_sweep_info", "potts_lr_set_rebuild_split", "potts_lr_rebuild_info",
 ]
 
 
@@ -89,6 +89,8 @@ def load(path: str = LIB_PATH):
         "potts_lr_near_log": [P, P, I, P],
         "potts_lr_set_wait_limits": [P, U64, U64],
         "potts_lr_sweep_info": [P, P, I],
+        "potts_lr_set_rebuild_split": [P, I],
+        "potts_lr_rebuild_info": [P, P, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)

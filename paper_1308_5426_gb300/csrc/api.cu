@@ -380,7 +380,7 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
     // first FP32 rebuild interval: short for long chains with few states (the
     // drift grows with the field updates per element, ~L/q per sweep); the
     // device doubles it while the measured drift stays small
-    int sched0[2] = {0, 0};
+    int sched0[4] = {0, 0, 0, 0};
     if (h->K > 0) {
         const int k0 = (int)std::max(1.0, std::min((double)h->K, 2500.0 * q / (double)L));
         sched0[0] = k0;
@@ -413,7 +413,7 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
     const size_t r_map = in_block((size_t)R * 4), r_E = in_block((size_t)R * 8);
     const size_t r_spins = in_block((size_t)R * h->W * 4), r_fields = in_block((size_t)R * q * Lp * h->wsize);
     const size_t r_nsw = in_block((size_t)R * 4), r_accf = in_block((size_t)R * 8), r_accs = in_block((size_t)R * 8);
-    const size_t r_near = in_block(16), r_sched = in_block(8), r_drift = in_block(8), r_nex = in_block(4);
+    const size_t r_near = in_block(16), r_sched = in_block(16), r_drift = in_block(16), r_nex = in_block(4);
     const size_t o_state = take(sb);
     h->state_off = o_state;
     h->state_len = sb;
@@ -489,6 +489,7 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
     h->onehot_blocks = tc_onehot_blocks(L, q, R);
     j.status = (int*)(base + o_status);
     j.tc_wait_ns = kTcWaitNs;
+    j.tc_parts = 3;
     j.sched = (int*)(base + o_sched);
     h->dtiles = (int4*)(base + o_tiles);
     h->ntiles = (int)tiles.size();
@@ -583,7 +584,7 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
         if (tc && (e = cudaMemcpyAsync((void*)j.Jhank, hank.data(), hank.size() * 2, cudaMemcpyHostToDevice, st)) !=
                       cudaSuccess)
             break;
-        if ((e = cudaMemcpyAsync(j.sched, sched0, 8, cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
+        if ((e = cudaMemcpyAsync(j.sched, sched0, 16, cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
         if (!tiles.empty() &&
             (e = cudaMemcpyAsync(h->dtiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice, st)) !=
                 cudaSuccess)
@@ -873,6 +874,31 @@ int potts_lr_sweep_info(potts_lr_t* h, int32_t* info, int n)
     const int32_t v[7] = {kind, kind == 0 ? j.h_smem : 0, kind == 0 ? j.j_smem : 0, j.rf, j.cl, threads,
                           (int32_t)h->sweep_smem};
     for (int i = 0; i < n && i < 7; ++i) info[i] = v[i];
+    return POTTS_LR_OK;
+}
+
+int potts_lr_set_rebuild_split(potts_lr_t* h, int parts)
+{
+    if (!h) return fail(POTTS_LR_EINVAL, "handle is NULL");
+    if (h->precision != POTTS_LR_FP32) return fail(POTTS_LR_EINVAL, "the split-BF16 rebuild is FP32 mode's");
+    if (parts != 2 && parts != 3) return fail(POTTS_LR_EINVAL, "parts must be 2 or 3");
+    h->hj.tc_parts = parts;
+    PLR_CUDA(cudaMemcpyAsync(h->dj, &h->hj, sizeof(JobDev), cudaMemcpyHostToDevice, h->stream));
+    PLR_CUDA(cudaStreamSynchronize(h->stream));
+    return POTTS_LR_OK;
+}
+
+int potts_lr_rebuild_info(potts_lr_t* h, int32_t* interval, uint32_t* rebuilds, double* last_drift)
+{
+    if (!h) return fail(POTTS_LR_EINVAL, "handle is NULL");
+    int sched[4] = {0, 0, 0, 0};
+    unsigned long long drift[2] = {0ull, 0ull};
+    PLR_CUDA(cudaMemcpyAsync(sched, h->hj.sched, 16, cudaMemcpyDeviceToHost, h->stream));
+    PLR_CUDA(cudaMemcpyAsync(drift, h->hj.drift_bits, 16, cudaMemcpyDeviceToHost, h->stream));
+    PLR_CUDA(cudaStreamSynchronize(h->stream));
+    if (interval) *interval = sched[0];
+    if (rebuilds) *rebuilds = (uint32_t)sched[2];
+    if (last_drift) std::memcpy(last_drift, &drift[1], 8);
     return POTTS_LR_OK;
 }
 

@@ -241,13 +241,15 @@ __global__ void rebuild_policy_kernel(const JobDev* __restrict__ jobs, const int
     if (i >= njobs) return;
     const JobDev& jb = jobs[idx ? idx[i] : i];
     if (cond && !rebuild_due(jb)) return;
-    const double d = __longlong_as_double((long long)*jb.drift_bits);
+    const double d = __longlong_as_double((long long)jb.drift_bits[0]);
     int k = jb.sched[0];
     if (d > kDriftHigh) k = max(1, k / 2);
     else if (d < kDriftLow) k = min(max(jb.recompute_every, 1), 2 * k);
     jb.sched[0] = k;
     jb.sched[1] = (int)(jb.nsweep[0] + (uint32_t)k);
-    *jb.drift_bits = 0ull;
+    jb.sched[2] += 1;                    // rebuilds done
+    jb.drift_bits[1] = jb.drift_bits[0];  // the drift of the period just closed
+    jb.drift_bits[0] = 0ull;
 }
 
 }  // namespace

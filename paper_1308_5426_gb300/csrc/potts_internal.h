@@ -67,8 +67,11 @@ struct JobDev {
     int NG;                        // 8-row groups of the B operand: q R rounded up to 128, / 8
     int* status;                   // 0 ok; 1 a bounded device wait expired
     unsigned long long tc_wait_ns; // bound of each pipeline wait of the tensor-core rebuild (kTcWaitNs)
-    int* sched;                    // FP32 rebuild schedule: [0] current interval k, [1] sweep of the next rebuild
-    unsigned long long* drift_bits;  // max |h_before - h_rebuilt| / Jtot of the last rebuild (double bits)
+    int* sched;                    // FP32 rebuild schedule: [0] current interval k, [1] sweep of the next rebuild,
+                                   // [2] rebuilds done (policy updates)
+    unsigned long long* drift_bits;  // max |h_before - h_rebuilt| / Jtot (double bits): [0] of the rebuild
+                                     // running now, [1] of the last completed one
+    int tc_parts;                  // BF16 parts of J* the rebuild multiplies: 3 (hi, mid, lo; default) or 2
 };
 
 // FP32 drift control: after each rebuild the measured drift d of the period

@@ -7,7 +7,7 @@
 // tcgen05.mma kind::f16 with BF16 operands and FP32 accumulation in tensor
 // memory.  X is exact in BF16 (0 or 1); C is carried as three BF16 parts
 // hi + mid + lo of the FP64 J* (representation error ~2^-25 J*), each part one
-// MMA per K-step.  One CTA computes a 128 x TN tile of H (TN = 64 or 128) over
+// MMA per K-step (a job may ask for hi + mid only: two MMAs per K-step).  One CTA computes a 128 x TN tile of H (TN = 64 or 128) over
 // all of K in chunks of kChunk = 128 sites.
 //
 // Both operands come from device memory, ready in the MMA's shared-memory
@@ -302,6 +302,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* 
                 const JobDev& jb = jobs[tile.x];
                 if (!tile_live(jb, cond)) continue;
                 const int nchunks = (jb.L + kChunk - 1) / kChunk;
+                const int parts = jb.tc_parts;
                 // the accumulators of the previous tile have been read
                 if (ntile > 0 && !mbar_wait(smem_u32(tempty), (ntile - 1) & 1u, abort, 0, jb.tc_wait_ns)) {
                     failed_job = tile.x;
@@ -324,6 +325,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* 
                         const uint64_t bdesc = make_desc(sb + s * 256, 128, 2048);
 #pragma unroll
                         for (int sp = 0; sp < kSplit; ++sp) {
+                            if (sp >= parts) break;  // two parts: hi + mid only
                             const uint64_t adesc = make_desc(sa + sp * kTileBytes + s * 256, 128, 128);
                             const uint32_t dcol = sp == 0 ? dhi : dsmall;
                             const bool first = s == 0 && (sp == 0 ? t < kAccHi : (t == 0 && sp == 1));

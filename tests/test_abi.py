@@ -117,6 +117,8 @@ def test_entry_point_argument_checks_without_gpu(lib):
     assert lib.potts_lr_set_wait_limits(None, 0, 0) == _lib.EINVAL
     info = np.zeros(7, np.int32)
     assert lib.potts_lr_sweep_info(None, _lib._ptr(info), 7) == _lib.EINVAL
+    assert lib.potts_lr_set_rebuild_split(None, 2) == _lib.EINVAL
+    assert lib.potts_lr_rebuild_info(None, None, None, None) == _lib.EINVAL
 
 
 @pytest.mark.parametrize("L", [2, 3, 64, 1000, 1024, 4096, 16384, 65536])

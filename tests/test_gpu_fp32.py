@@ -44,6 +44,50 @@ def test_tensor_core_rebuild_accuracy(plr, L, q, R, sigma):
     np.testing.assert_allclose(j.running_energy(), E, rtol=1e-12)
 
 
+@pytest.mark.parametrize("L,q,R,sigma", [(4096, 8, 128, 0.2), (16384, 5, 64, 0.4), (1024, 5, 64, 0.4)])
+def test_rebuild_split_two_and_three_parts(plr, L, q, R, sigma):
+    """The split of J* into BF16 parts: three (hi + mid + lo, the default) and
+    two (hi + mid) both rebuild within the 1e-5 Jtot bound; three parts are
+    measured several times more accurate (on GB300: 2e-8..1.1e-7 against
+    2.8e-7..5.9e-7 Jtot) at no measured extra time, which is why they are the
+    default."""
+    temps = workloads.geometric_ratios(R, 0.05, 1.0) * oracle.jtot(L, sigma)
+    err = {}
+    for parts in (3, 2):
+        j = plr.Job(L, q, sigma, temps, 3, precision="fp32", recompute_every=0)
+        j.sweep(3)
+        j.set_rebuild_split(parts)
+        j.fields_recompute()
+        err[parts] = j.fields_error()
+        j.close()
+    print("L=%d q=%d: rebuild error, 3 parts %.3e, 2 parts %.3e Jtot" % (L, q, err[3], err[2]))
+    assert err[3] < 2e-7 and err[2] < 1e-6
+    assert err[3] < err[2]
+
+
+def test_rebuild_schedule_is_reported(plr):
+    """potts_lr_rebuild_info: the adaptive interval, the rebuilds done and the
+    last measured drift of an FP32 job with K = 100."""
+    L, q, sigma, R = 4096, 8, 0.5, 16
+    temps = workloads.geometric_ratios(R, 0.05, 1.0) * oracle.jtot(L, sigma)
+    j = plr.Job(L, q, sigma, temps, 5, precision="fp32", recompute_every=100)
+    assert j.rebuild_info()["rebuilds"] == 0
+    for _ in range(120):
+        j.sweep(1)
+        j.exchange()
+    info = j.rebuild_info()
+    print("L=%d q=%d after 120 sweeps: %s" % (L, q, info))
+    assert info["rebuilds"] >= 2 and 1 <= info["interval"] <= 100
+    assert 0.0 < info["last_drift"] < 1e-5
+    g = plr.Job(L, q, sigma, temps, 5, precision="fp64")
+    g.sweep(2)
+    assert g.rebuild_info() == {"interval": 0, "rebuilds": 0, "last_drift": 0.0}
+    with pytest.raises(plr.PottsError):
+        g.set_rebuild_split(2)
+    j.close()
+    g.close()
+
+
 def test_tensor_core_rebuild_small_matches_oracle_fields(plr):
     """Rebuilt FP32 fields against the oracle's FP64 fields of the same spins."""
     L, q, R, sigma = 96, 4, 3, 0.6
