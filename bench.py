@@ -242,6 +242,9 @@ def kernel_label(info, prec):
     if k == "cluster":
         return "sweep_cluster_kernel<%s> (%s fields shared by a %d-CTA cluster)" % (
             FIELD_TYPE[prec], FIELD_NAME[prec], info["cluster"])
+    if k == "register_cluster":
+        return "sweep_rfc_kernel<%s> (%s fields in the registers of a %d-CTA cluster)" % (
+            FIELD_TYPE[prec], FIELD_NAME[prec], info["cluster"])
     return "sweep_direct_kernel (no fields)"
 
 
@@ -262,7 +265,7 @@ def sweep_roofline(plr, res, specs, sm_max_mhz, nsms):
     upd_launch = sum(s.L * s.R * s.L for s in specs) * A  # element updates per launch (per state row pair)
     sweep_s = float(np.mean(res["sweep_ms"])) / 1e3
     kernel = kernel_label(info, prec)
-    if prec == "fx64" and info["kernel"] == "registers":
+    if prec == "fx64" and info["kernel"] in ("registers", "register_cluster"):
         peak = plr.probe("i64_add")
         achieved = 2.0 * upd_launch / sweep_s
         roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tadd/s",
@@ -293,7 +296,7 @@ def sweep_roofline(plr, res, specs, sm_max_mhz, nsms):
                 "peak_source": "unit counts x max SM clock (2 FP64 / 128 FP32 add lanes per SM per clock, 152 SMs)",
                 "sweep_ms_avg": sweep_s * 1e3}
     nslots = sum(s.R for s in specs)
-    if nslots < nsms and info["kernel"] != "cluster":  # fewer slots than SMs: also against the SMs they occupy
+    if nslots < nsms and info["kernel"] not in ("cluster", "register_cluster"):  # also against the occupied SMs
         roof["frac_of_occupied_sms"] = roof["frac"] * nsms / nslots
         roof["occupied_sms"] = nslots
     if prec == "fp32":

@@ -113,7 +113,12 @@ typedef struct {
                             where the fields fit no registers and fit no single
                             CTA's shared memory, and in FP32 mode also where they
                             take more than 88 KB of it with R x C at most the SM
-                            count); FP32 mode:
+                            count); FP32 and FX64 modes: 6 = the slot's fields in the
+                            registers of a cluster of 2, 4 or 8 CTAs (FP32: q <= 8, L <=
+                            4320 C; FX64: q <= 7, L <= 2400 C; the smallest C that holds
+                            them; EINVAL beyond L = 34560 or 19200; chosen by 0 where
+                            no single CTA's registers hold the chain and this does,
+                            before either shared-memory placement); FP32 mode:
                             16 + c (c = 1..8) = register
                             configuration c (E sites per update thread x update warps:
                             1x7, 2x7, 5x7, 5x15, 9x15, 16x15, 26x15, 35x15; q at most
@@ -353,9 +358,10 @@ int potts_lr_probe(int what, double* value);
  * benchmark label and bound what it timed).  info: host array of n int32
  * (n >= 1; entries past 7 are not written): [0] kernel (0 = fields in shared
  * or global memory, 1 = fields in registers, 2 = fields shared by a CTA
- * cluster, 3 = the direct sweep without fields); [1] fields in shared memory
- * (0/1); [2] coupling table in shared memory (0/1); [3] register
- * configuration (1..8, else 0); [4] cluster size (2, 4 or 8, else 0); [5]
+ * cluster in shared memory, 3 = the direct sweep without fields, 4 = fields
+ * in the registers of a CTA cluster); [1] fields in shared memory (0/1); [2]
+ * coupling table in shared memory (0/1); [3] register configuration (1..8,
+ * else 0); [4] cluster size (2, 4 or 8, else 0); [5]
  * threads per CTA; [6] dynamic shared memory per CTA in bytes.  EINVAL for a
  * NULL handle or info, or n < 1. */
 int potts_lr_sweep_info(potts_lr_t* h, int32_t* info, int n);

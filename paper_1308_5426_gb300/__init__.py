@@ -43,17 +43,18 @@ def probe(what: str) -> float:
     return v.value
 
 
-SWEEP_VARIANTS = ("auto", "memory", "registers", "global", "direct", "cluster") + tuple(
+SWEEP_VARIANTS = ("auto", "memory", "registers", "global", "direct", "cluster", "rcluster") + tuple(
     "registers%d" % c for c in range(1, 9))
 
 
 def sweep_variant_code(name):
     """potts_lr_opts.sweep_variant for a variant name: "auto", "memory",
     "registers", "global", "direct" (the paper's O(L)-per-attempt sweep, FP64),
-    "cluster" (FP32: a slot's fields shared by a cluster of 2, 4 or 8 CTAs) or
+    "cluster" (a slot's fields shared by a cluster of 2, 4 or 8 CTAs in shared
+    memory), "rcluster" (the same in the CTAs' registers; FP32 and FX64) or
     "registers<c>" (register configuration c = 1..8)."""
-    if name in ("auto", "memory", "registers", "global", "direct", "cluster"):
-        return {"auto": 0, "memory": 1, "registers": 2, "global": 3, "direct": 4, "cluster": 5}[name]
+    if name in ("auto", "memory", "registers", "global", "direct", "cluster", "rcluster"):
+        return {"auto": 0, "memory": 1, "registers": 2, "global": 3, "direct": 4, "cluster": 5, "rcluster": 6}[name]
     if isinstance(name, str) and name.startswith("registers") and name[9:].isdigit() and 1 <= int(name[9:]) <= 8:
         return 16 + int(name[9:])
     raise ValueError("unknown sweep variant %r" % (name,))
@@ -185,7 +186,7 @@ class Job:
         """The sweep kernel this job runs (potts_lr_sweep_info)."""
         v = np.zeros(7, np.int32)
         _lib.check(self._lib.potts_lr_sweep_info(self._h, _lib._ptr(v), 7))
-        kind = ("memory", "registers", "cluster", "direct")[int(v[0])]
+        kind = ("memory", "registers", "cluster", "direct", "register_cluster")[int(v[0])]
         return {"kernel": kind, "fields_in_smem": bool(v[1]), "table_in_smem": bool(v[2]),
                 "register_config": int(v[3]), "cluster": int(v[4]), "threads": int(v[5]),
                 "smem_bytes": int(v[6])}

@@ -32,7 +32,8 @@ struct JobDev {
     int recompute_every;  // FP32 mode: longest interval K between field rebuilds (0 = on request only)
     int h_smem, j_smem;   // sweep kernel: fields / coupling table staged in shared memory
     int rf;               // register-resident sweep configuration (0 = none; FP32 mode 1..8, FX64 mode 1..6)
-    int cl;               // FP32 mode: CTAs of the cluster that shares a slot's fields (0 = none; 2, 4, 8)
+    int cl;               // CTAs of the cluster that shares a slot's fields in shared memory (0 = none; 2, 4, 8)
+    int rc;               // CTAs of the cluster that holds a slot's fields in registers (0 = none; 2, 4, 8)
     int random_sites;     // direct sweep: attempt m at a site drawn from Philox counter (m, slot, sweep, 3)
     uint32_t key0, key1;  // Philox key (seed low, high)
     double jtot;          // sum_r J*(r)
@@ -223,6 +224,18 @@ PLR_RFX_DECL(d)
 PLR_RFX_DECL(e)
 PLR_RFX_DECL(f)
 #undef PLR_RFX_DECL
+// Register-resident cluster sweep (sweep_rfc.cuh): a slot's fields in the
+// registers of a cluster of C = 2, 4 or 8 CTAs (FP32: 9 sites per update
+// thread, q <= 8, L <= 4320 C; FX64: 5 sites, q <= 7, L <= 2400 C).
+bool rfc_fits(int precision, int C, int L, int q);
+int rfc_cluster_for(int precision, int L, int q);  // smallest C that holds the chain (0: none)
+size_t rfc_smem_bytes(int precision, int q, int L);
+cudaError_t launch_sweep_rfc(int precision, int C, int q, const JobDev* jobs_dev, const int2* work, int nwork,
+                             int nsweeps, size_t smem, cudaStream_t st);
+cudaError_t launch_sweep_rfc_f(int q, int C, const JobDev*, const int2*, int, int, size_t, cudaStream_t);
+cudaError_t launch_sweep_rfc_x(int q, int C, const JobDev*, const int2*, int, int, size_t, cudaStream_t);
+size_t sweep_rfc_smem_f(int q, int L);
+size_t sweep_rfc_smem_x(int q, int L);
 size_t sweep_rf_smem_a(int q, int L, int Lpad);
 size_t sweep_rf_smem_b(int q, int L, int Lpad);
 size_t sweep_rf_smem_c(int q, int L, int Lpad);

@@ -99,3 +99,40 @@ cudaError_t launch_sweep_rf(int cfg, int q, const JobDev* jobs_dev, const int2* 
 }
 
 }  // namespace plr
+
+namespace plr {
+
+// Register-resident cluster sweep (sweep_rfc.cuh): FP32 fields 9 sites per
+// update thread (q <= 8), FX64 fields 5 (q <= 7); 15 update warps per CTA;
+// a cluster of C = 2, 4 or 8 CTAs holds 480 C E sites.
+bool rfc_fits(int precision, int C, int L, int q)
+{
+    if (C != 2 && C != 4 && C != 8) return false;
+    if (L <= kSiteBlock || q < 2) return false;  // at least two blocks of sites
+    if (precision == kPrecFP32) return q <= 8 && L <= C * 9 * 480;
+    if (precision == kPrecFX64) return q <= 7 && L <= C * 5 * 480;
+    return false;
+}
+
+int rfc_cluster_for(int precision, int L, int q)
+{
+    for (int C = 2; C <= 8; C *= 2)
+        if (rfc_fits(precision, C, L, q)) return C;
+    return 0;
+}
+
+size_t rfc_smem_bytes(int precision, int q, int L)
+{
+    return precision == kPrecFP32 ? sweep_rfc_smem_f(q, L) : precision == kPrecFX64 ? sweep_rfc_smem_x(q, L) : 0;
+}
+
+cudaError_t launch_sweep_rfc(int precision, int C, int q, const JobDev* jobs_dev, const int2* work, int nwork,
+                             int nsweeps, size_t smem, cudaStream_t st)
+{
+    if (nwork <= 0 || nsweeps <= 0) return cudaSuccess;
+    if (precision == kPrecFP32) return launch_sweep_rfc_f(q, C, jobs_dev, work, nwork, nsweeps, smem, st);
+    if (precision == kPrecFX64) return launch_sweep_rfc_x(q, C, jobs_dev, work, nwork, nsweeps, smem, st);
+    return cudaErrorNotSupported;
+}
+
+}  // namespace plr

@@ -245,6 +245,40 @@ def test_cluster_sweep_equals_global_sweep(plr, precision, L, q, sigma, R, round
     b.close()
 
 
+@pytest.mark.parametrize("precision,L,q,sigma,R,rounds", [
+    ("fp32", 2048, 5, 0.4, 3, 8),     # two CTAs, ragged use of the second
+    ("fp32", 8640, 8, 0.5, 2, 4),     # two CTAs, full
+    ("fp32", 10001, 3, 0.3, 2, 3),    # four CTAs, ragged last block
+    ("fp32", 16384, 5, 0.4, 2, 2),    # four CTAs (the long serving shape)
+    ("fp32", 20000, 8, 0.6, 2, 2),    # eight CTAs, the last one part empty
+    ("fx64", 1000, 7, 0.5, 3, 8),     # FX64: two CTAs
+    ("fx64", 9000, 5, 0.4, 2, 3),     # four CTAs
+    ("fx64", 16384, 3, 0.3, 2, 2),    # eight CTAs
+])
+def test_register_cluster_sweep_equals_global_sweep(plr, precision, L, q, sigma, R, rounds):
+    """A slot's fields held in the registers of a CTA cluster (flips sent to
+    every CTA through distributed shared memory) run the same arithmetic as the
+    single-CTA sweep with the fields in global memory: spins, fields, energies
+    and counters agree bit for bit, across sweeps, exchanges, multi-sweep
+    launches and (FP32) tensor-core rebuilds."""
+    temps = workloads.geometric_ratios(R, 0.05, 1.0) * oracle.jtot(L, sigma)
+    a = plr.Job(L, q, sigma, temps, 29, precision=precision, recompute_every=3, sweep_variant="global")
+    b = plr.Job(L, q, sigma, temps, 29, precision=precision, recompute_every=3, sweep_variant="rcluster")
+    assert b.sweep_info()["kernel"] == "register_cluster"
+    for _ in range(rounds):
+        for j in (a, b):
+            j.sweep(1)
+            j.exchange()
+    for j in (a, b):
+        j.sweep(2)
+    np.testing.assert_array_equal(a.spins(), b.spins())
+    np.testing.assert_array_equal(a.fields(), b.fields())
+    np.testing.assert_array_equal(a.running_energy(), b.running_energy())
+    np.testing.assert_array_equal(a.stats()["acc_flip"], b.stats()["acc_flip"])
+    a.close()
+    b.close()
+
+
 @pytest.mark.parametrize("precision,L,q", [("fp32", 65536, 16), ("fp64", 32768, 16), ("fx64", 65536, 4)])
 def test_cluster_sweep_rejects_oversize(plr, precision, L, q):
     """Fields beyond eight CTAs' shared memory (4 MB of FP32, 4 MB and 2 MB of

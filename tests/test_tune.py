@@ -15,7 +15,7 @@ def test_variant_codes():
     for bad in ("registers0", "registers9", "fast", 5):
         with pytest.raises(ValueError):
             sweep_variant_code(bad)
-    assert len(SWEEP_VARIANTS) == 14
+    assert len(SWEEP_VARIANTS) == 15
 
 
 def test_candidates():
