@@ -13,6 +13,7 @@ cases:
   rebuild_fp32  L=4096 q=8 R=128, FP32: 3 tensor-core field rebuilds + measurements
   long_fp32     one job L=16384 q=5 R=64, FP32, fields in global memory (memory kernel), 3 sweeps
   long_fp32_cluster  the same job with its fields shared by a two-CTA cluster, 3 sweeps
+  long_fp32_rcluster  the same job with its fields in the registers of a four-CTA cluster, 3 sweeps
 Each case builds its jobs, runs, synchronises and exits 0; inputs are the
 seeded workloads of paper_1308_5426_gb300.workloads.
 """
@@ -32,11 +33,12 @@ def main(argv):
     elif case in ("precision_fp32", "precision_fp64", "precision_fx64"):
         prec = case[-4:]
         specs, nsw = [workloads.precision_job(prec)], 3
-    elif case in ("long_fp32", "long_fp32_cluster"):
+    elif case in ("long_fp32", "long_fp32_cluster", "long_fp32_rcluster"):
         from paper_1308_5426_gb300.workloads import geometric_ratios
         L, q = 16384, 5
+        v = {"long_fp32": "memory", "long_fp32_cluster": "cluster", "long_fp32_rcluster": "rcluster"}[case]
         j = plr.Job(L, q, 0.4, geometric_ratios(64, 0.05, 1.0) * plr.jtot(L, 0.4), 3, precision="fp32",
-                    recompute_every=0, sweep_variant="memory" if case == "long_fp32" else "cluster")
+                    recompute_every=0, sweep_variant=v)
         for _ in range(3):
             j.sweep(1)
             j.exchange()
