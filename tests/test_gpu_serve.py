@@ -41,13 +41,33 @@ def _requests():
     return out
 
 
-def test_served_results_equal_alone():
+LONG_SPECS = [  # L, q, sigma, R, sweeps, arrival, precision: requests that take the cluster kernels
+    (16384, 5, 0.4, 4, 12, 0.00, "fp32"),   # FP32 fields in the registers of a 4-CTA cluster
+    (8192, 3, 0.6, 5, 15, 0.00, "fp32"),    # one CTA's registers (26 sites per thread)
+    (10000, 12, 0.5, 3, 10, 0.02, "fp32"),  # q > 8: the shared memory of a cluster
+    (9000, 5, 0.3, 3, 10, 0.03, "fx64"),    # FX64 fields in the registers of a 4-CTA cluster
+    (6000, 5, 0.7, 3, 8, 0.04, "fp64"),     # FP64 fields in the shared memory of a 2-CTA cluster
+]
+
+
+def _long_requests():
+    out = []
+    for i, (L, q, sigma, R, sweeps, arr, prec) in enumerate(LONG_SPECS):
+        temps = workloads.geometric_ratios(R, 0.05, 1.0) * oracle.jtot(L, sigma)
+        out.append(Request(rid=i, L=L, q=q, sigma=sigma, temps=temps, seed=200 + i, sweeps=sweeps,
+                           precision=prec, recompute_every=4, arrival=arr))
+    return out
+
+
+@pytest.mark.parametrize("which", ["short", "long"])
+def test_served_results_equal_alone(which):
     import __graft_entry__
     __graft_entry__.build()
     import paper_1308_5426_gb300 as plr
-    reqs = _requests()
+    reqs = _requests() if which == "short" else _long_requests()
     budget = int(2.2 * max(r.footprint for r in reqs))  # forces queueing
-    srv = Server(GpuEngine(), budget_bytes=budget, chunk=10, clock=StepClock(), keep_spins=True)
+    srv = Server(GpuEngine(), budget_bytes=budget, chunk=10 if which == "short" else 4, clock=StepClock(),
+                 keep_spins=True)
     res = srv.run(reqs, idle_sleep=0.0)
     assert all(r.status == "done" for r in res.values())
     # at least one job was admitted after another had started running
@@ -57,6 +77,9 @@ def test_served_results_equal_alone():
         out = res[r.rid]
         job = plr.Job(r.L, r.q, r.sigma, r.temps, r.seed, precision=r.precision,
                       recompute_every=r.recompute_every)
+        if which == "long":
+            want = {0: "register_cluster", 1: "registers", 2: "cluster", 3: "register_cluster", 4: "cluster"}
+            assert job.sweep_info()["kernel"] == want[r.rid], (r.rid, job.sweep_info())
         done = 0
         for at, E, M in zip(out.at, out.E, out.M):
             while done < at:
