@@ -596,7 +596,7 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
             return fail(POTTS_LR_EINVAL, "the direct sweep keeps the spins of its slot in shared memory: L too large");
         }
     }
-    h->measure_smem = measure_smem_bytes(L, h->W);
+    h->measure_smem = measure_smem_bytes(L, q);
     h->direct_smem = direct_smem_bytes(L, q);
 
     cudaStream_t st = h->stream;

@@ -30,18 +30,17 @@ __global__ void init_spins_kernel(const JobDev* __restrict__ jobs, int job)
     jb.spins[(size_t)r * jb.W + w] = word;
 }
 
-// Energy (Eq. 2) and magnetisation (Eq. 10) of one slot, from its packed spins:
+// Energy (Eq. 2) and magnetisation (Eq. 10) of one slot, from its packed spins
+// (the bit-plane count of measure_body.cuh):
 //   N_r = #{i : s_i = s_{(i+r) mod L}}, r = 1..L/2  (N_{L-r} = N_r),
 //   E = -(c/2) sum_{r=1}^{L-1} J*(r) N_r,  M = (q N_max / L - 1) / (q - 1).
-// The sum over r is split over the slot's jb.meas_parts CTAs (blockIdx.x =
-// item * max_parts + part; CTAs past the job's part count return at once):
-// part p takes a contiguous range of r, counts N_r 8 sites at a time (the
-// packed word of sites 8w..8w+7 XORed with the word of sites 8w+r..8w+r+7, a
-// funnel shift of the doubled packed string in shared memory, then its zero
-// nibbles counted) and sums J*(r) N_r in a fixed order (per thread, then a
-// fixed tree).  The CTA that finishes last (a per-slot ticket) adds the parts'
-// sums in part order and writes E and M, so the result does not depend on
-// which CTA ends first; the part count depends on L only.
+// The sum over (r, w) is cut into the jb.meas_parts tiles of meas_geom(L), one
+// CTA each (blockIdx.x = item * max_parts + part; CTAs past the job's part
+// count return at once).  A CTA builds the bit planes of the string words its
+// tile reads and sums J*(r) N_r over the tile in a fixed order (per thread,
+// then a fixed tree).  The CTA that finishes last (a per-slot ticket) adds the
+// tiles' sums in tile order, counts the states and writes E and M, so the
+// result does not depend on which CTA ends first.
 __global__ void __launch_bounds__(kAuxThreads) measure_kernel(const JobDev* __restrict__ jobs,
                                                               const int2* __restrict__ work, int max_parts,
                                                               int anchor, int cond)
@@ -57,44 +56,17 @@ __global__ void __launch_bounds__(kAuxThreads) measure_kernel(const JobDev* __re
     if (part >= np || (cond && !rebuild_due(jb))) return;
     const int t = wk.y;
     const int rep = jb.map[t];
-    const int L = jb.L, W = jb.W, tid = threadIdx.x;
-    const uint32_t* __restrict__ spins = jb.spins + (size_t)rep * W;
-    const int nd = 2 * W + 2;  // doubled packed string, enough words for any shift
-    uint32_t* dbl = (uint32_t*)smem;
-    uint8_t* s = (uint8_t*)(dbl + nd);
-    for (int i = tid; i < L; i += kAuxThreads) s[i] = (uint8_t)((spins[i >> 3] >> (4 * (i & 7))) & 15u);
+    const int L = jb.L, tid = threadIdx.x;
+    const uint32_t* __restrict__ spins = jb.spins + (size_t)rep * jb.W;
+    const MeasGeom g = meas_geom(L);
+    const int P = meas_planes(jb.q), ws = meas_window_words(g);
+    const int rt = part / g.nwt, wt = part - rt * g.nwt;
+    int w_lo, w_hi, nwin;
+    tile_words(g, rt, wt, &w_lo, &w_hi, &nwin);
+    uint32_t* win = (uint32_t*)smem;
+    build_planes(spins, L, P, w_lo, nwin, win, ws);
     __syncthreads();
-    for (int m = tid; m < nd; m += kAuxThreads) {
-        uint32_t word = 0;
-        for (int b = 0; b < 8; ++b) word |= (uint32_t)s[(8 * m + b) % L] << (4 * b);
-        dbl[m] = word;
-    }
-    __syncthreads();
-
-    const int tail = L & 7;  // valid nibbles of the last word (0 = all 8)
-    const uint32_t tail_bits = tail ? (0x11111111u & ((1u << (4 * tail)) - 1u)) : 0x11111111u;
-    const int nr = L / 2, per = (nr + np - 1) / np;
-    const int r_hi = min(nr, (part + 1) * per);
-    double partial = 0.0;
-    for (int r = 1 + part * per + tid; r <= r_hi; r += kAuxThreads) {
-        const int qo = r >> 3, sh = 4 * (r & 7);
-        int nz = 0;  // differing sites (nonzero nibbles of the XOR) in the full words
-        uint32_t lo = dbl[qo];
-#pragma unroll 4
-        for (int w = 0; w < W - 1; ++w) {
-            const uint32_t hi = dbl[w + qo + 1];
-            const uint32_t x = dbl[w] ^ __funnelshift_r(lo, hi, sh);
-            // bit 3 of a nibble of this is set iff the nibble of x is nonzero
-            nz += __popc((((x & 0x77777777u) + 0x77777777u) | x) & 0x88888888u);
-            lo = hi;
-        }
-        uint32_t x = dbl[W - 1] ^ __funnelshift_r(lo, dbl[W + qo], sh);
-        x |= x >> 1;
-        x |= x >> 2;
-        const int Nr = 8 * (W - 1) + __popc(tail_bits) - nz - __popc(x & tail_bits);
-        partial += ((2 * r == L) ? 1.0 : 2.0) * jb.J64d[r] * (double)Nr;
-    }
-    const double tot = block_sum_fixed(partial, red);
+    const double tot = block_sum_fixed(measure_tile_any(P, win, ws, w_lo, g, L, rt, w_lo, w_hi, jb.J64d), red);
     if (tid == 0) {
         jb.meas_part[(size_t)t * kMeasMaxParts + part] = tot;
         __threadfence();
@@ -103,7 +75,7 @@ __global__ void __launch_bounds__(kAuxThreads) measure_kernel(const JobDev* __re
     if (tid < kMaxQ) cnt[tid] = 0;
     __syncthreads();
     if (!last) return;
-    for (int i = tid; i < L; i += kAuxThreads) atomicAdd(&cnt[s[i]], 1);
+    count_states(spins, L, jb.q, cnt);
     __syncthreads();
     if (tid == 0) {
         __threadfence();
@@ -273,8 +245,8 @@ cudaError_t launch_init_spins(const JobDev* jobs_dev, int job, int L, int W, int
 
 int measure_parts(int L)
 {
-    const int p = (L / 2) / kAuxThreads;  // at least one pair distance per thread
-    return p < 1 ? 1 : (p > kMeasMaxParts ? kMeasMaxParts : p);
+    const MeasGeom g = meas_geom(L);
+    return g.nrt * g.nwt;
 }
 
 cudaError_t launch_measure(const JobDev* jobs_dev, const int2* work, int nwork, int anchor, int cond,

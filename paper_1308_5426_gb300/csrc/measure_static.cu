@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(kAuxThreads) measure_static_kernel(const uint3
     extern __shared__ __align__(16) unsigned char smem[];
     const int r = blockIdx.x;
     double E, M;
-    measure_body(spins + (size_t)r * W, L, q, W, c, J, smem, &E, &M);
+    measure_body(spins + (size_t)r * W, L, q, c, J, smem, &E, &M);
     if (threadIdx.x == 0) {
         scratch[r] = E;
         scratch[kStaticMeasureMaxR + r] = M;
@@ -104,7 +104,7 @@ extern "C" int potts_lr_measure_static(const uint32_t* spins, int L, int q, int 
     }
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const int W = (L + 7) / 8;
-    const size_t smem = measure_smem_bytes(L, W);
+    const size_t smem = measure_smem_bytes(L, q);
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(measure_static_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)

@@ -11,6 +11,7 @@ cases:
   precision_fp64  L=4096 q=8 R=128, FP64 fields shared by two-CTA clusters, 3 sweeps
   precision_fx64  L=4096 q=8 R=128, FX64 fields shared by two-CTA clusters, 3 sweeps
   rebuild_fp32  L=4096 q=8 R=128, FP32: 3 tensor-core field rebuilds + measurements
+  rebuild_fp32_long  L=16384 q=5 R=64, FP32: 3 tensor-core field rebuilds + measurements
   long_fp32     one job L=16384 q=5 R=64, FP32, fields in global memory (memory kernel), 3 sweeps
   long_fp32_cluster  the same job with its fields shared by a two-CTA cluster, 3 sweeps
   long_fp32_rcluster  the same job with its fields in the registers of a four-CTA cluster, 3 sweeps
@@ -45,8 +46,11 @@ def main(argv):
         j.sync()
         print("ok", case)
         return 0
-    elif case == "rebuild_fp32":
+    elif case in ("rebuild_fp32", "rebuild_fp32_long"):
         s = workloads.precision_job("fp32")
+        if case == "rebuild_fp32_long":
+            s = workloads.JobSpec(L=16384, q=5, sigma=0.4, ratios=workloads.geometric_ratios(64, 0.05, 1.0), seed=3,
+                                  sweeps=1, precision="fp32")
         j = plr.Job(s.L, s.q, s.sigma, s.ratios * plr.jtot(s.L, s.sigma), s.seed, precision="fp32",
                     recompute_every=0)
         j.sweep(1)
