@@ -217,11 +217,11 @@ cudaError_t launch_variant(int key, const JobDev* jobs, const int2* work, int nw
 {
     if (key >= kRfcKey) {
         const int r = key - kRfcKey;
-        return launch_sweep_rfc(r / 1024, (r % 1024) / 64, r % 64, jobs, work, nwork, nsweeps, smem, st);
+        return launch_sweep_rfc(r / 1024, (r % 1024) / 64, r % 64, jobs, work, nwork, nsweeps, smem, sched, st);
     }
     if (key > kClusterKey)
         return launch_sweep_cluster((key - kClusterKey) % 16, (key - kClusterKey) / 16, jobs, work, nwork, nsweeps,
-                                    smem, st);
+                                    smem, sched, st);
     if (key >= kRfxKey)
         return launch_sweep_rfx((key - kRfxKey) / 32, (key - kRfxKey) % 32, jobs, work, nwork, nsweeps, smem, sched,
                                 st);

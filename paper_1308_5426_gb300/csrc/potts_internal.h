@@ -99,6 +99,7 @@ __device__ __forceinline__ bool rebuild_due(const JobDev& jb)
 constexpr int kSchedMaxOcc = 8;    // resident sweep CTAs per SM that a plan can address
 struct SweepSched {
     int* order;   // [n] item indices, heaviest first
+    int2* sorted; // [n] the items themselves in that order (cluster launches)
     int* bins;    // [nsm * occ] item of each (SM, resident CTA) place, -1 for none
     int* claim;   // [n] 0 until an item is taken
     int* ctr;     // [nsm + 2]: arrivals per SM, next list position, CTAs past their claim
@@ -112,6 +113,14 @@ void sweep_sched_carve(char* base, int n, int nsm, SweepSched* s);
 int device_sm_count();
 // the plan kernel (one CTA); weights from jobs[work[i].x] counters
 cudaError_t launch_sweep_plan(const JobDev* jobs_dev, const int2* work, const SweepSched& s, cudaStream_t st);
+// Placement of a cluster launch (cfg: its grid, CTA size, shared memory and
+// cluster attribute): when its nwork clusters are more than can be resident
+// at once, the plan kernel (on st) writes the items heaviest first to
+// sched->sorted and *items points there, so that the clusters dispatched
+// first take the heaviest items and the light ones fill the last wave;
+// otherwise *items is left as it is.
+cudaError_t cluster_plan(const void* kernel, const cudaLaunchConfig_t& cfg, int nwork, const SweepSched* sched,
+                         const JobDev* jobs_dev, const int2* work, const int2** items, cudaStream_t st);
 
 // ---- host-side helpers (jstar.cpp) ----
 void jstar_table(int L, double sigma, double* out);
@@ -174,7 +183,7 @@ cudaError_t launch_sweep_direct(const JobDev* jobs_dev, const int2* work, int nw
 size_t cluster_sweep_smem(int L, int q, int C, int precision);
 int cluster_size_for(int L, int q, size_t budget, int precision);  // smallest C whose share fits (0: none)
 cudaError_t launch_sweep_cluster(int C, int precision, const JobDev* jobs_dev, const int2* work, int nwork,
-                                 int nsweeps, size_t smem, cudaStream_t st);
+                                 int nsweeps, size_t smem, const SweepSched* sched, cudaStream_t st);
 
 // Register-resident FP32 sweep (sweep_rf.cuh): configuration 1..8 =
 // (E sites per update thread, update warps) = (1, 7), (2, 7), (5, 7) for
@@ -231,9 +240,11 @@ bool rfc_fits(int precision, int C, int L, int q);
 int rfc_cluster_for(int precision, int L, int q);  // smallest C that holds the chain (0: none)
 size_t rfc_smem_bytes(int precision, int q, int L);
 cudaError_t launch_sweep_rfc(int precision, int C, int q, const JobDev* jobs_dev, const int2* work, int nwork,
-                             int nsweeps, size_t smem, cudaStream_t st);
-cudaError_t launch_sweep_rfc_f(int q, int C, const JobDev*, const int2*, int, int, size_t, cudaStream_t);
-cudaError_t launch_sweep_rfc_x(int q, int C, const JobDev*, const int2*, int, int, size_t, cudaStream_t);
+                             int nsweeps, size_t smem, const SweepSched* sched, cudaStream_t st);
+cudaError_t launch_sweep_rfc_f(int q, int C, const JobDev*, const int2*, int, int, size_t, const SweepSched*,
+                               cudaStream_t);
+cudaError_t launch_sweep_rfc_x(int q, int C, const JobDev*, const int2*, int, int, size_t, const SweepSched*,
+                               cudaStream_t);
 size_t sweep_rfc_smem_f(int q, int L);
 size_t sweep_rfc_smem_x(int q, int L);
 size_t sweep_rf_smem_a(int q, int L, int Lpad);

@@ -341,7 +341,8 @@ __global__ void __launch_bounds__(kClThreads, 1) sweep_cluster_kernel(const JobD
 }
 
 template <typename T, int C>
-cudaError_t launch_c(const JobDev* jobs_dev, const int2* work, int nwork, int nsweeps, size_t smem, cudaStream_t st)
+cudaError_t launch_c(const JobDev* jobs_dev, const int2* work, int nwork, int nsweeps, size_t smem,
+                     const SweepSched* sched, cudaStream_t st)
 {
     auto k = sweep_cluster_kernel<T, C>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -358,17 +359,19 @@ cudaError_t launch_c(const JobDev* jobs_dev, const int2* work, int nwork, int ns
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k, jobs_dev, work, nsweeps);
+    const int2* items = work;
+    if ((e = cluster_plan((const void*)k, cfg, nwork, sched, jobs_dev, work, &items, st)) != cudaSuccess) return e;
+    return cudaLaunchKernelEx(&cfg, k, jobs_dev, items, nsweeps);
 }
 
 template <typename T>
 cudaError_t launch_t(int C, const JobDev* jobs_dev, const int2* work, int nwork, int nsweeps, size_t smem,
-                     cudaStream_t st)
+                     const SweepSched* sched, cudaStream_t st)
 {
     switch (C) {
-    case 2: return launch_c<T, 2>(jobs_dev, work, nwork, nsweeps, smem, st);
-    case 4: return launch_c<T, 4>(jobs_dev, work, nwork, nsweeps, smem, st);
-    case 8: return launch_c<T, 8>(jobs_dev, work, nwork, nsweeps, smem, st);
+    case 2: return launch_c<T, 2>(jobs_dev, work, nwork, nsweeps, smem, sched, st);
+    case 4: return launch_c<T, 4>(jobs_dev, work, nwork, nsweeps, smem, sched, st);
+    case 8: return launch_c<T, 8>(jobs_dev, work, nwork, nsweeps, smem, sched, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -388,13 +391,13 @@ int cluster_size_for(int L, int q, size_t budget, int precision)
 }
 
 cudaError_t launch_sweep_cluster(int C, int precision, const JobDev* jobs_dev, const int2* work, int nwork,
-                                 int nsweeps, size_t smem, cudaStream_t st)
+                                 int nsweeps, size_t smem, const SweepSched* sched, cudaStream_t st)
 {
     if (nwork <= 0 || nsweeps <= 0) return cudaSuccess;
     switch (precision) {
-    case kPrecFP32: return launch_t<float>(C, jobs_dev, work, nwork, nsweeps, smem, st);
-    case kPrecFP64: return launch_t<double>(C, jobs_dev, work, nwork, nsweeps, smem, st);
-    case kPrecFX64: return launch_t<long long>(C, jobs_dev, work, nwork, nsweeps, smem, st);
+    case kPrecFP32: return launch_t<float>(C, jobs_dev, work, nwork, nsweeps, smem, sched, st);
+    case kPrecFP64: return launch_t<double>(C, jobs_dev, work, nwork, nsweeps, smem, sched, st);
+    case kPrecFX64: return launch_t<long long>(C, jobs_dev, work, nwork, nsweeps, smem, sched, st);
     default: return cudaErrorInvalidValue;
     }
 }

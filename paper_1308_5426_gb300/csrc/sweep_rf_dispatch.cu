@@ -127,11 +127,11 @@ size_t rfc_smem_bytes(int precision, int q, int L)
 }
 
 cudaError_t launch_sweep_rfc(int precision, int C, int q, const JobDev* jobs_dev, const int2* work, int nwork,
-                             int nsweeps, size_t smem, cudaStream_t st)
+                             int nsweeps, size_t smem, const SweepSched* sched, cudaStream_t st)
 {
     if (nwork <= 0 || nsweeps <= 0) return cudaSuccess;
-    if (precision == kPrecFP32) return launch_sweep_rfc_f(q, C, jobs_dev, work, nwork, nsweeps, smem, st);
-    if (precision == kPrecFX64) return launch_sweep_rfc_x(q, C, jobs_dev, work, nwork, nsweeps, smem, st);
+    if (precision == kPrecFP32) return launch_sweep_rfc_f(q, C, jobs_dev, work, nwork, nsweeps, smem, sched, st);
+    if (precision == kPrecFX64) return launch_sweep_rfc_x(q, C, jobs_dev, work, nwork, nsweeps, smem, sched, st);
     return cudaErrorNotSupported;
 }
 

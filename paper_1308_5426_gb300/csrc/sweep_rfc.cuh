@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_rfc_kernel(const JobDev* __
 
 template <typename T, int Q, int E, int C>
 cudaError_t launch_rfc(const JobDev* jobs_dev, const int2* work, int nwork, int nsweeps, size_t smem,
-                       cudaStream_t st)
+                       const SweepSched* sched, cudaStream_t st)
 {
     auto k = sweep_rfc_kernel<T, Q, E, C>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -330,18 +330,20 @@ cudaError_t launch_rfc(const JobDev* jobs_dev, const int2* work, int nwork, int 
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k, jobs_dev, work, nsweeps);
+    const int2* items = work;
+    if ((e = cluster_plan((const void*)k, cfg, nwork, sched, jobs_dev, work, &items, st)) != cudaSuccess) return e;
+    return cudaLaunchKernelEx(&cfg, k, jobs_dev, items, nsweeps);
 }
 
 // dispatch over Q (2..QMAX) and C (2, 4, 8) for one field type and E
 template <typename T, int E, int QMAX>
 cudaError_t launch_rfc_qc(int q, int C, const JobDev* jobs_dev, const int2* work, int nwork, int nsweeps,
-                          size_t smem, cudaStream_t st)
+                          size_t smem, const SweepSched* sched, cudaStream_t st)
 {
     switch (q * 16 + C) {
 #define PLR_RFC(Qv, Cv)                                                                                     \
     case Qv * 16 + Cv:                                                                                      \
-        if constexpr (Qv <= QMAX) return launch_rfc<T, Qv, E, Cv>(jobs_dev, work, nwork, nsweeps, smem, st); \
+        if constexpr (Qv <= QMAX) return launch_rfc<T, Qv, E, Cv>(jobs_dev, work, nwork, nsweeps, smem, sched, st); \
         break;
 #define PLR_RFC_Q(Qv) PLR_RFC(Qv, 2) PLR_RFC(Qv, 4) PLR_RFC(Qv, 8)
         PLR_RFC_Q(2) PLR_RFC_Q(3) PLR_RFC_Q(4) PLR_RFC_Q(5) PLR_RFC_Q(6) PLR_RFC_Q(7) PLR_RFC_Q(8)

@@ -5,9 +5,9 @@
 namespace plr {
 
 cudaError_t launch_sweep_rfc_x(int q, int C, const JobDev* jobs_dev, const int2* work, int nwork, int nsweeps,
-                               size_t smem, cudaStream_t st)
+                               size_t smem, const SweepSched* sched, cudaStream_t st)
 {
-    return rfc::launch_rfc_qc<long long, 5, 7>(q, C, jobs_dev, work, nwork, nsweeps, smem, st);
+    return rfc::launch_rfc_qc<long long, 5, 7>(q, C, jobs_dev, work, nwork, nsweeps, smem, sched, st);
 }
 
 size_t sweep_rfc_smem_x(int q, int L) { return rfc::rfc_smem_q<long long, 5, 7>(q, L); }

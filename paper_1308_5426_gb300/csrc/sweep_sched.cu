@@ -55,6 +55,7 @@ __global__ void __launch_bounds__(kPlanThreads) sweep_plan_kernel(const JobDev* 
     __syncthreads();
     for (int i = tid; i < s.n; i += kPlanThreads) s.order[atomicAdd(&start[plan_bucket(jobs, work[i])], 1)] = i;
     __syncthreads();
+    for (int p = tid; p < s.n; p += kPlanThreads) s.sorted[p] = work[s.order[p]];
     const int ndeal = s.n < nplace ? s.n : nplace;
     for (int p = tid; p < ndeal; p += kPlanThreads) {
         const int pass = p / s.nsm, idx = p - pass * s.nsm;
@@ -67,7 +68,8 @@ __global__ void __launch_bounds__(kPlanThreads) sweep_plan_kernel(const JobDev* 
 
 size_t sweep_sched_bytes(int n, int nsm)
 {
-    return a256((size_t)n * 4) * 2 + a256((size_t)nsm * kSchedMaxOcc * 4) + a256((size_t)(nsm + 2) * 4);
+    return a256((size_t)n * 4) * 2 + a256((size_t)n * 8) + a256((size_t)nsm * kSchedMaxOcc * 4) +
+           a256((size_t)(nsm + 2) * 4);
 }
 
 void sweep_sched_carve(char* base, int n, int nsm, SweepSched* s)
@@ -77,6 +79,8 @@ void sweep_sched_carve(char* base, int n, int nsm, SweepSched* s)
     off += a256((size_t)n * 4);
     s->claim = (int*)(base + off);
     off += a256((size_t)n * 4);
+    s->sorted = (int2*)(base + off);
+    off += a256((size_t)n * 8);
     s->bins = (int*)(base + off);
     off += a256((size_t)nsm * kSchedMaxOcc * 4);
     s->ctr = (int*)(base + off);
@@ -105,6 +109,22 @@ cudaError_t launch_sweep_plan(const JobDev* jobs_dev, const int2* work, const Sw
 {
     sweep_plan_kernel<<<1, kPlanThreads, 0, st>>>(jobs_dev, work, s);
     return cudaGetLastError();
+}
+
+cudaError_t cluster_plan(const void* kernel, const cudaLaunchConfig_t& cfg, int nwork, const SweepSched* sched,
+                         const JobDev* jobs_dev, const int2* work, const int2** items, cudaStream_t st)
+{
+    if (!sched || sched->nsm <= 0 || nwork <= 1) return cudaSuccess;
+    int resident = 0;
+    cudaError_t e = cudaOccupancyMaxActiveClusters(&resident, kernel, &cfg);
+    if (e != cudaSuccess) return e;
+    if (resident <= 0 || nwork <= resident) return cudaSuccess;
+    SweepSched sc = *sched;
+    sc.n = nwork;
+    sc.occ = 0;  // no places dealt: the plan only orders the items
+    if ((e = launch_sweep_plan(jobs_dev, work, sc, st)) != cudaSuccess) return e;
+    *items = sc.sorted;
+    return cudaSuccess;
 }
 
 }  // namespace plr
