@@ -119,6 +119,25 @@ __device__ __forceinline__ void draw_proposal(int k, int t, uint32_t n, uint32_t
 // units, Jfx the rounded integer table, fxs = 2^-F the value of one unit; the
 // corrections are integer adds, so the difference is exact before its one
 // conversion to FP64.
+// Lanes j whose proposal shares a state with this lane's, from the bit planes
+// of the block's states (q <= 16): bit j of m_ab is [a == b_j], of m_aa
+// [a == a_j], of m_bb [b == b_j], of m_ba [b == a_j].  The whole warp calls it.
+__device__ __forceinline__ void state_masks(int a, int b, unsigned& m_ab, unsigned& m_aa, unsigned& m_bb,
+                                            unsigned& m_ba)
+{
+    m_ab = m_aa = m_bb = m_ba = kFullMask;
+#pragma unroll
+    for (int bit = 0; bit < 4; ++bit) {
+        const unsigned pa = __ballot_sync(kFullMask, (a >> bit) & 1);
+        const unsigned pb = __ballot_sync(kFullMask, (b >> bit) & 1);
+        const bool ia = (a >> bit) & 1, ib = (b >> bit) & 1;
+        m_ab &= ia ? pb : ~pb;
+        m_aa &= ia ? pa : ~pa;
+        m_bb &= ib ? pb : ~pb;
+        m_ba &= ib ? pa : ~pa;
+    }
+}
+
 template <int kMode>
 __device__ __forceinline__ int decide_block(int lane, int nv, int k, int L, int a, int b, float nlu, uint32_t ux1,
                                             uint32_t ux2, float d32, double base64, const int* pk, const int* pab,
@@ -130,13 +149,19 @@ __device__ __forceinline__ int decide_block(int lane, int nv, int k, int L, int 
 {
     constexpr bool kFP64 = kMode != 0;
     const bool valid = lane < nv;
-    // corrections for the previous block's flips, four independent loads at a time
+    // The state masks (state_masks) give the change of this lane's difference
+    // by a flip at j of this block: ([a == b_j] - [a == a_j] - [b == b_j] +
+    // [b == a_j]) J*(lane - j).  They are made at the block's first accepted
+    // flip, so that blocks without flips do not pay for them.
+    unsigned m_ab = 0u, m_aa = 0u, m_bb = 0u, m_ba = 0u;
+    bool masks = false;
+    // corrections for the previous block's flips, eight independent loads at a time
     int f = 0;
-    for (; f + 4 <= npend; f += 4) {
-        float jv[4];
-        int cf[4];
+    for (; f + 8 <= npend; f += 8) {
+        float jv[8];
+        int cf[8];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
+        for (int e = 0; e < 8; ++e) {
             const int kf = pk[f + e], af = pab[f + e] >> 8, bf = pab[f + e] & 255;
             int r = k - kf;
             r += r < 0 ? L : 0;  // 1..63 for valid lanes
@@ -144,7 +169,7 @@ __device__ __forceinline__ int decide_block(int lane, int nv, int k, int L, int 
             cf[e] = (a == bf) - (a == af) - (b == bf) + (b == af);
         }
 #pragma unroll
-        for (int e = 0; e < 4; ++e) d32 = fmaf((float)cf[e], jv[e], d32);
+        for (int e = 0; e < 8; ++e) d32 = fmaf((float)cf[e], jv[e], d32);
     }
     for (; f < npend; ++f) {
         const int kf = pk[f], af = pab[f] >> 8, bf = pab[f] & 255;
@@ -219,13 +244,18 @@ __device__ __forceinline__ int decide_block(int lane, int nv, int k, int L, int 
             }
         }
         if (acc) {
-            const int abj = __shfl_sync(kFullMask, ab, j);
+            if (!masks) {  // warp-uniform
+                masks = true;
+                state_masks(a, b, m_ab, m_aa, m_bb, m_ba);
+            }
             const float jd = Jn[(lane - j) & 31];
-            const int aj = abj >> 8, bj = abj & 255;
-            accmask |= 1u << j;
+            const unsigned bj = 1u << j;
+            accmask |= bj;
             dmine = lane == j ? d32 : dmine;
-            const int coef = (lane > j && valid) ? (a == bj) - (a == aj) - (b == bj) + (b == aj) : 0;
-            d32 = fmaf((float)coef, jd, d32);
+            // coefficient x J*, exact (a multiple of jd by -2..2), then one rounding
+            const float t = (((m_ab & bj) ? jd : 0.0f) + ((m_ba & bj) ? jd : 0.0f)) -
+                            (((m_aa & bj) ? jd : 0.0f) + ((m_bb & bj) ? jd : 0.0f));
+            d32 += (lane > j && valid) ? t : 0.0f;
         }
         p = j + 1;
     }

@@ -58,11 +58,72 @@ struct RfSmem {
         }                                                                               \
         break;
 
+// Two FP32 values in one 64-bit register, for the packed two-lane adds of
+// sm_100-class GPUs (add/sub.rn.f32x2: each half rounds as a scalar add).
+__device__ __forceinline__ unsigned long long pack_f32x2(float lo, float hi)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void unpack_f32x2(unsigned long long p, float& lo, float& hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(p));
+}
+
+// FP32 rows, sites m and m+1 of the thread paired: one packed add or subtract
+// applies a flip to both (an odd last site takes a scalar one)
+#define PLR_RF2_CASE(c, PTX, OP)                                                       \
+    case c:                                                                            \
+        if constexpr ((c) < Q) {                                                       \
+            _Pragma("unroll") for (int m = 0; m + 1 < E; m += 2) {                     \
+                unsigned long long hp = pack_f32x2(h[m][c], h[m + 1][c]);              \
+                asm(PTX " %0, %0, %1;" : "+l"(hp) : "l"(vv[m / 2]));                    \
+                unpack_f32x2(hp, h[m][c], h[m + 1][c]);                                \
+            }                                                                          \
+            if constexpr (E & 1) h[E - 1][c] OP v[E - 1];                              \
+        }                                                                              \
+        break;
+#define PLR_RF2_SWITCH(s, PTX, OP)                                                                          \
+    switch (s) {                                                                                            \
+        PLR_RF2_CASE(0, PTX, OP) PLR_RF2_CASE(1, PTX, OP) PLR_RF2_CASE(2, PTX, OP) PLR_RF2_CASE(3, PTX, OP)     \
+        PLR_RF2_CASE(4, PTX, OP) PLR_RF2_CASE(5, PTX, OP) PLR_RF2_CASE(6, PTX, OP) PLR_RF2_CASE(7, PTX, OP)     \
+        PLR_RF2_CASE(8, PTX, OP) PLR_RF2_CASE(9, PTX, OP) PLR_RF2_CASE(10, PTX, OP) PLR_RF2_CASE(11, PTX, OP)   \
+        PLR_RF2_CASE(12, PTX, OP) PLR_RF2_CASE(13, PTX, OP) PLR_RF2_CASE(14, PTX, OP) PLR_RF2_CASE(15, PTX, OP) \
+        default: break;                                                                                     \
+    }
+
+template <int Q, int E, int NU>
+__device__ __forceinline__ void apply_rows_paired(float (&h)[E][Q], const float* __restrict__ J2, int u, int L,
+                                                  const int* pk, const int* pab, int nf)
+{
+    for (int f = 0; f < nf; ++f) {
+        const int kf = pk[f], af = pab[f] >> 8, bf = pab[f] & 255;
+        float v[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = J2[m * 32 * NU + u - kf + L];
+        unsigned long long vv[E / 2];
+#pragma unroll
+        for (int m = 0; m + 1 < E; m += 2) vv[m / 2] = pack_f32x2(v[m], v[m + 1]);
+        PLR_RF2_SWITCH(af, "sub.rn.f32x2", -=)
+        PLR_RF2_SWITCH(bf, "add.rn.f32x2", +=)
+    }
+}
+
+#undef PLR_RF2_SWITCH
+#undef PLR_RF2_CASE
+
 // apply flips (pk, pab)[0..nf) to all register rows of update thread u
 template <typename T, int Q, int E, int NU>
 __device__ __forceinline__ void apply_rows(T (&h)[E][Q], const T* __restrict__ J2, int u, int L, const int* pk,
                                            const int* pab, int nf)
 {
+    // FP32 fields in 512-thread CTAs: packed pairs (measured faster there; the
+    // 256-thread configurations have no registers to spare for the packing)
+    if constexpr (sizeof(T) == 4 && NU >= 15 && E >= 2) {
+        apply_rows_paired<Q, E, NU>(h, J2, u, L, pk, pab, nf);
+        return;
+    }
     for (int f = 0; f < nf; ++f) {
         const int kf = pk[f], af = pab[f] >> 8, bf = pab[f] & 255;
         T v[E];

@@ -15,6 +15,8 @@ cases:
   long_fp32     one job L=16384 q=5 R=64, FP32, fields in global memory (memory kernel), 3 sweeps
   long_fp32_cluster  the same job with its fields shared by a two-CTA cluster, 3 sweeps
   long_fp32_rcluster  the same job with its fields in the registers of a four-CTA cluster, 3 sweeps
+  hot_fp32_rcluster   L=16384 q=5, four slots at T = Jtot (acceptance 0.86), FP32 fields in the
+                      registers of four-CTA clusters; 10 sweeps to equilibrate, then 2
 Each case builds its jobs, runs, synchronises and exits 0; inputs are the
 seeded workloads of paper_1308_5426_gb300.workloads.
 """
@@ -43,6 +45,16 @@ def main(argv):
         for _ in range(3):
             j.sweep(1)
             j.exchange()
+        j.sync()
+        print("ok", case)
+        return 0
+    elif case == "hot_fp32_rcluster":
+        import numpy as np
+        L = 16384
+        j = plr.Job(L, 5, 0.4, np.full(4, plr.jtot(L, 0.4)), 3, precision="fp32", recompute_every=0,
+                    sweep_variant="rcluster")
+        for _ in range(12):
+            j.sweep(1)
         j.sync()
         print("ok", case)
         return 0
