@@ -545,7 +545,6 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
     // CTA per SM sweeps the slot with few update warps) while the job's
     // clusters fit on the GPU at once (measured: 2-2.6x faster at 64 slots;
     // on a GPU already filled by many jobs' slots, about even); or when asked
-    // for (variant 5)
     // for (variant 5).  FP64 and FX64 fields take a cluster when they fit no
     // single CTA's shared memory.
     // First, FP32 and FX64 chains that no single CTA's registers hold go to the
@@ -554,9 +553,9 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
     // 4.07 against 11.68 ms per sweep; L = 8192, q = 5: 1.41 against 3.01).
     if (!j.rf && o.sweep_variant == 0 && h->precision != POTTS_LR_FP64) {
         const int C = rfc_cluster_for(h->precision, L, q);
-        if (C && rfc_smem_bytes(h->precision, q, L) <= kSmemBudget) {
+        if (C && rfc_smem_bytes(h->precision, q, C, L) <= kSmemBudget) {
             j.rc = C;
-            h->sweep_smem = rfc_smem_bytes(h->precision, q, L);
+            h->sweep_smem = rfc_smem_bytes(h->precision, q, C, L);
         }
     }
     if (!j.rf && !j.rc && (o.sweep_variant == 0 || o.sweep_variant == 5)) {
@@ -577,7 +576,7 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
     }
     if (o.sweep_variant == 6) {  // the slot's fields in the registers of a cluster of CTAs
         const int C = rfc_cluster_for(h->precision, L, q);
-        if (!C || rfc_smem_bytes(h->precision, q, L) > kSmemBudget) {
+        if (!C || rfc_smem_bytes(h->precision, q, C, L) > kSmemBudget) {
             potts_lr_destroy(h);
             return fail(POTTS_LR_EINVAL, "the register-resident cluster sweep holds FP32 chains of q <= 8 and L <= "
                                          "34560, FX64 chains of q <= 7 and L <= 19200 (and more than 32 sites)");
@@ -585,7 +584,7 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
         j.rc = C;
         j.rf = 0;
         j.cl = 0;
-        h->sweep_smem = rfc_smem_bytes(h->precision, q, L);
+        h->sweep_smem = rfc_smem_bytes(h->precision, q, C, L);
     }
     j.random_sites = o.site_order;
     if (o.sweep_variant == 4 || o.site_order == 1) {

@@ -238,15 +238,15 @@ PLR_RFX_DECL(f)
 // thread, q <= 8, L <= 4320 C; FX64: 5 sites, q <= 7, L <= 2400 C).
 bool rfc_fits(int precision, int C, int L, int q);
 int rfc_cluster_for(int precision, int L, int q);  // smallest C that holds the chain (0: none)
-size_t rfc_smem_bytes(int precision, int q, int L);
+size_t rfc_smem_bytes(int precision, int q, int C, int L);
 cudaError_t launch_sweep_rfc(int precision, int C, int q, const JobDev* jobs_dev, const int2* work, int nwork,
                              int nsweeps, size_t smem, const SweepSched* sched, cudaStream_t st);
 cudaError_t launch_sweep_rfc_f(int q, int C, const JobDev*, const int2*, int, int, size_t, const SweepSched*,
                                cudaStream_t);
 cudaError_t launch_sweep_rfc_x(int q, int C, const JobDev*, const int2*, int, int, size_t, const SweepSched*,
                                cudaStream_t);
-size_t sweep_rfc_smem_f(int q, int L);
-size_t sweep_rfc_smem_x(int q, int L);
+size_t sweep_rfc_smem_f(int q, int C, int L);
+size_t sweep_rfc_smem_x(int q, int C, int L);
 size_t sweep_rf_smem_a(int q, int L, int Lpad);
 size_t sweep_rf_smem_b(int q, int L, int Lpad);
 size_t sweep_rf_smem_c(int q, int L, int Lpad);

@@ -32,11 +32,35 @@
 namespace plr {
 namespace rf {
 
+// FP32 fields in 512-thread CTAs apply flips to pairs of a thread's sites
+// (m, m+1) with packed two-lane adds (measured faster there; the 256-thread
+// configurations have no registers to spare for the packing) ...
+template <typename T, int E, int NU>
+__host__ __device__ constexpr bool rf_paired()
+{
+    return sizeof(T) == 4 && NU >= 15 && E >= 2;
+}
+// ... and, where it fits beside the rest of the shared memory (up to 26
+// sites per thread), take both couplings of a pair in one 64-bit load from a
+// table of pairs (J*(i), J*(i + 32 NU)): sites m and m+1 of a thread lie 32 NU
+// apart, so the pair's index is that of site m.
+template <typename T, int E, int NU>
+__host__ __device__ constexpr bool rf_pair_table()
+{
+    return rf_paired<T, E, NU>() && E <= 26;
+}
+
 template <typename T, int NU, int E, int Q>
 struct RfSmem {
+    // J*(m mod L), m < E 32 NU + L (as pairs with J*((m + 32 NU) mod L) when
+    // rf_pair_table); the kernel's carve-up takes its size from here too
+    __host__ __device__ static size_t table_bytes(int L)
+    {
+        return (size_t)(E * 32 * NU + L) * (rf_pair_table<T, E, NU>() ? 8 : sizeof(T));
+    }
     static size_t bytes(int L, int Lpad)
     {
-        size_t b = (size_t)(E * 32 * NU + L) * sizeof(T);  // J*(m mod L), m < E 32 NU + L
+        size_t b = table_bytes(L);
         b += (size_t)Lpad;                                   // spins
         b = (b + 15) & ~(size_t)15;
         b += 2 * 2 * kSiteBlock * sizeof(int);   // double-buffered flip lists
@@ -81,7 +105,7 @@ __device__ __forceinline__ void unpack_f32x2(unsigned long long p, float& lo, fl
                 asm(PTX " %0, %0, %1;" : "+l"(hp) : "l"(vv[m / 2]));                    \
                 unpack_f32x2(hp, h[m][c], h[m + 1][c]);                                \
             }                                                                          \
-            if constexpr (E & 1) h[E - 1][c] OP v[E - 1];                              \
+            if constexpr (E & 1) h[E - 1][c] OP vl;                                    \
         }                                                                              \
         break;
 #define PLR_RF2_SWITCH(s, PTX, OP)                                                                          \
@@ -93,18 +117,30 @@ __device__ __forceinline__ void unpack_f32x2(unsigned long long p, float& lo, fl
         default: break;                                                                                     \
     }
 
-template <int Q, int E, int NU>
+// PT: J2 is the table of pairs (rf_pair_table), else the plain shifted table
+template <int Q, int E, int NU, bool PT>
 __device__ __forceinline__ void apply_rows_paired(float (&h)[E][Q], const float* __restrict__ J2, int u, int L,
                                                   const int* pk, const int* pab, int nf)
 {
     for (int f = 0; f < nf; ++f) {
         const int kf = pk[f], af = pab[f] >> 8, bf = pab[f] & 255;
-        float v[E];
-#pragma unroll
-        for (int m = 0; m < E; ++m) v[m] = J2[m * 32 * NU + u - kf + L];
+        const int i0 = u - kf + L;  // the index of this thread's site 0
         unsigned long long vv[E / 2];
+        float vl = 0.0f;  // the odd last site's coupling
+        if constexpr (PT) {
+            const float2* JP = reinterpret_cast<const float2*>(J2);
 #pragma unroll
-        for (int m = 0; m + 1 < E; m += 2) vv[m / 2] = pack_f32x2(v[m], v[m + 1]);
+            for (int m = 0; m + 1 < E; m += 2) {
+                const float2 p = JP[m * 32 * NU + i0];
+                vv[m / 2] = pack_f32x2(p.x, p.y);
+            }
+            if constexpr (E & 1) vl = J2[2 * ((E - 1) * 32 * NU + i0)];
+        } else {
+#pragma unroll
+            for (int m = 0; m + 1 < E; m += 2)
+                vv[m / 2] = pack_f32x2(J2[m * 32 * NU + i0], J2[(m + 1) * 32 * NU + i0]);
+            if constexpr (E & 1) vl = J2[(E - 1) * 32 * NU + i0];
+        }
         PLR_RF2_SWITCH(af, "sub.rn.f32x2", -=)
         PLR_RF2_SWITCH(bf, "add.rn.f32x2", +=)
     }
@@ -113,35 +149,34 @@ __device__ __forceinline__ void apply_rows_paired(float (&h)[E][Q], const float*
 #undef PLR_RF2_SWITCH
 #undef PLR_RF2_CASE
 
-// apply flips (pk, pab)[0..nf) to all register rows of update thread u
-template <typename T, int Q, int E, int NU>
+// apply flips (pk, pab)[0..nf) to all register rows of update thread u; PT:
+// J2 is the table of pairs (rf_pair_table)
+template <typename T, int Q, int E, int NU, bool PT>
 __device__ __forceinline__ void apply_rows(T (&h)[E][Q], const T* __restrict__ J2, int u, int L, const int* pk,
                                            const int* pab, int nf)
 {
-    // FP32 fields in 512-thread CTAs: packed pairs (measured faster there; the
-    // 256-thread configurations have no registers to spare for the packing)
-    if constexpr (sizeof(T) == 4 && NU >= 15 && E >= 2) {
-        apply_rows_paired<Q, E, NU>(h, J2, u, L, pk, pab, nf);
-        return;
-    }
-    for (int f = 0; f < nf; ++f) {
-        const int kf = pk[f], af = pab[f] >> 8, bf = pab[f] & 255;
-        T v[E];
-#pragma unroll
-        for (int m = 0; m < E; ++m) v[m] = J2[m * 32 * NU + u - kf + L];
-        switch (af) {
-            PLR_RF_CASE(0, -=) PLR_RF_CASE(1, -=) PLR_RF_CASE(2, -=) PLR_RF_CASE(3, -=)
-            PLR_RF_CASE(4, -=) PLR_RF_CASE(5, -=) PLR_RF_CASE(6, -=) PLR_RF_CASE(7, -=)
-            PLR_RF_CASE(8, -=) PLR_RF_CASE(9, -=) PLR_RF_CASE(10, -=) PLR_RF_CASE(11, -=)
-            PLR_RF_CASE(12, -=) PLR_RF_CASE(13, -=) PLR_RF_CASE(14, -=) PLR_RF_CASE(15, -=)
-            default: break;
-        }
-        switch (bf) {
-            PLR_RF_CASE(0, +=) PLR_RF_CASE(1, +=) PLR_RF_CASE(2, +=) PLR_RF_CASE(3, +=)
-            PLR_RF_CASE(4, +=) PLR_RF_CASE(5, +=) PLR_RF_CASE(6, +=) PLR_RF_CASE(7, +=)
-            PLR_RF_CASE(8, +=) PLR_RF_CASE(9, +=) PLR_RF_CASE(10, +=) PLR_RF_CASE(11, +=)
-            PLR_RF_CASE(12, +=) PLR_RF_CASE(13, +=) PLR_RF_CASE(14, +=) PLR_RF_CASE(15, +=)
-            default: break;
+    if constexpr (rf_paired<T, E, NU>()) {
+        apply_rows_paired<Q, E, NU, PT>(h, J2, u, L, pk, pab, nf);
+    } else {
+        for (int f = 0; f < nf; ++f) {
+            const int kf = pk[f], af = pab[f] >> 8, bf = pab[f] & 255;
+            T v[E];
+    #pragma unroll
+            for (int m = 0; m < E; ++m) v[m] = J2[m * 32 * NU + u - kf + L];
+            switch (af) {
+                PLR_RF_CASE(0, -=) PLR_RF_CASE(1, -=) PLR_RF_CASE(2, -=) PLR_RF_CASE(3, -=)
+                PLR_RF_CASE(4, -=) PLR_RF_CASE(5, -=) PLR_RF_CASE(6, -=) PLR_RF_CASE(7, -=)
+                PLR_RF_CASE(8, -=) PLR_RF_CASE(9, -=) PLR_RF_CASE(10, -=) PLR_RF_CASE(11, -=)
+                PLR_RF_CASE(12, -=) PLR_RF_CASE(13, -=) PLR_RF_CASE(14, -=) PLR_RF_CASE(15, -=)
+                default: break;
+            }
+            switch (bf) {
+                PLR_RF_CASE(0, +=) PLR_RF_CASE(1, +=) PLR_RF_CASE(2, +=) PLR_RF_CASE(3, +=)
+                PLR_RF_CASE(4, +=) PLR_RF_CASE(5, +=) PLR_RF_CASE(6, +=) PLR_RF_CASE(7, +=)
+                PLR_RF_CASE(8, +=) PLR_RF_CASE(9, +=) PLR_RF_CASE(10, +=) PLR_RF_CASE(11, +=)
+                PLR_RF_CASE(12, +=) PLR_RF_CASE(13, +=) PLR_RF_CASE(14, +=) PLR_RF_CASE(15, +=)
+                default: break;
+            }
         }
     }
 }
@@ -191,8 +226,9 @@ __device__ __forceinline__ void rf_item(const JobDev* __restrict__ jobs, const i
     uint32_t* __restrict__ spins = jp->spins + (size_t)rep * W;
     const T* __restrict__ Jsrc = kFX ? (const T*)(const void*)jp->Jfxd : (const T*)(const void*)jp->J32d;
 
+    constexpr bool PT = rf_pair_table<T, E, NU>();
     T* J2 = (T*)smem;
-    size_t off = (size_t)(E * NUT + L) * sizeof(T);
+    size_t off = RfSmem<T, NU, E, Q>::table_bytes(L);
     uint8_t* s = smem + off;
     off = (off + (size_t)Lpad + 15) & ~(size_t)15;
     int* lk = (int*)(smem + off);
@@ -205,7 +241,12 @@ __device__ __forceinline__ void rf_item(const JobDev* __restrict__ jobs, const i
     uint32_t* pux = (uint32_t*)(pnlu + 2 * kSiteBlock);  // [2][2][32] words of u (FP64 rule)
     int* lcnt = (int*)(pux + 4 * kSiteBlock);
 
-    for (int m = tid; m < E * NUT + L; m += blockDim.x) J2[m] = Jsrc[m % L];
+    if constexpr (PT) {
+        float2* JP = reinterpret_cast<float2*>(J2);
+        for (int m = tid; m < E * NUT + L; m += blockDim.x) JP[m] = make_float2(Jsrc[m % L], Jsrc[(m + NUT) % L]);
+    } else {
+        for (int m = tid; m < E * NUT + L; m += blockDim.x) J2[m] = Jsrc[m % L];
+    }
     for (int i = tid; i < L; i += blockDim.x) s[i] = (uint8_t)((spins[i >> 3] >> (4 * (i & 7))) & 15u);
     if (tid < kNearTable) Jn[tid] = tid < L ? (float)jp->J64d[tid] : 0.0f;
     if (tid < 32) dEl[tid] = 0.0;
@@ -315,7 +356,7 @@ __device__ __forceinline__ void rf_item(const JobDev* __restrict__ jobs, const i
                 }
             }
         } else {
-            apply_rows<T, Q, E, NU>(h, J2, tid, L, pk, pl, npend);
+            apply_rows<T, Q, E, NU, PT>(h, J2, tid, L, pk, pl, npend);
             if (g + 1 < total) publish_block(g + 1);
         }
         __syncthreads();

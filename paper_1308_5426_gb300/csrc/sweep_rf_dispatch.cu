@@ -121,9 +121,11 @@ int rfc_cluster_for(int precision, int L, int q)
     return 0;
 }
 
-size_t rfc_smem_bytes(int precision, int q, int L)
+size_t rfc_smem_bytes(int precision, int q, int C, int L)
 {
-    return precision == kPrecFP32 ? sweep_rfc_smem_f(q, L) : precision == kPrecFX64 ? sweep_rfc_smem_x(q, L) : 0;
+    return precision == kPrecFP32   ? sweep_rfc_smem_f(q, C, L)
+           : precision == kPrecFX64 ? sweep_rfc_smem_x(q, C, L)
+                                    : 0;
 }
 
 cudaError_t launch_sweep_rfc(int precision, int C, int q, const JobDev* jobs_dev, const int2* work, int nwork,

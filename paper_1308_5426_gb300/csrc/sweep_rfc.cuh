@@ -45,15 +45,24 @@ __device__ __forceinline__ void cluster_sync_all()
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
+// FP32 clusters of 2 or 4 CTAs keep their shifted coupling table as pairs
+// (J*((lo + y) mod L), J*((lo + y + NUT) mod L)) -- see rf::rf_pair_table;
+// at 8 CTAs (L above 4 x 4320) the pairs would not fit
+template <typename T, int E, int C>
+__host__ __device__ constexpr bool rfc_pair_table()
+{
+    return rf::rf_paired<T, E, NU>() && C <= 4;
+}
+
 // carve-up of the dynamic shared memory (must match the kernel)
-template <typename T, int Q, int E>
+template <typename T, int Q, int E, int C>
 struct RfcLayout {
     size_t o_j, o_s, o_lk, o_lab, o_lcnt, o_jn, o_del, o_dacc, o_hv, o_pab, o_pnlu, o_pux, bytes;
     __host__ __device__ RfcLayout(int L)
     {
         size_t o = 0;
-        o_j = o;     // J*((lo + y) mod L), y < E NUT + L
-        o += (size_t)(E * NUT + L) * sizeof(T);
+        o_j = o;     // J*((lo + y) mod L), y < E NUT + L (pairs: rfc_pair_table)
+        o += (size_t)(E * NUT + L) * (rfc_pair_table<T, E, C>() ? 8 : sizeof(T));
         o = (o + 15) & ~(size_t)15;
         o_s = o;     // spins of this CTA's sites
         o += (size_t)E * NUT;
@@ -105,7 +114,8 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_rfc_kernel(const JobDev* __
     const int lo = rank * S;
     const int n = max(0, min(L, lo + S) - lo);  // sites held here
 
-    const RfcLayout<T, Q, E> lay(L);
+    constexpr bool PT = rfc_pair_table<T, E, C>();
+    const RfcLayout<T, Q, E, C> lay(L);
     T* J2 = (T*)(smem + lay.o_j);
     uint8_t* s = smem + lay.o_s;
     int* lk = (int*)(smem + lay.o_lk);
@@ -125,7 +135,13 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_rfc_kernel(const JobDev* __
 
     // the coupling of local site y (site lo + y) to a flip at k is
     // J2[y - k + L] = J*((lo + y - k) mod L): a table shifted by lo
-    for (int m = tid; m < S + L; m += kThreads) J2[m] = Jsrc[(lo + m) % L];
+    if constexpr (PT) {
+        float2* JP = reinterpret_cast<float2*>(J2);
+        for (int m = tid; m < S + L; m += kThreads)
+            JP[m] = make_float2(Jsrc[(lo + m) % L], Jsrc[(lo + m + NUT) % L]);
+    } else {
+        for (int m = tid; m < S + L; m += kThreads) J2[m] = Jsrc[(lo + m) % L];
+    }
     for (int y = tid; y < S; y += kThreads) {
         const int i = lo + y;
         s[y] = y < n ? (uint8_t)((spins[i >> 3] >> (4 * (i & 7))) & 15u) : (uint8_t)0;
@@ -254,7 +270,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_rfc_kernel(const JobDev* __
                     cl.map_shared_rank(dacc, holder(g + 1))[lane] = dEl[lane];
             }
         } else {
-            rf::apply_rows<T, Q, E, NU>(h, J2, tid, L, pk, pl, npend);
+            rf::apply_rows<T, Q, E, NU, PT>(h, J2, tid, L, pk, pl, npend);
             if (g + 1 < total && holder(g + 1) == rank) publish_block(g + 1);
         }
         cluster_sync_all();
@@ -355,12 +371,14 @@ cudaError_t launch_rfc_qc(int q, int C, const JobDev* jobs_dev, const int2* work
 }
 
 template <typename T, int E, int QMAX>
-size_t rfc_smem_q(int q, int L)
+size_t rfc_smem_q(int q, int C, int L)
 {
-    switch (q) {
-#define PLR_RFC_S(Qv) \
-    case Qv: return Qv <= QMAX ? RfcLayout<T, Qv, E>(L).bytes : 0;
-        PLR_RFC_S(2) PLR_RFC_S(3) PLR_RFC_S(4) PLR_RFC_S(5) PLR_RFC_S(6) PLR_RFC_S(7) PLR_RFC_S(8)
+    switch (q * 16 + C) {
+#define PLR_RFC_S(Qv, Cv) \
+    case Qv * 16 + Cv: return Qv <= QMAX ? RfcLayout<T, Qv, E, Cv>(L).bytes : 0;
+#define PLR_RFC_SQ(Qv) PLR_RFC_S(Qv, 2) PLR_RFC_S(Qv, 4) PLR_RFC_S(Qv, 8)
+        PLR_RFC_SQ(2) PLR_RFC_SQ(3) PLR_RFC_SQ(4) PLR_RFC_SQ(5) PLR_RFC_SQ(6) PLR_RFC_SQ(7) PLR_RFC_SQ(8)
+#undef PLR_RFC_SQ
 #undef PLR_RFC_S
     default: return 0;
     }
