@@ -32,7 +32,8 @@
 // fill the 512 TMEM columns.  The epilogue adds them in FP32 with error-free
 // (TwoSum) compensation -- as accurate, for the FP32 fields it stores, as an
 // FP64 sum, at a 64th of the cost on GB300's narrow FP64 pipe -- and the old
-// values (for the drift) are copied to shared memory while the MMAs still run.
+// values (for the drift) are read from global memory a group of columns ahead,
+// which leaves the shared memory to the copy ring.
 //
 // Operand layout (both K-major, no swizzle): 8-row x 16-byte core matrices.
 // A: core matrix h of the strip at byte 128 h; leading (K) and stride (row
@@ -72,10 +73,11 @@ struct TcShape {
     static constexpr int kAccHi = kAcc - 1;          // rotating accumulators of the hi parts; the last takes mid + lo
     static constexpr int kTileBytesB = TN * kChunk * 2;  // TN x kChunk BF16 B tile
     static constexpr int kStageBytes = kSplit * kTileBytes + kTileBytesB;  // three A tiles + the B tile
-    static constexpr int kStages = TN == 128 ? 3 : 4;  // copies run up to kStages - 1 chunks ahead of the MMAs
-    static constexpr int kOldBytes = kEpiWarps * 32 * (TN / 2) * 4;  // the replaced fields, per epilogue thread
+    // copies run up to kStages - 1 chunks ahead of the MMAs (179 KB of stages
+    // at TN = 128, 198 KB at TN = 64)
+    static constexpr int kStages = TN == 128 ? 4 : 7;
 };
-constexpr int kBarBytes = 128;  // full[kStages], empty[kStages], tfull, tempty, drain; TMEM slot; abort flag
+constexpr int kBarBytes = 256;  // full[kStages], empty[kStages], tfull, tempty, drain; TMEM slot; abort flag
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
 {
@@ -219,11 +221,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* 
     constexpr int kAcc = S::kAcc, kAccHi = S::kAccHi, kStageBytes = S::kStageBytes, kStages = S::kStages;
     static_assert(kAcc * TN == kTmemCols, "accumulators fill the tensor memory");
     static_assert(kStageBytes % 128 == 0, "stages stay 128-byte aligned");
+    static_assert((2 * kStages + 3) * 8 + 8 <= kBarBytes, "barriers, TMEM slot and abort flag fit their area");
+    static_assert(kStages * kStageBytes + kBarBytes <= 227 * 1024, "one CTA's shared memory");
     extern __shared__ __align__(1024) unsigned char smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-    float* olds = (float*)(smem + kStages * kStageBytes);         // [TN / 2][256]: column e of epilogue thread
-    uint64_t* full = (uint64_t*)(smem + kStages * kStageBytes + S::kOldBytes);  // copies of stage b landed
+    uint64_t* full = (uint64_t*)(smem + kStages * kStageBytes);  // copies of stage b landed
     uint64_t* empty = full + kStages;                              // MMAs reading stage b done
     uint64_t* tfull = empty + kStages;                             // a tile's MMAs done
     uint64_t* tempty = tfull + 1;                                  // its accumulators read
@@ -321,15 +324,28 @@ __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* 
                     const uint32_t sb = sa + kSplit * kTileBytes;
                     const uint32_t dhi = tmem + (uint32_t)((t % kAccHi) * TN);
                     const uint32_t dsmall = tmem + (uint32_t)(kAccHi * TN);
+                    // The descriptors of the chunk's MMAs differ from the stage's
+                    // first ones only in the address field (byte address / 16,
+                    // 14 bits), and shared-memory addresses stay below 256 KB, so
+                    // desc(addr + off) = desc(addr) + off / 16: one add per MMA
+                    // instead of a full descriptor build in this single issuing
+                    // thread (checked on the host for every stage address)
+                    const uint64_t a0 = make_desc(sa, 128, 128), b0 = make_desc(sb, 128, 2048);
+                    const bool first_hi = t < kAccHi, first_small = t == 0;
+                    // part by part, each over the chunk's 8 K-steps into one
+                    // accumulator: issued K-step by K-step with the parts
+                    // interleaved (accumulators alternating), every K-step took
+                    // about 250 cycles whether it held 2 or 3 MMAs; this order
+                    // runs near the tensor cores' rate (measured)
 #pragma unroll
-                    for (int s = 0; s < kChunk / 16; ++s) {
-                        const uint64_t bdesc = make_desc(sb + s * 256, 128, 2048);
+                    for (int sp = 0; sp < kSplit; ++sp) {
+                        if (sp >= parts) break;  // two parts: hi + mid only
 #pragma unroll
-                        for (int sp = 0; sp < kSplit; ++sp) {
-                            if (sp >= parts) break;  // two parts: hi + mid only
-                            const uint64_t adesc = make_desc(sa + sp * kTileBytes + s * 256, 128, 128);
+                        for (int s = 0; s < kChunk / 16; ++s) {
+                            const uint64_t bdesc = b0 + (uint64_t)((s * 256) >> 4);
+                            const uint64_t adesc = a0 + (uint64_t)((sp * kTileBytes + s * 256) >> 4);
                             const uint32_t dcol = sp == 0 ? dhi : dsmall;
-                            const bool first = s == 0 && (sp == 0 ? t < kAccHi : (t == 0 && sp == 1));
+                            const bool first = s == 0 && (sp == 0 ? first_hi : (first_small && sp == 1));
                             const uint32_t accumulate = first ? 0u : 1u;
                             asm volatile(
                                 "{\n\t.reg .pred p;\n\t"
@@ -369,21 +385,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* 
             const int m0 = tile.y, n0 = tile.z;
             const int i = m0 + 32 * quad + lane;
             float* F = (float*)jb.fields;
-            // the fields being replaced (for the drift): copied to shared memory
-            // (zero-filled outside the job) while the MMAs run
-            float* old = olds + (tid - 64);
-            {
-                const float* src = F + (size_t)(n0 + cb0) * Lpad + i;
-                uint32_t dst = smem_u32(old);
-#pragma unroll 4
-                for (int e = 0; e < kCols; ++e, src += Lpad, dst += 256 * 4) {
-                    const bool in = i < L && n0 + cb0 + e < N;
-                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(in ? src : F),
-                                 "r"(in ? 4 : 0)
-                                 : "memory");
+            // the fields being replaced (for the drift), read by this thread
+            // alone before it writes them: a group of 8 columns one group ahead
+            // of its use (the shared memory goes to the copy ring)
+            auto load_old = [&](int cb, float (&o)[8]) {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const bool in = i < L && n0 + cb0 + cb + e < N;
+                    o[e] = in ? __ldcg(F + (size_t)(n0 + cb0 + cb + e) * Lpad + i) : 0.0f;
                 }
-            }
-            asm volatile("cp.async.commit_group;" ::: "memory");
+            };
+            float onext[8];
+            load_old(0, onext);
             // lane 0 polls (backing off: the wait spans the tile's main loop, and
             // polls compete with the copies and MMAs for shared memory); then
             // every lane observes the completed phase itself
@@ -395,11 +408,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* 
             }
             mbar_wait(smem_u32(tfull), ntile & 1u, nullptr);
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            asm volatile("cp.async.wait_all;" ::: "memory");
             const int nhi = nchunks < kAccHi ? nchunks : kAccHi;
             float dmaxf = 0.0f;
 #pragma unroll
             for (int cb = 0; cb < kCols; cb += 8) {
+                float ocur[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) ocur[e] = onext[e];
+                if (cb + 8 < kCols) load_old(cb + 8, onext);
                 uint32_t v[kAcc][8];
 #pragma unroll
                 for (int a = 0; a < kAcc; ++a) {
@@ -440,7 +456,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* 
                         const int n = n0 + cb0 + cb + e;
                         if (n < N) {
                             const float r = fs[e] + fc[e];
-                            dmaxf = fmaxf(dmaxf, fabsf(old[(cb + e) * 256] - r));  // drift of the ending period
+                            dmaxf = fmaxf(dmaxf, fabsf(ocur[e] - r));  // drift of the ending period
                             F[(size_t)n * Lpad + i] = r;
                         }
                     }
@@ -456,7 +472,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* 
             if (lane == 0) mbar_arrive(smem_u32(tempty));
             ++ntile;
         }
-        asm volatile("cp.async.wait_all;" ::: "memory");  // none still in flight at exit
     }
     if (failed_job >= 0) atomicExch(jobs[failed_job].status, 1);  // the host reports ETIMEOUT
     __syncthreads();
@@ -476,7 +491,7 @@ template <int TN>
 size_t tc_smem_bytes()
 {
     using S = TcShape<TN>;
-    const size_t b = (size_t)S::kStages * S::kStageBytes + S::kOldBytes + kBarBytes;
+    const size_t b = (size_t)S::kStages * S::kStageBytes + kBarBytes;
     return b < kTcMinSmem ? kTcMinSmem : b;
 }
 
