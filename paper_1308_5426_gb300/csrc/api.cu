@@ -439,7 +439,10 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
     const size_t o_nlog = take((size_t)kNearLogCap * sizeof(int4)), o_nlogn = take(4);
     std::vector<int4> tiles;
     h->tc_tn = tc_tile_width(tc_tile_count(L, q, R, 64), tc_tile_count(L, q, R, 128), device_sm_count());
-    if (h->precision == POTTS_LR_FP32) tc_tiles(0, L, q, R, h->tc_tn, tiles);
+    if (h->precision == POTTS_LR_FP32) {
+        tc_tiles(0, L, q, R, h->tc_tn, tiles);
+        tc_order_tiles(tiles);
+    }
     const size_t o_tiles = take(tiles.size() * sizeof(int4) + 16);
     const int nsm = device_sm_count();
     const size_t o_plan = take(sweep_sched_bytes(R, nsm));
@@ -1065,6 +1068,7 @@ int potts_lr_batch_create(potts_lr_t* const* jobs, int n, void* cuda_stream, pot
         b->fp_meas_smem = std::max(b->fp_meas_smem, h->measure_smem);
         b->fp_meas_parts = std::max(b->fp_meas_parts, h->hj.meas_parts);
     }
+    tc_order_tiles(btiles);
     b->ntc_tiles = (int)btiles.size();
     b->nfp_work = (int)fwork.size();
     size_t bytes = align256(n * sizeof(JobDev));

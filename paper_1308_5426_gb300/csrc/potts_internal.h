@@ -157,6 +157,7 @@ cudaError_t launch_fields_direct(const JobDev* job_dev, int L, int R, int mode, 
 cudaError_t launch_fields_tc(const JobDev* jobs_dev, const int* idx, int njobs, int onehot_blocks,
                              const int4* tiles, int ntiles, int cond, int tn, cudaStream_t st);
 void tc_tiles(int job, int L, int q, int R, int tn, std::vector<int4>& out);
+void tc_order_tiles(std::vector<int4>& tiles);  // full-width tiles first (the rebuild's round-robin)
 long long tc_tile_count(int L, int q, int R, int tn);
 int tc_tile_width(long long tiles64, long long tiles128, int nsm);
 int tc_onehot_blocks(int L, int q, int R);  // one-hot grid width for one job of this shape

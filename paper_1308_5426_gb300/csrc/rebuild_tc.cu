@@ -46,6 +46,7 @@
 // ends the other roles' loops, the job's status word is set, and the CTA
 // still drains its own copies and MMAs (waits bounded by 4 s, which such
 // waits never approach) before it frees the tensor memory.
+#include <algorithm>
 #include <cstdint>
 #include <vector>
 
@@ -178,6 +179,14 @@ __device__ __forceinline__ int chunk_of(int t, int m0, int nchunks)
 
 __device__ __forceinline__ bool tile_live(const JobDev& jb, int cond) { return !cond || rebuild_due(jb); }
 
+// output columns of a tile: TN, or 64 for the half-width last column tile of a
+// job whose remaining columns are at most 64 (tile.w == 64, only with TN = 128)
+template <int TN>
+__device__ __forceinline__ int tile_width(const int4& tile)
+{
+    return (TN == 128 && tile.w == 64) ? 64 : TN;
+}
+
 // One-hot B operand of the jobs due for a rebuild (blockIdx.y: entry of the
 // job list).  Thread u writes the 16-byte row rr of core matrix (row group G,
 // K group kc) of chunk c, u = ((c NG + G) 16 + kc) 8 + rr: element e is 1 when
@@ -286,11 +295,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* 
                     const int j0 = (m0 - c * kChunk) / 8 + 16 * nchunks - 16;  // first core matrix of the strip
                     const uint32_t st = smem_u32(smem + b * kStageBytes);
                     const uint32_t fb = smem_u32(full + b);
-                    mbar_expect_tx(fb, (uint32_t)kStageBytes);
+                    // a half-width tile (tile.w == 64) copies the first 64 rows of the B tile
+                    const uint32_t bbytes = tile_width<TN>(tile) * kChunk * 2;
+                    mbar_expect_tx(fb, (uint32_t)(kSplit * kTileBytes) + bbytes);
 #pragma unroll
                     for (int sp = 0; sp < kSplit; ++sp)
                         bulk_g2s(st + sp * kTileBytes, hank + sp * hank_part + (size_t)j0 * 128, kTileBytes, fb);
-                    bulk_g2s(st + kSplit * kTileBytes, xb + (size_t)c * xchunk, S::kTileBytesB, fb);
+                    bulk_g2s(st + kSplit * kTileBytes, xb + (size_t)c * xchunk, bbytes, fb);
                     ++issued;
                 }
             }
@@ -299,7 +310,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* 
     } else if (warp == 1) {
         // ---- MMAs: one thread issues the chunk's 24 MMAs and commits them
         if (lane == 0) {
-            const uint32_t idesc = make_idesc(kTileM, TN);
+            const uint32_t idesc_full = make_idesc(kTileM, TN), idesc_half = make_idesc(kTileM, 64);
             uint32_t used = 0, ntile = 0;
             for (int ti = blockIdx.x; ti < ntiles && failed_job < 0 && !*abort; ti += gridDim.x) {
                 const int4 tile = tiles[ti];
@@ -307,6 +318,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* 
                 if (!tile_live(jb, cond)) continue;
                 const int nchunks = (jb.L + kChunk - 1) / kChunk;
                 const int parts = jb.tc_parts;
+                const uint32_t idesc = tile_width<TN>(tile) == TN ? idesc_full : idesc_half;
                 // the accumulators of the previous tile have been read
                 if (ntile > 0 && !mbar_wait(smem_u32(tempty), (ntile - 1) & 1u, abort, 0, jb.tc_wait_ns)) {
                     failed_job = tile.x;
@@ -563,8 +575,18 @@ cudaError_t launch_fields_tc(const JobDev* jobs_dev, const int* idx, int njobs, 
 
 void tc_tiles(int job, int L, int q, int R, int tn, std::vector<int4>& out)
 {
+    // at TN = 128 a last column tile with at most 64 columns left runs at
+    // half width (w = 64): half the MMA work and B copies
+    const int N = q * R;
     for (int m = 0; m < L; m += kTileM)
-        for (int n = 0; n < q * R; n += tn) out.push_back(make_int4(job, m, n, 0));
+        for (int n = 0; n < N; n += tn) out.push_back(make_int4(job, m, n, tn == 128 && N - n <= 64 ? 64 : 0));
+}
+
+void tc_order_tiles(std::vector<int4>& tiles)
+{
+    // full-width tiles first: the persistent CTAs take tiles round-robin, so the
+    // half-width ones fill the last round
+    std::stable_partition(tiles.begin(), tiles.end(), [](const int4& t) { return t.w == 0; });
 }
 
 long long tc_tile_count(int L, int q, int R, int tn)
