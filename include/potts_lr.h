@@ -98,8 +98,9 @@ typedef struct {
     void* cuda_stream;   /* cudaStream_t to run on; NULL = a stream the handle creates */
     int sweep_variant;   /* 0 = automatic (default); FP32 mode: 1 = fields in shared or
                             global memory, 2 = fields in registers (EINVAL if the shape
-                            does not fit: L <= 1120, or L <= 4320 with q <= 8, L <= 7680
-                            with q <= 5, L <= 12480 with q <= 3, L <= 16800 with q = 2);
+                            does not fit: L <= 1120, or L <= 2400 with q <= 10, L <= 4320
+                            with q <= 8, L <= 7680 with q <= 5, L <= 12480 with q <= 3,
+                            L <= 16800 with q = 2);
                             either mode: 3 = fields in global memory even where they fit
                             in shared memory (FX64 mode: 0, 1, 2, 3 and 5; 2 = the FX64 fields
                             in registers, EINVAL unless L <= 448, or L <= 1120 with q <= 8,
@@ -115,14 +116,15 @@ typedef struct {
                             take more than 88 KB of it with R x C at most the SM
                             count); FP32 and FX64 modes: 6 = the slot's fields in the
                             registers of a cluster of 2, 4 or 8 CTAs (FP32: q <= 8, L <=
-                            4320 C; FX64: q <= 7, L <= 2400 C; the smallest C that holds
-                            them; EINVAL beyond L = 34560 or 19200; chosen by 0 where
+                            4320 C, or q <= 12, L <= 2400 C; FX64: q <= 7, L <= 2400 C;
+                            the smallest C that holds them; EINVAL beyond L = 34560 or
+                            19200; chosen by 0 where
                             no single CTA's registers hold the chain and this does,
                             before either shared-memory placement); FP32 mode:
                             16 + c (c = 1..8) = register
                             configuration c (E sites per update thread x update warps:
                             1x7, 2x7, 5x7, 5x15, 9x15, 16x15, 26x15, 35x15; q at most
-                            16, 16, 16, 8, 8, 5, 3, 2; EINVAL if L > 32 x E x warps or q
+                            16, 16, 16, 10, 8, 5, 3, 2; EINVAL if L > 32 x E x warps or q
                             too large); FX64 mode: 16 + c (c = 1..6) = FX64 register
                             configuration c (1x7, 2x7, 4x8, 5x7, 5x15, 9x15; q at most 16,
                             16, 8, 8, 5, 3).  All variants of a precision give identical

@@ -16,7 +16,7 @@ SOURCES = ["api.cu", "sweep.cu", "sweep_rf_a.cu", "sweep_rf_b.cu", "sweep_rf_c.c
            "sweep_rf_f.cu", "sweep_rf_g.cu", "sweep_rf_h.cu", "aux_kernels.cu", "rebuild_tc.cu", "probe.cu",
            "measure_static.cu", "sweep_sched.cu", "sweep_direct.cu", "sweep_rf_dispatch.cu", "sweep_cluster.cu",
            "sweep_rfx_a.cu", "sweep_rfx_b.cu", "sweep_rfx_c.cu", "sweep_rfx_d.cu", "sweep_rfx_e.cu", "sweep_rfx_f.cu",
-           "sweep_rfc_f.cu", "sweep_rfc_x.cu", "jstar.cpp"]
+           "sweep_rfc_f.cu", "sweep_rfc_fq.cu", "sweep_rfc_x.cu", "jstar.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr"] + ARCH

@@ -534,8 +534,9 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
     }
     if (o.sweep_variant == 2 && !j.rf) {
         potts_lr_destroy(h);
-        return fail(POTTS_LR_EINVAL, "register-resident sweep needs FP32 and L <= 1120, or L <= 4320 with q <= 8 "
-                                     "(7680 with q <= 5, 12480 with q <= 3, 16800 with q = 2), or FX64 and L <= 448, "
+        return fail(POTTS_LR_EINVAL, "register-resident sweep needs FP32 and L <= 1120, or L <= 2400 with q <= 10, "
+                                     "L <= 4320 with q <= 8 (7680 with q <= 5, 12480 with q <= 3, 16800 with q = 2), "
+                                     "or FX64 and L <= 448, "
                                      "or L <= 1120 with q <= 8 (2400 with q <= 5, 4320 with q <= 3)");
     }
     h->dj = (JobDev*)(base + o_job);
@@ -582,7 +583,8 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
         if (!C || rfc_smem_bytes(h->precision, q, C, L) > kSmemBudget) {
             potts_lr_destroy(h);
             return fail(POTTS_LR_EINVAL, "the register-resident cluster sweep holds FP32 chains of q <= 8 and L <= "
-                                         "34560, FX64 chains of q <= 7 and L <= 19200 (and more than 32 sites)");
+                                         "34560 or q <= 12 and L <= 19200, FX64 chains of q <= 7 and L <= 19200 (and "
+                                         "more than 32 sites)");
         }
         j.rc = C;
         j.rf = 0;

@@ -236,7 +236,8 @@ PLR_RFX_DECL(f)
 #undef PLR_RFX_DECL
 // Register-resident cluster sweep (sweep_rfc.cuh): a slot's fields in the
 // registers of a cluster of C = 2, 4 or 8 CTAs (FP32: 9 sites per update
-// thread, q <= 8, L <= 4320 C; FX64: 5 sites, q <= 7, L <= 2400 C).
+// thread, q <= 8, L <= 4320 C, or 5 sites, q <= 12, L <= 2400 C; FX64: 5
+// sites, q <= 7, L <= 2400 C).
 bool rfc_fits(int precision, int C, int L, int q);
 int rfc_cluster_for(int precision, int L, int q);  // smallest C that holds the chain (0: none)
 size_t rfc_smem_bytes(int precision, int q, int C, int L);
@@ -247,6 +248,9 @@ cudaError_t launch_sweep_rfc_f(int q, int C, const JobDev*, const int2*, int, in
 cudaError_t launch_sweep_rfc_x(int q, int C, const JobDev*, const int2*, int, int, size_t, const SweepSched*,
                                cudaStream_t);
 size_t sweep_rfc_smem_f(int q, int C, int L);
+cudaError_t launch_sweep_rfc_fq(int q, int C, const JobDev*, const int2*, int, int, size_t, const SweepSched*,
+                                cudaStream_t);
+size_t sweep_rfc_smem_fq(int q, int C, int L);
 size_t sweep_rfc_smem_x(int q, int C, int L);
 size_t sweep_rf_smem_a(int q, int L, int Lpad);
 size_t sweep_rf_smem_b(int q, int L, int Lpad);

@@ -8,7 +8,7 @@ namespace plr {
 namespace {
 // capacity of each register configuration: largest L (E x 32 x update warps) and q
 constexpr int kRfMaxL[9] = {0, 224, 448, 1120, 2400, 4320, 7680, 12480, 16800};
-constexpr int kRfMaxQ[9] = {0, 16, 16, 16, 8, 8, 5, 3, 2};
+constexpr int kRfMaxQ[9] = {0, 16, 16, 16, 10, 8, 5, 3, 2};
 // FX64 configurations 1..6: (E, NU) = (1, 7), (2, 7), (4, 8), (5, 7), (5, 15), (9, 15)
 constexpr int kRfxMaxL[7] = {0, 224, 448, 1024, 1120, 2400, 4320};
 constexpr int kRfxMaxQ[7] = {0, 16, 16, 8, 8, 5, 3};
@@ -109,7 +109,7 @@ bool rfc_fits(int precision, int C, int L, int q)
 {
     if (C != 2 && C != 4 && C != 8) return false;
     if (L <= kSiteBlock || q < 2) return false;  // at least two blocks of sites
-    if (precision == kPrecFP32) return q <= 8 && L <= C * 9 * 480;
+    if (precision == kPrecFP32) return q <= 8 ? L <= C * 9 * 480 : (q <= 12 && L <= C * 5 * 480);
     if (precision == kPrecFX64) return q <= 7 && L <= C * 5 * 480;
     return false;
 }
@@ -123,7 +123,7 @@ int rfc_cluster_for(int precision, int L, int q)
 
 size_t rfc_smem_bytes(int precision, int q, int C, int L)
 {
-    return precision == kPrecFP32   ? sweep_rfc_smem_f(q, C, L)
+    return precision == kPrecFP32   ? (q <= 8 ? sweep_rfc_smem_f(q, C, L) : sweep_rfc_smem_fq(q, C, L))
            : precision == kPrecFX64 ? sweep_rfc_smem_x(q, C, L)
                                     : 0;
 }
@@ -132,7 +132,9 @@ cudaError_t launch_sweep_rfc(int precision, int C, int q, const JobDev* jobs_dev
                              int nsweeps, size_t smem, const SweepSched* sched, cudaStream_t st)
 {
     if (nwork <= 0 || nsweeps <= 0) return cudaSuccess;
-    if (precision == kPrecFP32) return launch_sweep_rfc_f(q, C, jobs_dev, work, nwork, nsweeps, smem, sched, st);
+    if (precision == kPrecFP32)
+        return q <= 8 ? launch_sweep_rfc_f(q, C, jobs_dev, work, nwork, nsweeps, smem, sched, st)
+                      : launch_sweep_rfc_fq(q, C, jobs_dev, work, nwork, nsweeps, smem, sched, st);
     if (precision == kPrecFX64) return launch_sweep_rfc_x(q, C, jobs_dev, work, nwork, nsweeps, smem, sched, st);
     return cudaErrorNotSupported;
 }

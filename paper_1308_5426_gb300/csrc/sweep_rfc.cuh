@@ -351,18 +351,20 @@ cudaError_t launch_rfc(const JobDev* jobs_dev, const int2* work, int nwork, int 
     return cudaLaunchKernelEx(&cfg, k, jobs_dev, items, nsweeps);
 }
 
-// dispatch over Q (2..QMAX) and C (2, 4, 8) for one field type and E
-template <typename T, int E, int QMAX>
+// dispatch over Q (QMIN..QMAX, within 2..12) and C (2, 4, 8) for one field type and E
+template <typename T, int E, int QMIN, int QMAX>
 cudaError_t launch_rfc_qc(int q, int C, const JobDev* jobs_dev, const int2* work, int nwork, int nsweeps,
                           size_t smem, const SweepSched* sched, cudaStream_t st)
 {
     switch (q * 16 + C) {
-#define PLR_RFC(Qv, Cv)                                                                                     \
-    case Qv * 16 + Cv:                                                                                      \
-        if constexpr (Qv <= QMAX) return launch_rfc<T, Qv, E, Cv>(jobs_dev, work, nwork, nsweeps, smem, sched, st); \
+#define PLR_RFC(Qv, Cv)                                                                             \
+    case Qv * 16 + Cv:                                                                              \
+        if constexpr (Qv >= QMIN && Qv <= QMAX)                                                     \
+            return launch_rfc<T, Qv, E, Cv>(jobs_dev, work, nwork, nsweeps, smem, sched, st);        \
         break;
 #define PLR_RFC_Q(Qv) PLR_RFC(Qv, 2) PLR_RFC(Qv, 4) PLR_RFC(Qv, 8)
         PLR_RFC_Q(2) PLR_RFC_Q(3) PLR_RFC_Q(4) PLR_RFC_Q(5) PLR_RFC_Q(6) PLR_RFC_Q(7) PLR_RFC_Q(8)
+        PLR_RFC_Q(9) PLR_RFC_Q(10) PLR_RFC_Q(11) PLR_RFC_Q(12)
 #undef PLR_RFC_Q
 #undef PLR_RFC
     default: break;
@@ -370,14 +372,15 @@ cudaError_t launch_rfc_qc(int q, int C, const JobDev* jobs_dev, const int2* work
     return cudaErrorNotSupported;
 }
 
-template <typename T, int E, int QMAX>
+template <typename T, int E, int QMIN, int QMAX>
 size_t rfc_smem_q(int q, int C, int L)
 {
     switch (q * 16 + C) {
 #define PLR_RFC_S(Qv, Cv) \
-    case Qv * 16 + Cv: return Qv <= QMAX ? RfcLayout<T, Qv, E, Cv>(L).bytes : 0;
+    case Qv * 16 + Cv: return (Qv >= QMIN && Qv <= QMAX) ? RfcLayout<T, Qv, E, Cv>(L).bytes : 0;
 #define PLR_RFC_SQ(Qv) PLR_RFC_S(Qv, 2) PLR_RFC_S(Qv, 4) PLR_RFC_S(Qv, 8)
         PLR_RFC_SQ(2) PLR_RFC_SQ(3) PLR_RFC_SQ(4) PLR_RFC_SQ(5) PLR_RFC_SQ(6) PLR_RFC_SQ(7) PLR_RFC_SQ(8)
+        PLR_RFC_SQ(9) PLR_RFC_SQ(10) PLR_RFC_SQ(11) PLR_RFC_SQ(12)
 #undef PLR_RFC_SQ
 #undef PLR_RFC_S
     default: return 0;

@@ -7,9 +7,9 @@ namespace plr {
 cudaError_t launch_sweep_rfc_x(int q, int C, const JobDev* jobs_dev, const int2* work, int nwork, int nsweeps,
                                size_t smem, const SweepSched* sched, cudaStream_t st)
 {
-    return rfc::launch_rfc_qc<long long, 5, 7>(q, C, jobs_dev, work, nwork, nsweeps, smem, sched, st);
+    return rfc::launch_rfc_qc<long long, 5, 2, 7>(q, C, jobs_dev, work, nwork, nsweeps, smem, sched, st);
 }
 
-size_t sweep_rfc_smem_x(int q, int C, int L) { return rfc::rfc_smem_q<long long, 5, 7>(q, C, L); }
+size_t sweep_rfc_smem_x(int q, int C, int L) { return rfc::rfc_smem_q<long long, 5, 2, 7>(q, C, L); }
 
 }  // namespace plr

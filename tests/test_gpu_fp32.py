@@ -158,7 +158,7 @@ def test_fp32_and_fp64_sample_the_same_observables(plr):
     (65, 4, 0.5, 4), (96, 3, 0.6, 3), (200, 3, 0.5, 4), (256, 16, 0.3, 3), (500, 5, 0.7, 5), (500, 11, 0.7, 3),
     (1000, 16, 0.4, 3), (1024, 5, 0.4, 8), (1536, 7, 0.5, 3), (2048, 8, 0.6, 3), (1999, 2, 0.2, 4),
     (4096, 8, 0.2, 3), (4224, 3, 0.3, 2), (3000, 6, 0.9, 2), (6000, 5, 0.4, 2), (10000, 3, 0.2, 2),
-    (16000, 2, 0.6, 2),
+    (16000, 2, 0.6, 2), (2000, 10, 0.5, 3), (2400, 9, 0.3, 2),
 ])
 def test_register_path_equals_memory_path(plr, L, q, sigma, R):
     """The register-resident FP32 sweep and the shared/global-memory FP32 sweep
@@ -180,7 +180,7 @@ def test_register_path_equals_memory_path(plr, L, q, sigma, R):
     np.testing.assert_array_equal(a.stats()["acc_flip"], b.stats()["acc_flip"])
 
 
-@pytest.mark.parametrize("L,q", [(8192, 10), (4400, 6), (2048, 9), (8000, 4), (13000, 3), (17000, 2)])
+@pytest.mark.parametrize("L,q", [(8192, 10), (4400, 6), (2048, 11), (2500, 9), (8000, 4), (13000, 3), (17000, 2)])
 def test_register_path_rejects_unsupported_shapes(plr, L, q):
     temps = np.linspace(1.0, 2.0, 2)
     with pytest.raises(plr.PottsError):
@@ -251,6 +251,9 @@ def test_cluster_sweep_equals_global_sweep(plr, precision, L, q, sigma, R, round
     ("fp32", 10001, 3, 0.3, 2, 3),    # four CTAs, ragged last block
     ("fp32", 16384, 5, 0.4, 2, 2),    # four CTAs (the long serving shape)
     ("fp32", 20000, 8, 0.6, 2, 2),    # eight CTAs, the last one part empty
+    ("fp32", 4000, 10, 0.5, 2, 4),    # q = 9..12 (five sites per thread): two CTAs
+    ("fp32", 9000, 12, 0.4, 2, 3),    # four CTAs, ragged last block
+    ("fp32", 16384, 9, 0.7, 2, 2),    # eight CTAs
     ("fx64", 1000, 7, 0.5, 3, 8),     # FX64: two CTAs
     ("fx64", 9000, 5, 0.4, 2, 3),     # four CTAs
     ("fx64", 16384, 3, 0.3, 2, 2),    # eight CTAs
