@@ -241,11 +241,15 @@ int potts_lr_near_log(potts_lr_t* h, int32_t* events, int cap, int* n);
 int potts_lr_set_wait_limits(potts_lr_t* h, uint64_t rebuild_ns, uint64_t plan_ns);
 
 /* FP32 mode: how many BF16 parts of J* the tensor-core rebuild multiplies
- * (the paper has no counterpart): 3 (hi + mid + lo, the default,
- * representation error about 2^-25 of each coupling) or 2 (hi + mid, about
- * 2^-17, two thirds of the tensor-core work).  Applies to the handle's own
+ * (the paper has no counterpart): 3 (hi + mid + lo, representation error
+ * about 2^-25 of each coupling), 2 (hi + mid, about 2^-17, two thirds of the
+ * tensor-core work) or 0 (the default: 2 while the automatic schedule rebuilds
+ * every sweep, where the sweep's drift is an order of magnitude larger than
+ * the split's error, else 3).  Applies to the handle's own
  * rebuilds and to batches created afterwards.  EINVAL for a NULL handle, a
- * job not in FP32 mode, or parts other than 2 and 3.  Synchronises. */
+ * job not in FP32 mode, or parts other than 0, 2 and 3.  Synchronises.
+ * (Scheduled rebuilds re-anchor the running energy from the spins once at
+ * least 8 sweeps have passed since the last anchor; explicit ones always.) */
 int potts_lr_set_rebuild_split(potts_lr_t* h, int parts);
 
 /* FP32 mode's rebuild schedule (any argument may be NULL): *interval = the

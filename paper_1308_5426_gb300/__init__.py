@@ -192,7 +192,8 @@ class Job:
                 "smem_bytes": int(v[6])}
 
     def set_rebuild_split(self, parts):
-        """FP32: BF16 parts of J* in the tensor-core rebuild, 3 (default) or 2."""
+        """FP32: BF16 parts of J* in the tensor-core rebuild: 3, 2, or 0 (default:
+        2 while scheduled rebuilds come every sweep, else 3)."""
         _lib.check(self._lib.potts_lr_set_rebuild_split(self._h, int(parts)))
 
     def rebuild_info(self):

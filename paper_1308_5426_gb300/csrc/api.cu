@@ -500,7 +500,7 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
     h->onehot_blocks = tc_onehot_blocks(L, q, R);
     j.status = (int*)(base + o_status);
     j.tc_wait_ns = kTcWaitNs;
-    j.tc_parts = 3;
+    j.tc_parts = 0;  // automatic (rebuild_parts)
     j.sched = (int*)(base + o_sched);
     h->dtiles = (int4*)(base + o_tiles);
     h->ntiles = (int)tiles.size();
@@ -916,7 +916,7 @@ int potts_lr_set_rebuild_split(potts_lr_t* h, int parts)
 {
     if (!h) return fail(POTTS_LR_EINVAL, "handle is NULL");
     if (h->precision != POTTS_LR_FP32) return fail(POTTS_LR_EINVAL, "the split-BF16 rebuild is FP32 mode's");
-    if (parts != 2 && parts != 3) return fail(POTTS_LR_EINVAL, "parts must be 2 or 3");
+    if (parts != 0 && parts != 2 && parts != 3) return fail(POTTS_LR_EINVAL, "parts must be 0, 2 or 3");
     h->hj.tc_parts = parts;
     PLR_CUDA(cudaMemcpyAsync(h->dj, &h->hj, sizeof(JobDev), cudaMemcpyHostToDevice, h->stream));
     PLR_CUDA(cudaStreamSynchronize(h->stream));

@@ -54,6 +54,7 @@ __global__ void __launch_bounds__(kAuxThreads) measure_kernel(const JobDev* __re
     const JobDev& jb = jobs[wk.x];
     const int np = jb.meas_parts;
     if (part >= np || (cond && !rebuild_due(jb))) return;
+    if (anchor && cond && !anchor_due(jb)) return;  // a scheduled rebuild between energy anchors
     const int t = wk.y;
     const int rep = jb.map[t];
     const int L = jb.L, tid = threadIdx.x;
@@ -217,6 +218,7 @@ __global__ void rebuild_policy_kernel(const JobDev* __restrict__ jobs, const int
     int k = jb.sched[0];
     if (d > kDriftHigh) k = max(1, k / 2);
     else if (d < kDriftLow) k = min(max(jb.recompute_every, 1), 2 * k);
+    if (!cond || anchor_due(jb)) jb.sched[3] = (int)jb.nsweep[0];  // this rebuild re-anchored the energy
     jb.sched[0] = k;
     jb.sched[1] = (int)(jb.nsweep[0] + (uint32_t)k);
     jb.sched[2] += 1;                    // rebuilds done

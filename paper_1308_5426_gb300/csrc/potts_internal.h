@@ -69,10 +69,11 @@ struct JobDev {
     int* status;                   // 0 ok; 1 a bounded device wait expired
     unsigned long long tc_wait_ns; // bound of each pipeline wait of the tensor-core rebuild (kTcWaitNs)
     int* sched;                    // FP32 rebuild schedule: [0] current interval k, [1] sweep of the next rebuild,
-                                   // [2] rebuilds done (policy updates)
+                                   // [2] rebuilds done (policy updates), [3] sweep of the last energy anchor
     unsigned long long* drift_bits;  // max |h_before - h_rebuilt| / Jtot (double bits): [0] of the rebuild
                                      // running now, [1] of the last completed one
-    int tc_parts;                  // BF16 parts of J* the rebuild multiplies: 3 (hi, mid, lo; default) or 2
+    int tc_parts;                  // BF16 parts of J* the rebuild multiplies: 3 (hi, mid, lo), 2 (hi, mid) or
+                                   // 0 = automatic (default; rebuild_parts)
 };
 
 // FP32 drift control: after each rebuild the measured drift d of the period
@@ -85,6 +86,32 @@ constexpr double kDriftLow = 3.5e-6;
 __device__ __forceinline__ bool rebuild_due(const JobDev& jb)
 {
     return jb.recompute_every > 0 && jb.nsweep[0] >= (uint32_t)jb.sched[1];
+}
+
+// The exact energy that re-anchors the running FP32 energy at a scheduled
+// rebuild is taken once at least kAnchorSweeps sweeps have passed since the
+// last one: long chains rebuild every sweep or two, and the O(L^2) energy
+// costs a quarter of their rebuild.  In between, the running energy carries
+// the FP32 fields' error in the energy changes it sums (measured about 3e-5
+// of Jtot per sweep, so at most about 2.4e-4 Jtot; in the exchange exponent
+// that is the size of the FP32 Metropolis decisions' own error).  Explicit
+// rebuilds always re-anchor.  The policy kernel, which runs after the
+// measurement, moves sched[3].
+constexpr int kAnchorSweeps = 8;
+__device__ __forceinline__ bool anchor_due(const JobDev& jb)
+{
+    return jb.nsweep[0] - (uint32_t)jb.sched[3] >= (uint32_t)kAnchorSweeps;
+}
+
+// BF16 parts of a rebuild: as set, or automatically two where scheduled
+// rebuilds come every sweep (there the sweep's own drift, 4e-6 to 9e-6 of Jtot,
+// dwarfs the two-part split's 3e-7, and the interval cannot shrink further)
+// and three elsewhere (at longer intervals the split's error would enter the
+// measured drift that lets the interval grow)
+__device__ __forceinline__ int rebuild_parts(const JobDev& jb)
+{
+    if (jb.tc_parts) return jb.tc_parts;
+    return (jb.recompute_every > 0 && jb.sched[0] <= 1) ? 2 : 3;
 }
 
 // Placement of the work items of one sweep launch on the SMs.  The field

@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* 
                 const JobDev& jb = jobs[tile.x];
                 if (!tile_live(jb, cond)) continue;
                 const int nchunks = (jb.L + kChunk - 1) / kChunk;
-                const int parts = jb.tc_parts;
+                const int parts = rebuild_parts(jb);
                 const uint32_t idesc = tile_width<TN>(tile) == TN ? idesc_full : idesc_half;
                 // the accumulators of the previous tile have been read
                 if (ntile > 0 && !mbar_wait(smem_u32(tempty), (ntile - 1) & 1u, abort, 0, jb.tc_wait_ns)) {

@@ -46,11 +46,10 @@ def test_tensor_core_rebuild_accuracy(plr, L, q, R, sigma):
 
 @pytest.mark.parametrize("L,q,R,sigma", [(4096, 8, 128, 0.2), (16384, 5, 64, 0.4), (1024, 5, 64, 0.4)])
 def test_rebuild_split_two_and_three_parts(plr, L, q, R, sigma):
-    """The split of J* into BF16 parts: three (hi + mid + lo, the default) and
-    two (hi + mid) both rebuild within the 1e-5 Jtot bound; three parts are
-    measured several times more accurate (on GB300: 2e-8..1.1e-7 against
-    2.8e-7..5.9e-7 Jtot) at no measured extra time, which is why they are the
-    default."""
+    """The split of J* into BF16 parts: three (hi + mid + lo) and two (hi +
+    mid) both rebuild within the 1e-5 Jtot bound; three parts are measured
+    several times more accurate (on GB300: 2e-8..1.1e-7 against 2.8e-7..9.6e-7
+    Jtot), which is why explicit rebuilds and slow schedules use them."""
     temps = workloads.geometric_ratios(R, 0.05, 1.0) * oracle.jtot(L, sigma)
     err = {}
     for parts in (3, 2):
@@ -63,6 +62,37 @@ def test_rebuild_split_two_and_three_parts(plr, L, q, R, sigma):
     print("L=%d q=%d: rebuild error, 3 parts %.3e, 2 parts %.3e Jtot" % (L, q, err[3], err[2]))
     assert err[3] < 2e-7 and err[2] < 1e-6
     assert err[3] < err[2]
+
+
+def test_automatic_split_and_energy_anchor_on_fast_schedules(plr):
+    """With rebuilds every sweep (K = 1) the automatic split is the two-part
+    one (identical to asking for it, unlike three parts), and the running
+    energy, re-anchored from the spins every 8 sweeps, carries the FP32
+    fields' error in between (measured about 3e-5 Jtot per sweep; bounded here
+    by 1e-3 Jtot); an explicit rebuild re-anchors it at once."""
+    L, q, sigma, R = 4096, 5, 0.4, 8
+    temps = workloads.geometric_ratios(R, 0.05, 1.0) * oracle.jtot(L, sigma)
+    jobs = {}
+    for name, parts in (("auto", None), ("two", 2), ("three", 3)):
+        j = plr.Job(L, q, sigma, temps, 11, precision="fp32", recompute_every=1)
+        if parts is not None:
+            j.set_rebuild_split(parts)
+        for _ in range(13):
+            j.sweep(1)
+            j.exchange()
+        jobs[name] = j
+    np.testing.assert_array_equal(jobs["auto"].fields(), jobs["two"].fields())
+    np.testing.assert_array_equal(jobs["auto"].spins(), jobs["two"].spins())
+    assert not np.array_equal(jobs["auto"].fields(), jobs["three"].fields())
+    j = jobs["auto"]
+    assert j.fields_error() < DRIFT_BOUND
+    E, _ = j.measure()
+    np.testing.assert_allclose(j.running_energy(), E, rtol=0, atol=1e-3 * oracle.jtot(L, sigma))
+    j.fields_recompute()
+    E, _ = j.measure()
+    np.testing.assert_allclose(j.running_energy(), E, rtol=1e-12)
+    for j in jobs.values():
+        j.close()
 
 
 def test_rebuild_schedule_is_reported(plr):
