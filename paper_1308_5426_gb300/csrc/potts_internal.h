@@ -215,7 +215,8 @@ cudaError_t launch_sweep_cluster(int C, int precision, const JobDev* jobs_dev, c
 
 // Register-resident FP32 sweep (sweep_rf.cuh): configuration 1..8 =
 // (E sites per update thread, update warps) = (1, 7), (2, 7), (5, 7) for
-// L <= 224, 448, 1120; (5, 15), (9, 15) with q <= 8 for L <= 2400, 4320;
+// L <= 224, 448, 1120; (5, 15) with q <= 10 for L <= 2400; (9, 15) with
+// q <= 8 for L <= 4320;
 // (16, 15) with q <= 5 for L <= 7680; (26, 15) with q <= 3 for L <= 12480;
 // (35, 15) with q = 2 for L <= 16800; 0 if the shape does not fit in registers.
 int rf_config(int L, int q);

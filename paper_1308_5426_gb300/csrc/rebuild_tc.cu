@@ -22,9 +22,9 @@
 // - B: a one-hot kernel writes X before the rebuild, per chunk and 8-row group
 //   the 16 core matrices of the chunk's K groups (2 KB); a TN-row tile of a
 //   chunk is one contiguous copy of TN x 256 bytes.
-// Warp 0 issues the copies into a ring of stages (3 or 4), warp 1 issues the
-// 24 MMAs of each chunk (8 K-steps x 3 parts) and commits them to the stage's
-// "empty" barrier, warps 2..9 read the accumulators.  The FP32 accumulation
+// Warp 0 issues the copies into a ring of stages (4 or 7), warp 1 issues the
+// MMAs of each chunk part by part (8 K-steps each, 2 or 3 parts) and commits
+// them to the stage's "empty" barrier, warps 2..9 read the accumulators.  The FP32 accumulation
 // rounds every MMA's sum into the accumulator, so the chains are kept short:
 // the hi parts of successive chunks rotate over 512 / TN - 1 accumulators
 // (seven or three), and the small mid + lo parts go to one of their own
@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) fields_tc_kernel(const JobDev* 
         }
         __syncwarp();
     } else if (warp == 1) {
-        // ---- MMAs: one thread issues the chunk's 24 MMAs and commits them
+        // ---- MMAs: one thread issues the chunk's MMAs (8 K-steps x 2 or 3 parts) and commits them
         if (lane == 0) {
             const uint32_t idesc_full = make_idesc(kTileM, TN), idesc_half = make_idesc(kTileM, 64);
             uint32_t used = 0, ntile = 0;
