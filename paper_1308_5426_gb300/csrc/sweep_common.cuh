@@ -189,11 +189,14 @@ __device__ __forceinline__ int decide_block(int lane, int nv, int k, int L, int 
             else st = (d32 <= 0.0f || cb32 * d32 < nlu) ? kAccept : kReject;
         }
         const unsigned hit = __ballot_sync(kFullMask, st != kReject);
+        // FP64 rule: the lanes the FP32 screen left unsure, from a ballot beside
+        // the first (a bit test of lane j, no shuffle on the round's chain)
+        const unsigned unsure = kFP64 ? __ballot_sync(kFullMask, st == kUnsure) : 0u;
         if (!hit) break;
         const int j = __ffs(hit) - 1;
         bool acc = true;
         if constexpr (kFP64) {
-            if (__shfl_sync(kFullMask, st, j) == kUnsure) {
+            if ((unsure >> j) & 1u) {
                 // rare: lane j applies the FP64 rule to the FP64 difference, rebuilt
                 // from the previous block's flips and this block's accepted ones
                 const unsigned before = accmask & ((1u << j) - 1u);
