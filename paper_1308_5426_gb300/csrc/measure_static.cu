@@ -104,7 +104,7 @@ extern "C" int potts_lr_measure_static(const uint32_t* spins, int L, int q, int 
     }
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const int W = (L + 7) / 8;
-    const size_t smem = measure_smem_bytes(L, q);
+    const size_t smem = measure_smem_bytes(L, q);  // at most 32 KB for L <= 65536 (one tile's window)
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(measure_static_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)

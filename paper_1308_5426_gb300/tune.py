@@ -1,7 +1,8 @@
 """Autotuner of the sweep kernel's shape: for a job shape (L, q, precision) it
 times every sweep variant that can hold it -- fields in shared memory, in
-global memory, shared by a cluster of CTAs (FP32), and each register
-configuration (E sites per update thread x update warps; FP32 and FX64) --
+global memory, in the shared memory of a cluster of CTAs, in the registers of
+a cluster (FP32 and FX64), and each single-CTA register configuration (E sites
+per update thread x update warps; FP32 and FX64) --
 on this GPU and keeps the fastest.
 
 All variants give bit-identical results, so the choice affects speed only.
@@ -27,10 +28,10 @@ def candidates(L, q, precision):
     those that do not; the tuner skips them)."""
     regs = [v for v in SWEEP_VARIANTS if v.startswith("registers") and v != "registers"]
     if precision == "fp64":
-        return ["memory", "global"]
+        return ["memory", "global", "cluster"]
     if precision == "fx64":
-        return ["memory", "global"] + regs[:6]  # FX64 register configurations 1..6
-    return ["memory", "global", "cluster"] + regs
+        return ["memory", "global", "cluster", "rcluster"] + regs[:6]  # FX64 register configurations 1..6
+    return ["memory", "global", "cluster", "rcluster"] + regs
 
 
 def _time_variant(L, q, sigma, temps, variant, precision, sweeps, warm, torch):

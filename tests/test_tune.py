@@ -19,10 +19,11 @@ def test_variant_codes():
 
 
 def test_candidates():
-    assert candidates(1000, 5, "fp64") == ["memory", "global"]
+    assert candidates(1000, 5, "fp64") == ["memory", "global", "cluster"]
     c = candidates(1000, 5, "fp32")
-    assert c[:3] == ["memory", "global", "cluster"] and c[3:] == ["registers%d" % k for k in range(1, 9)]
-    assert candidates(1000, 5, "fx64") == ["memory", "global"] + ["registers%d" % k for k in range(1, 7)]
+    assert c[:4] == ["memory", "global", "cluster", "rcluster"] and c[4:] == ["registers%d" % k for k in range(1, 9)]
+    assert candidates(1000, 5, "fx64") == ["memory", "global", "cluster", "rcluster"] + [
+        "registers%d" % k for k in range(1, 7)]
 
 
 @pytest.fixture(scope="module")
@@ -67,3 +68,16 @@ def test_tuner_picks_a_valid_fastest_variant(plr, tmp_path):
     assert {"memory", "global", "registers3"} <= set(ms)  # registers1/2 cannot hold L = 1024
     assert "registers1" not in ms
     assert tune.tune(1024, 5, precision="fp32", cache_file=f)[0] == best  # cached
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", ["fp32", "fx64"])
+def test_tuner_times_the_cluster_sweeps_on_long_chains(plr, precision):
+    """At L = 8192 no single CTA's registers hold a slot: the tuner times the
+    global-memory sweep and both cluster sweeps (shared memory and registers of
+    a cluster of CTAs) and picks the fastest of those it timed."""
+    from paper_1308_5426_gb300 import tune
+    best, ms = tune.tune(8192, 5, sigma=0.5, precision=precision, R=8, sweeps=2, warm=1)
+    assert {"global", "cluster", "rcluster"} <= set(ms)
+    assert not any(v.startswith("registers") for v in ms)
+    assert best in ms and ms[best] == min(ms.values())

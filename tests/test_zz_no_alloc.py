@@ -62,10 +62,10 @@ def test_measure_static_matches_measure():
 
 
 def test_measure_static_long_chain_pair_once_against_oracle():
-    """L = 25001 (a ragged last word, and more than 48 KB of dynamic shared
-    memory, so the opt-in attribute is set) with c = 1: energies equal the
-    oracle's plain O(L^2) double sum to 1e-10 and magnetisations to 1e-14, on
-    two calls in a row."""
+    """L = 25001 (a ragged last word; 7 distance tiles x 4 word tiles, so the
+    tile sum of one slot spans many window loads) with c = 1: energies equal
+    the oracle's plain O(L^2) double sum to 1e-10 and magnetisations to 1e-14,
+    on two calls in a row."""
     import __graft_entry__
     __graft_entry__.build()
     torch = pytest.importorskip("torch")
