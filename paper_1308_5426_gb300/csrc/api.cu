@@ -98,6 +98,7 @@ struct potts_lr {
     SweepSched sched;             // placement of the R slots on the SMs
     bool direct;                  // sweeps by the direct O(L) sum: fields are rebuilt on demand
     bool cl_auto;                 // the cluster sweep was chosen automatically (not asked for)
+    int cl_min;                   // the smallest cluster whose shares fit (j.cl may be larger)
     size_t state_off, state_len;  // the checkpointed arrays: one block of the arena
 };
 
@@ -574,8 +575,18 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
                             kSmemBudget);
             }
             j.cl = C;
+            h->cl_min = C;
             h->cl_auto = o.sweep_variant == 0;
-            h->sweep_smem = cluster_sweep_smem(L, q, C, h->precision);
+            // FP64 and FX64 chosen automatically: a larger cluster while the
+            // job's CTAs still fit four per SM.  A hot slot's rank-1 updates
+            // (8-byte adds) then spread over more SMs; they set the sweep's
+            // length on a ladder with slots above the transition (measured at
+            // equilibrium, L = 4096, q = 8, R = 128: FP64 4.78 ms per sweep
+            // with 2 CTAs, 2.69 with 4, 3.65 with 8; FX64 1.82, 1.49, 3.32;
+            // L = 16384, q = 5, R = 64, FP64: 34.9 ms with 4, 29.5 with 8).
+            if (h->cl_auto && !fp32)
+                while (j.cl < 8 && (long long)R * 2 * j.cl <= 4LL * std::max(1, device_sm_count())) j.cl *= 2;
+            h->sweep_smem = cluster_sweep_smem(L, q, j.cl, h->precision);
         }
     }
     if (o.sweep_variant == 6) {  // the slot's fields in the registers of a cluster of CTAs
@@ -1023,7 +1034,8 @@ int potts_lr_batch_create(potts_lr_t* const* jobs, int n, void* cuda_stream, pot
     // throughput, not by the latency of single slots: there jobs that took the
     // cluster sweep automatically although their fields fit one CTA's shared
     // memory sweep with one CTA per slot (measured: about even per SM, and
-    // fewer CTAs; identical results either way).
+    // fewer CTAs; identical results either way), and automatic clusters larger
+    // than their fields need go back to the smallest.
     long long total_slots = 0;
     for (int i = 0; i < n; ++i) total_slots += jobs[i]->R;
     const bool crowded = total_slots > 16LL * std::max(1, device_sm_count());
@@ -1035,6 +1047,10 @@ int potts_lr_batch_create(potts_lr_t* const* jobs, int n, void* cuda_stream, pot
             hjobs[i].cl = 0;
             key = jobs[i]->precision * 4 + 2 + jobs[i]->hj.j_smem;
             sm = sweep_smem_bytes(hjobs[i]);
+        } else if (crowded && jobs[i]->cl_auto && jobs[i]->hj.cl > jobs[i]->cl_min) {
+            hjobs[i].cl = jobs[i]->cl_min;
+            key = kClusterKey + 16 * jobs[i]->precision + jobs[i]->cl_min;
+            sm = cluster_sweep_smem(jobs[i]->L, jobs[i]->q, jobs[i]->cl_min, jobs[i]->precision);
         }
         for (int t = 0; t < jobs[i]->R; ++t) works[key].push_back(make_int2(i, t));
         smem[key] = std::max(smem[key], sm);

@@ -171,3 +171,33 @@ def test_crowded_batch_equals_alone(plr):
     b.close()
     for j in alone + batched:
         j.close()
+
+
+def test_crowded_batch_takes_the_smallest_automatic_cluster(plr):
+    """An FP64 job whose automatic cluster is larger than its fields need
+    (L = 4096, q = 8, R = 3: 8 CTAs alone, 2 needed) sweeps on the smallest
+    cluster inside a batch of more than 16 slots per SM (filled with small FP32
+    jobs); its spins, fields and energies equal the job run alone."""
+    import torch
+    nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    L, q, sigma, R = 4096, 8, 0.2, 3
+    temps = workloads.geometric_ratios(R, 0.05, 1.0) * oracle.jtot(L, sigma)
+    alone = plr.Job(L, q, sigma, temps, 41, precision="fp64")
+    assert alone.sweep_info()["cluster"] > plr.Job(L, q, sigma, temps, 41, precision="fp64",
+                                                   sweep_variant="cluster").sweep_info()["cluster"]
+    for _ in range(3):
+        alone.sweep(1)
+        alone.exchange()
+    nsmall = (16 * nsm) // 64 + 1
+    small_temps = workloads.geometric_ratios(64, 0.05, 1.0) * oracle.jtot(64, 0.5)
+    small = [plr.Job(64, 2, 0.5, small_temps, 300 + i, precision="fp32", recompute_every=0) for i in range(nsmall)]
+    big = plr.Job(L, q, sigma, temps, 41, precision="fp64")
+    b = plr.Batch([big] + small)
+    b.run(3, 3)
+    b.sync()
+    np.testing.assert_array_equal(alone.spins(), big.spins())
+    np.testing.assert_array_equal(alone.fields(), big.fields())
+    np.testing.assert_array_equal(alone.running_energy(), big.running_energy())
+    b.close()
+    for j in [alone, big] + small:
+        j.close()

@@ -46,7 +46,7 @@ LONG_SPECS = [  # L, q, sigma, R, sweeps, arrival, precision: requests that take
     (8192, 3, 0.6, 5, 15, 0.00, "fp32"),    # one CTA's registers (26 sites per thread)
     (10000, 16, 0.5, 3, 10, 0.02, "fp32"),  # q > 12: the shared memory of a cluster
     (9000, 5, 0.3, 3, 10, 0.03, "fx64"),    # FX64 fields in the registers of a 4-CTA cluster
-    (6000, 5, 0.7, 3, 8, 0.04, "fp64"),     # FP64 fields in the shared memory of a 2-CTA cluster
+    (6000, 5, 0.7, 3, 8, 0.04, "fp64"),     # FP64 fields in the shared memory of a cluster (2 CTAs needed)
 ]
 
 
