@@ -473,13 +473,15 @@ def timed_e2e(plr, torch, specs, steps, warmup, dev):
             "d2h_bytes_per_step": d2h}
 
 
-def per_job_rates(plr, torch, dev, reqs, precision, min_seconds=0.25, max_sweeps=200):
+def per_job_rates(plr, torch, dev, reqs, precision, min_seconds=0.25, max_sweeps=200, warm_sweeps=30,
+                  warm_seconds=1.0):
     """Each request's shape as a plain job of the given precision, alone on the
-    GPU (the per-job path), from its random start: one sweep + exchange of
-    warm-up, then as many timed sweeps + exchanges as take about min_seconds
-    (CUDA events on the job's stream, at least two).  Returns the attempts a
-    request asks for, the time the per-job path needs for all of them at its
-    sampled rate, and the samples."""
+    GPU (the per-job path), from its random start: warm-up sweeps + exchanges
+    past the quench from random spins (warm_sweeps, or fewer where they would
+    take more than about warm_seconds), then as many timed sweeps + exchanges
+    as take about min_seconds (CUDA events on the job's stream, at least two).
+    Returns the attempts a request asks for, the time the per-job path needs
+    for all of them at its sampled rate, and the samples."""
     st = torch.cuda.Stream(device=dev)
     total_att, total_s, rows = 0, 0.0, []
     for r in reqs:
@@ -491,6 +493,15 @@ def per_job_rates(plr, torch, dev, reqs, precision, min_seconds=0.25, max_sweeps
         e1.record(st)
         e1.synchronize()
         first = max(e0.elapsed_time(e1) / 1e3, 1e-6)
+        nwarm = max(0, min(warm_sweeps, int(warm_seconds / first)) - 1)
+        e0.record(st)
+        for _ in range(nwarm):
+            j.sweep(1)
+            j.exchange()
+        e1.record(st)
+        e1.synchronize()
+        if nwarm:
+            first = max(e0.elapsed_time(e1) / 1e3 / nwarm, 1e-6)
         n = max(2, min(max_sweeps, int(min_seconds / first)))
         e0.record(st)
         for _ in range(n):
@@ -500,7 +511,8 @@ def per_job_rates(plr, torch, dev, reqs, precision, min_seconds=0.25, max_sweeps
         e1.synchronize()
         dt = e0.elapsed_time(e1) / 1e3
         rate = n * r.L * r.R / dt
-        rows.append({"L": r.L, "q": r.q, "sigma": round(r.sigma, 4), "sampled_sweeps": n, "attempts_per_s": rate,
+        rows.append({"L": r.L, "q": r.q, "sigma": round(r.sigma, 4), "warm_sweeps": nwarm + 1, "sampled_sweeps": n,
+                     "attempts_per_s": rate,
                      "kernel": kernel_label(j.sweep_info(), precision)})
         total_att += r.attempts
         total_s += r.attempts / rate
@@ -609,8 +621,8 @@ def serving_run(plr, torch, dev, njobs, sweeps, budget_bytes):
             "rebuild_share_by_shape": shares,
             "fp64_per_job_attempts_per_s": att64 / t64,
             "fp64_per_job": "every request's shape as a plain FP64 job alone on the GPU, rate sampled over >= 0.25 s "
-                            "after one warm-up sweep; the full %d sweeps of all %d requests would take %.0f s at "
-                            "those rates" % (sweeps, len(reqs), t64),
+                            "after up to 30 warm-up sweeps (about 1 s at most) from random spins; the full %d sweeps "
+                            "of all %d requests would take %.0f s at those rates" % (sweeps, len(reqs), t64),
             "fp64_per_job_samples": rows64,
             "fx64_per_job_attempts_per_s": attx / tx, "fx64_per_job_samples": rowsx,
             "served_fp32_over_fp64_per_job": served / (att64 / t64),

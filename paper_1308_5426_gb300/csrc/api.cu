@@ -41,7 +41,8 @@ int cuda_fail(cudaError_t e, const char* where)
     } while (0)
 
 constexpr size_t kSmemBudget = 220 * 1024;  // dynamic shared memory a sweep CTA may take
-constexpr size_t kClusterFieldBytes = 88 * 1024;  // FP32 fields above this go to a cluster (see create)
+constexpr size_t kClusterFieldBytes = 88 * 1024;   // FP32 fields above this go to a cluster (see create)
+constexpr size_t kClusterFieldBytes8 = 64 * 1024;  // FP64 and FX64 fields above this (see create)
 constexpr uint32_t kStateMagic = 0x31524c50u; // "PLR1"
 constexpr uint32_t kStateVersion = 4;          // header + the job's checkpoint block
 
@@ -545,13 +546,15 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
     h->sweep_smem = !j.rf                              ? sweep_smem_bytes(j)
                     : h->precision == POTTS_LR_FX64 ? rfx_smem_bytes(j.rf, q, L, h->Lpad)
                                                     : rf_smem_bytes(j.rf, q, L, h->Lpad);
-    // FP32 fields that fit no registers: a cluster of CTAs shares them when
-    // they fit no single CTA's shared memory, or fill most of one (then one
-    // CTA per SM sweeps the slot with few update warps) while the job's
-    // clusters fit on the GPU at once (measured: 2-2.6x faster at 64 slots;
-    // on a GPU already filled by many jobs' slots, about even); or when asked
-    // for (variant 5).  FP64 and FX64 fields take a cluster when they fit no
-    // single CTA's shared memory.
+    // Fields that fit no registers: a cluster of CTAs shares them when they
+    // fit no single CTA's shared memory, or when they are large (FP32: fill
+    // most of one CTA, which then sweeps the slot alone with few update warps;
+    // FP64, FX64: more than 64 KB, so that a hot slot's 8-byte updates keep
+    // one SM busy) while the job's clusters fit on the GPU at once; or when
+    // asked for (variant 5).  Measured, one job of 64 slots: FP32 2-2.6x
+    // faster; FP64 at equilibrium L = 2048, q = 5 2.13 -> 0.85 ms per sweep,
+    // L = 4096, q = 5 7.96 -> 2.36, L = 8192, q = 3 29.6 -> 5.37; on a GPU
+    // already filled by many jobs' slots about even (see the batch rule).
     // First, FP32 and FX64 chains that no single CTA's registers hold go to the
     // registers of a cluster where one holds them (measured on GB300 2-3x
     // faster than the shared-memory cluster: L = 16384, q = 5, R = 64, FP32
@@ -566,9 +569,10 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
     if (!j.rf && !j.rc && (o.sweep_variant == 0 || o.sweep_variant == 5)) {
         const int C = cluster_size_for(L, q, kSmemBudget, h->precision);
         const bool fp32 = h->precision == POTTS_LR_FP32;
-        const bool big = (size_t)q * h->Lpad * 4 > kClusterFieldBytes;
+        const bool big = fp32 ? (size_t)q * h->Lpad * 4 > kClusterFieldBytes
+                              : (size_t)q * h->Lpad * 8 > kClusterFieldBytes8;
         const bool fits_gpu = (long long)R * C <= (long long)std::max(1, device_sm_count());
-        if (o.sweep_variant == 5 || (C && (!j.h_smem || (fp32 && big && fits_gpu)))) {
+        if (o.sweep_variant == 5 || (C && (!j.h_smem || (big && fits_gpu)))) {
             if (!C) {
                 potts_lr_destroy(h);
                 return fail(POTTS_LR_EINVAL, "the cluster sweep holds at most 8 x %zu bytes of fields and spins",
@@ -578,14 +582,21 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
             h->cl_min = C;
             h->cl_auto = o.sweep_variant == 0;
             // FP64 and FX64 chosen automatically: a larger cluster while the
-            // job's CTAs still fit four per SM.  A hot slot's rank-1 updates
-            // (8-byte adds) then spread over more SMs; they set the sweep's
-            // length on a ladder with slots above the transition (measured at
-            // equilibrium, L = 4096, q = 8, R = 128: FP64 4.78 ms per sweep
-            // with 2 CTAs, 2.69 with 4, 3.65 with 8; FX64 1.82, 1.49, 3.32;
-            // L = 16384, q = 5, R = 64, FP64: 34.9 ms with 4, 29.5 with 8).
+            // job's CTAs still fit four per SM and each CTA keeps at least
+            // C * 128 sites.  A hot slot's rank-1 updates (8-byte adds) then
+            // spread over more SMs; they set the sweep's length on a ladder
+            // with slots above the transition, against a per-block cost of the
+            // cluster (flip lists to C CTAs, one cluster barrier) that does
+            // not shrink with C.  Measured at equilibrium, FP64 (ms per sweep,
+            // C = 2 / 4 / 8): L = 1024, q = 8, R = 64 0.437 / 0.417 / 0.790;
+            // L = 2048, q = 5 1.28 / 0.851 / 1.32; L = 4096, q = 5 4.20 /
+            // 2.36 / 2.65; L = 8192, q = 3 14.7 / 7.99 / 5.37; L = 4096, q = 8,
+            // R = 128 4.78 / 2.69 / 3.65 (FX64 1.82 / 1.49 / 3.32); L = 16384,
+            // q = 5, R = 64 - / 34.9 / 29.5.
             if (h->cl_auto && !fp32)
-                while (j.cl < 8 && (long long)R * 2 * j.cl <= 4LL * std::max(1, device_sm_count())) j.cl *= 2;
+                while (j.cl < 8 && (long long)R * 2 * j.cl <= 4LL * std::max(1, device_sm_count()) &&
+                       4 * j.cl * j.cl * 128 <= L)
+                    j.cl *= 2;
             h->sweep_smem = cluster_sweep_smem(L, q, j.cl, h->precision);
         }
     }
@@ -1035,14 +1046,17 @@ int potts_lr_batch_create(potts_lr_t* const* jobs, int n, void* cuda_stream, pot
     // cluster sweep automatically although their fields fit one CTA's shared
     // memory sweep with one CTA per slot (measured: about even per SM, and
     // fewer CTAs; identical results either way), and automatic clusters larger
-    // than their fields need go back to the smallest.
+    // than their fields need go back to the smallest.  8-byte fields, whose
+    // clusters serve to spread the hot slots' updates, do so from four slots
+    // per SM on: there every SM already holds a share of the hot slots.
     long long total_slots = 0;
     for (int i = 0; i < n; ++i) total_slots += jobs[i]->R;
-    const bool crowded = total_slots > 16LL * std::max(1, device_sm_count());
+    const long long nsm_b = std::max(1, device_sm_count());
     for (int i = 0; i < n; ++i) {
         hjobs[i] = jobs[i]->hj;
         int key = variant_key(jobs[i]);
         size_t sm = jobs[i]->sweep_smem;
+        const bool crowded = total_slots > (jobs[i]->precision == POTTS_LR_FP32 ? 16 : 4) * nsm_b;
         if (crowded && jobs[i]->cl_auto && jobs[i]->hj.h_smem) {
             hjobs[i].cl = 0;
             key = jobs[i]->precision * 4 + 2 + jobs[i]->hj.j_smem;

@@ -10,6 +10,8 @@ cases:
   precision_fp32  L=4096 q=8 R=128, FP32 (register-resident sweep), 3 sweeps
   precision_fp64  L=4096 q=8 R=128, FP64 fields shared by two-CTA clusters, 3 sweeps
   precision_fx64  L=4096 q=8 R=128, FX64 fields shared by two-CTA clusters, 3 sweeps
+  precision_fp64_eq  the same FP64 job with its automatic cluster size (four CTAs on 152 SMs):
+                200 sweeps + exchanges to equilibrate, then 2 more
   rebuild_fp32  L=4096 q=8 R=128, FP32: 3 tensor-core field rebuilds + measurements
   rebuild_fp32_long  L=16384 q=5 R=64, FP32: 3 tensor-core field rebuilds + measurements
   long_fp32     one job L=16384 q=5 R=64, FP32, fields in global memory (memory kernel), 3 sweeps
@@ -36,6 +38,17 @@ def main(argv):
     elif case in ("precision_fp32", "precision_fp64", "precision_fx64"):
         prec = case[-4:]
         specs, nsw = [workloads.precision_job(prec)], 3
+        if prec != "fp32":
+            variant = "cluster"
+    elif case == "precision_fp64_eq":
+        s = workloads.precision_job("fp64")
+        j = plr.Job(s.L, s.q, s.sigma, s.ratios * plr.jtot(s.L, s.sigma), s.seed, precision="fp64")
+        for _ in range(202):
+            j.sweep(1)
+            j.exchange()
+        j.sync()
+        print("ok", case, j.sweep_info()["cluster"])
+        return 0
     elif case in ("long_fp32", "long_fp32_cluster", "long_fp32_rcluster"):
         from paper_1308_5426_gb300.workloads import geometric_ratios
         L, q = 16384, 5

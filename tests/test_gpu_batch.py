@@ -201,3 +201,32 @@ def test_crowded_batch_takes_the_smallest_automatic_cluster(plr):
     b.close()
     for j in [alone, big] + small:
         j.close()
+
+
+def test_batch_of_many_slots_gives_8byte_jobs_one_cta_per_slot(plr):
+    """FP64 jobs of L = 4096, q = 5, R = 64 (160 KB of fields, which fit one
+    CTA) take a cluster alone; ten of them in one batch (640 slots, more than
+    four per SM) sweep one CTA per slot, the fields in its shared memory.
+    Spins, fields and energies equal each job run alone."""
+    import torch
+    nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    L, q, sigma, R = 4096, 5, 0.85, 64
+    n = (4 * nsm) // R + 1
+    temps = workloads.geometric_ratios(R, 0.05, 1.0) * oracle.jtot(L, sigma)
+    alone = [plr.Job(L, q, sigma, temps, 500 + i, precision="fp64") for i in range(n)]
+    assert all(j.sweep_info()["kernel"] == "cluster" for j in alone)
+    for j in alone:
+        for _ in range(2):
+            j.sweep(1)
+            j.exchange()
+    batched = [plr.Job(L, q, sigma, temps, 500 + i, precision="fp64") for i in range(n)]
+    b = plr.Batch(batched)
+    b.run(2, 2)
+    b.sync()
+    for x, y in zip(alone, batched):
+        np.testing.assert_array_equal(x.spins(), y.spins())
+        np.testing.assert_array_equal(x.fields(), y.fields())
+        np.testing.assert_array_equal(x.running_energy(), y.running_energy())
+    b.close()
+    for j in alone + batched:
+        j.close()

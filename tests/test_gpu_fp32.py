@@ -275,26 +275,29 @@ def test_cluster_sweep_equals_global_sweep(plr, precision, L, q, sigma, R, round
     b.close()
 
 
-def _spread_cluster(cmin, R):
+def _spread_cluster(cmin, R, L):
     import torch
     nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     c = cmin
-    while c < 8 and R * 2 * c <= 4 * nsm:
+    while c < 8 and R * 2 * c <= 4 * nsm and (2 * c) ** 2 * 128 <= L:
         c *= 2
     return c
 
 
 @pytest.mark.parametrize("precision,L,q,sigma,R,rounds", [
     ("fp64", 4096, 8, 0.2, 128, 3),   # the precision shape: 2 CTAs needed, 4 taken on 152 SMs
-    ("fx64", 4096, 8, 0.2, 3, 4),     # few slots: 8 CTAs
+    ("fx64", 4096, 8, 0.2, 3, 4),     # few slots: 4 CTAs (8 would keep under 128 C sites each)
     ("fp64", 10000, 7, 0.5, 2, 2),    # 4 CTAs needed, 8 taken; ragged last block
+    ("fp64", 4096, 5, 0.85, 64, 2),   # 160 KB of fields fit one CTA: a cluster all the same, 4 CTAs
 ])
 def test_automatic_cluster_spreads_8byte_fields(plr, precision, L, q, sigma, R, rounds):
-    """Chosen automatically, FP64 and FX64 fields that fit no single CTA take
-    the largest cluster of 2, 4 or 8 CTAs -- no smaller than their shares need
-    -- whose CTAs still fit four per SM, so that a hot slot's updates spread
-    over more SMs; asked for explicitly, the smallest.  Spins, fields,
-    energies and counters equal the global-memory sweep's bit for bit."""
+    """Chosen automatically, FP64 and FX64 fields of more than 64 KB take a
+    cluster while the job's smallest clusters fit the GPU at once -- the
+    largest of 2, 4 or 8 CTAs, no smaller than their shares need, whose CTAs
+    still fit four per SM and hold at least 128 C sites each -- so that a hot
+    slot's updates spread over more SMs; asked for explicitly, the smallest.
+    Spins, fields, energies and counters equal the global-memory sweep's bit
+    for bit."""
     temps = workloads.geometric_ratios(R, 0.05, 1.0) * oracle.jtot(L, sigma)
     a = plr.Job(L, q, sigma, temps, 31, precision=precision, sweep_variant="global")
     b = plr.Job(L, q, sigma, temps, 31, precision=precision)
@@ -303,7 +306,7 @@ def test_automatic_cluster_spreads_8byte_fields(plr, precision, L, q, sigma, R, 
     c.close()
     info = b.sweep_info()
     assert info["kernel"] == "cluster"
-    assert info["cluster"] == _spread_cluster(cmin, R) and info["cluster"] > cmin
+    assert info["cluster"] == _spread_cluster(cmin, R, L) and info["cluster"] > cmin
     for _ in range(rounds):
         for j in (a, b):
             j.sweep(1)
