@@ -181,17 +181,23 @@ __device__ __forceinline__ int decide_block(int lane, int nv, int k, int L, int 
     const int ab = (a << 8) | b;
     unsigned accmask = 0;  // lanes whose flip was accepted
     dmine = 0.0f;
+    // One round per accepted flip; the loop ends on an empty ballot (lanes at
+    // or past nv never vote), with no separate test of p on the round's chain.
     int p = 0;
-    while (p < nv) {
-        int st = kReject;
-        if (valid && lane >= p) {
-            if constexpr (kFP64) st = decide_fp64_filter(d32, cb32, nlu, errd);
-            else st = (d32 <= 0.0f || cb32 * d32 < nlu) ? kAccept : kReject;
+    while (true) {
+        bool vote, unsure_l = false;
+        if constexpr (kFP64) {
+            const int st = decide_fp64_filter(d32, cb32, nlu, errd);
+            vote = st != kReject;
+            unsure_l = st == kUnsure;
+        } else {
+            vote = d32 <= 0.0f || cb32 * d32 < nlu;
         }
-        const unsigned hit = __ballot_sync(kFullMask, st != kReject);
+        const bool live = valid && lane >= p;
+        const unsigned hit = __ballot_sync(kFullMask, vote && live);
         // FP64 rule: the lanes the FP32 screen left unsure, from a ballot beside
         // the first (a bit test of lane j, no shuffle on the round's chain)
-        const unsigned unsure = kFP64 ? __ballot_sync(kFullMask, st == kUnsure) : 0u;
+        const unsigned unsure = kFP64 ? __ballot_sync(kFullMask, unsure_l && live) : 0u;
         if (!hit) break;
         const int j = __ffs(hit) - 1;
         bool acc = true;
@@ -258,7 +264,7 @@ __device__ __forceinline__ int decide_block(int lane, int nv, int k, int L, int 
             // coefficient x J*, exact (a multiple of jd by -2..2), then one rounding
             const float t = (((m_ab & bj) ? jd : 0.0f) + ((m_ba & bj) ? jd : 0.0f)) -
                             (((m_aa & bj) ? jd : 0.0f) + ((m_bb & bj) ? jd : 0.0f));
-            d32 += (lane > j && valid) ? t : 0.0f;
+            d32 += (lane > j) ? t : 0.0f;  // lanes past nv: never read
         }
         p = j + 1;
     }
