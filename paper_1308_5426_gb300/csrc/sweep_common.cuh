@@ -80,6 +80,27 @@ __device__ __forceinline__ int decide_fp64_filter(float d, float cb, float nlu, 
     return kUnsure;
 }
 
+// The same screen in threshold form, fixed per lane for a block: a lane
+// accepts for sure if d <= -errd or errd <= d < dA, rejects for sure if
+// d > dR (always > errd), and is unsure otherwise, with
+//   dA = (nlu (1 - 2e-6) - cb errd - 2e-6) / (cb (1 + 2e-6)),
+//   dR = (nlu (1 + 2e-6) + cb errd + 2e-6) / (cb (1 - 2e-6)):
+// the margins of decide_fp64_filter doubled, which also covers the rounding
+// of the division (each bound is formed with a reciprocal and products that
+// move it towards the unsure band).  Within a block's scan the verdict is
+// then one compare (d <= dR) and the unsure test runs beside it.
+struct Screen {
+    float dAe;  // max(dA, errd): sure accepts below, from errd up
+    float dR;
+};
+__device__ __forceinline__ Screen fp64_screen(float cb, float nlu, float errd)
+{
+    const float r = 1.0f / cb;
+    const float dA = (nlu * (1.0f - 2e-6f) - cb * errd - 2e-6f) * r * (1.0f - 2e-6f);
+    const float dR = (nlu * (1.0f + 2e-6f) + cb * errd + 2e-6f) * r * (1.0f + 2e-6f);
+    return Screen{fmaxf(dA, errd), dR};
+}
+
 // Proposal of site k of slot t at sweep n: b uniform over the other q-1 states
 // and nlu = -ln u in FP32.  (ux1, ux2) are the words u is made of: FP64 mode's
 // u = ((ux1:ux2 >> 11) + 1) 2^-53 is formed only when the exact rule runs; its
@@ -183,13 +204,14 @@ __device__ __forceinline__ int decide_block(int lane, int nv, int k, int L, int 
     dmine = 0.0f;
     // One round per accepted flip; the loop ends on an empty ballot (lanes at
     // or past nv never vote), with no separate test of p on the round's chain.
+    Screen scr{0.0f, 0.0f};
+    if constexpr (kFP64) scr = fp64_screen(cb32, nlu, errd);
     int p = 0;
     while (true) {
         bool vote, unsure_l = false;
         if constexpr (kFP64) {
-            const int st = decide_fp64_filter(d32, cb32, nlu, errd);
-            vote = st != kReject;
-            unsure_l = st == kUnsure;
+            vote = d32 <= scr.dR;
+            unsure_l = (d32 > -errd && d32 < errd) || (d32 >= scr.dAe && d32 <= scr.dR);
         } else {
             vote = d32 <= 0.0f || cb32 * d32 < nlu;
         }
