@@ -159,6 +159,68 @@ __device__ __forceinline__ void state_masks(int a, int b, unsigned& m_ab, unsign
     }
 }
 
+// The FP64 rule for lane j of a block, where the FP32 screen is unsure: lane
+// j rebuilds its FP64 difference from the previous block's flips and this
+// block's accepted ones before j (written to ck, cab here), in FX64 fields
+// exactly in integers (kMode 2) or in FP64 (kMode 1).  The whole warp calls
+// it; returns the decision (bit 0, every lane) and lane j's near-tie count
+// (bit 1).
+template <int kMode>
+__device__ __noinline__ int decide_exact_lane(int lane, int j, unsigned accmask, int k, int L, int a, int b, int ab,
+                                              uint32_t ux1, uint32_t ux2, double base64, const int* pk,
+                                              const int* pab, int npend, double cb64, const double* J64, int* ck,
+                                              int* cab, long long basefx, const long long* Jfx, double fxs,
+                                              NearSink ns)
+{
+    const unsigned before = accmask & ((1u << j) - 1u);
+    if (accmask & (1u << lane)) {
+        const int pos = __popc(accmask & ((1u << lane) - 1u));
+        ck[pos] = k;
+        cab[pos] = ab;
+    }
+    __syncwarp();
+    bool dec = false;
+    unsigned long long near = 0;
+    if (lane == j) {
+        double d64;
+        const int nb = __popc(before);
+        if constexpr (kMode == 2) {
+            long long dx = basefx;
+            for (int g = 0; g < npend; ++g) {
+                const int kf = pk[g], af = pab[g] >> 8, bf = pab[g] & 255;
+                int r = k - kf;
+                r += r < 0 ? L : 0;
+                const int coef = (a == bf) - (a == af) - (b == bf) + (b == af);
+                if (coef) dx += (long long)coef * Jfx[r];
+            }
+            for (int g = 0; g < nb; ++g) {
+                const int kf = ck[g], af = cab[g] >> 8, bf = cab[g] & 255;
+                const int coef = (a == bf) - (a == af) - (b == bf) + (b == af);
+                if (coef) dx += (long long)coef * Jfx[k - kf];
+            }
+            d64 = (double)dx * fxs;
+        } else {
+            d64 = base64;
+            for (int g = 0; g < npend; ++g) {
+                const int kf = pk[g], af = pab[g] >> 8, bf = pab[g] & 255;
+                int r = k - kf;
+                r += r < 0 ? L : 0;
+                const int coef = (a == bf) - (a == af) - (b == bf) + (b == af);
+                if (coef) d64 += (double)coef * J64[r];
+            }
+            for (int g = 0; g < nb; ++g) {
+                const int kf = ck[g], af = cab[g] >> 8, bf = cab[g] & 255;
+                const int coef = (a == bf) - (a == af) - (b == bf) + (b == af);
+                if (coef) d64 += (double)coef * J64[k - kf];
+            }
+        }
+        dec = decide_fp64_exact(d64, cb64, unit53(ux1, ux2), near, ns, k);
+    }
+    const bool acc = __shfl_sync(kFullMask, dec, j);
+    __syncwarp();
+    return (acc ? 1 : 0) | (int)(near << 1);
+}
+
 template <int kMode>
 __device__ __forceinline__ int decide_block(int lane, int nv, int k, int L, int a, int b, float nlu, uint32_t ux1,
                                             uint32_t ux2, float d32, double base64, const int* pk, const int* pab,
@@ -225,53 +287,12 @@ __device__ __forceinline__ int decide_block(int lane, int nv, int k, int L, int 
         bool acc = true;
         if constexpr (kFP64) {
             if ((unsure >> j) & 1u) {
-                // rare: lane j applies the FP64 rule to the FP64 difference, rebuilt
-                // from the previous block's flips and this block's accepted ones
-                const unsigned before = accmask & ((1u << j) - 1u);
-                if (accmask & (1u << lane)) {
-                    const int pos = __popc(accmask & ((1u << lane) - 1u));
-                    ck[pos] = k;
-                    cab[pos] = ab;
-                }
-                __syncwarp();
-                bool dec = false;
-                if (lane == j) {
-                    double d64;
-                    const int nb = __popc(before);
-                    if constexpr (kMode == 2) {
-                        long long dx = basefx;
-                        for (int g = 0; g < npend; ++g) {
-                            const int kf = pk[g], af = pab[g] >> 8, bf = pab[g] & 255;
-                            int r = k - kf;
-                            r += r < 0 ? L : 0;
-                            const int coef = (a == bf) - (a == af) - (b == bf) + (b == af);
-                            if (coef) dx += (long long)coef * Jfx[r];
-                        }
-                        for (int g = 0; g < nb; ++g) {
-                            const int kf = ck[g], af = cab[g] >> 8, bf = cab[g] & 255;
-                            const int coef = (a == bf) - (a == af) - (b == bf) + (b == af);
-                            if (coef) dx += (long long)coef * Jfx[k - kf];
-                        }
-                        d64 = (double)dx * fxs;
-                    } else {
-                        d64 = base64;
-                        for (int g = 0; g < npend; ++g) {
-                            const int kf = pk[g], af = pab[g] >> 8, bf = pab[g] & 255;
-                            int r = k - kf;
-                            r += r < 0 ? L : 0;
-                            const int coef = (a == bf) - (a == af) - (b == bf) + (b == af);
-                            if (coef) d64 += (double)coef * J64[r];
-                        }
-                        for (int g = 0; g < nb; ++g) {
-                            const int kf = ck[g], af = cab[g] >> 8, bf = cab[g] & 255;
-                            const int coef = (a == bf) - (a == af) - (b == bf) + (b == af);
-                            if (coef) d64 += (double)coef * J64[k - kf];
-                        }
-                    }
-                    dec = decide_fp64_exact(d64, cb64, unit53(ux1, ux2), nnear, ns, k);
-                }
-                acc = __shfl_sync(kFullMask, dec, j);
-                __syncwarp();
+                // rare: lane j applies the FP64 rule to the FP64 difference (out of
+                // line, so that the common round carries none of its code)
+                const int r = decide_exact_lane<kMode>(lane, j, accmask, k, L, a, b, ab, ux1, ux2, base64, pk, pab,
+                                                       npend, cb64, J64, ck, cab, basefx, Jfx, fxs, ns);
+                acc = r & 1;
+                nnear += (unsigned long long)(r >> 1);
             }
         }
         if (acc) {
