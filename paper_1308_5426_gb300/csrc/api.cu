@@ -616,6 +616,7 @@ int potts_lr_create(int L, int q, double sigma, const double* temps, int R, uint
     j.random_sites = o.site_order;
     if (o.sweep_variant == 4 || o.site_order == 1) {
         h->direct = true;
+        h->cl_auto = false;  // the direct sweep keeps its kernel in every batch
         h->sweep_smem = direct_sweep_smem_bytes(L, h->Lpad);
         if (h->sweep_smem > kSmemBudget) {
             potts_lr_destroy(h);
@@ -1056,7 +1057,8 @@ int potts_lr_batch_create(potts_lr_t* const* jobs, int n, void* cuda_stream, pot
         hjobs[i] = jobs[i]->hj;
         int key = variant_key(jobs[i]);
         size_t sm = jobs[i]->sweep_smem;
-        const bool crowded = total_slots > (jobs[i]->precision == POTTS_LR_FP32 ? 16 : 4) * nsm_b;
+        const bool crowded =
+            !jobs[i]->direct && total_slots > (jobs[i]->precision == POTTS_LR_FP32 ? 16 : 4) * nsm_b;
         if (crowded && jobs[i]->cl_auto && jobs[i]->hj.h_smem) {
             hjobs[i].cl = 0;
             key = jobs[i]->precision * 4 + 2 + jobs[i]->hj.j_smem;

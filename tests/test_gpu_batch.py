@@ -230,3 +230,31 @@ def test_batch_of_many_slots_gives_8byte_jobs_one_cta_per_slot(plr):
     b.close()
     for j in alone + batched:
         j.close()
+
+
+def test_random_site_job_keeps_the_direct_sweep_in_a_batch_of_many_slots(plr):
+    """An FP64 job with random site order (the direct sweep) whose fields would
+    take a cluster (L = 2048, q = 5: 80 KB) keeps the direct sweep inside a
+    batch of more than four slots per SM; its spins and energies equal the job
+    run alone."""
+    import torch
+    nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    L, q, sigma, R = 2048, 5, 0.5, 64
+    temps = workloads.geometric_ratios(R, 0.05, 1.0) * oracle.jtot(L, sigma)
+    alone = plr.Job(L, q, sigma, temps, 61, precision="fp64", site_order="random")
+    assert alone.sweep_info()["kernel"] == "direct"
+    for _ in range(2):
+        alone.sweep(1)
+        alone.exchange()
+    nsmall = (4 * nsm) // 64 + 1
+    small_temps = workloads.geometric_ratios(64, 0.05, 1.0) * oracle.jtot(64, 0.5)
+    small = [plr.Job(64, 2, 0.5, small_temps, 700 + i, precision="fp64") for i in range(nsmall)]
+    job = plr.Job(L, q, sigma, temps, 61, precision="fp64", site_order="random")
+    b = plr.Batch([job] + small)
+    b.run(2, 2)
+    b.sync()
+    np.testing.assert_array_equal(alone.spins(), job.spins())
+    np.testing.assert_array_equal(alone.running_energy(), job.running_energy())
+    b.close()
+    for j in [alone, job] + small:
+        j.close()
