@@ -1,5 +1,6 @@
 """Autotuner of the sweep kernel's shape: for a job shape (L, q, precision) it
-times every sweep variant that can hold it -- fields in shared memory, in
+times the library's automatic choice and every sweep variant that can hold
+it -- fields in shared memory, in
 global memory, in the shared memory of a cluster of CTAs, in the registers of
 a cluster (FP32 and FX64), and each single-CTA register configuration (E sites
 per update thread x update warps; FP32 and FX64) --
@@ -25,13 +26,15 @@ _cache = {}
 
 def candidates(L, q, precision):
     """Variant names that might hold a job of this shape (the library refuses
-    those that do not; the tuner skips them)."""
+    those that do not; the tuner skips them).  "auto" comes first: the
+    library's own choice, which can also size a cluster beyond what its fields
+    need (a cluster asked for by name keeps the smallest size)."""
     regs = [v for v in SWEEP_VARIANTS if v.startswith("registers") and v != "registers"]
     if precision == "fp64":
-        return ["memory", "global", "cluster"]
+        return ["auto", "memory", "global", "cluster"]
     if precision == "fx64":
-        return ["memory", "global", "cluster", "rcluster"] + regs[:6]  # FX64 register configurations 1..6
-    return ["memory", "global", "cluster", "rcluster"] + regs
+        return ["auto", "memory", "global", "cluster", "rcluster"] + regs[:6]  # FX64 register configurations 1..6
+    return ["auto", "memory", "global", "cluster", "rcluster"] + regs
 
 
 def _time_variant(L, q, sigma, temps, variant, precision, sweeps, warm, torch):

@@ -19,10 +19,11 @@ def test_variant_codes():
 
 
 def test_candidates():
-    assert candidates(1000, 5, "fp64") == ["memory", "global", "cluster"]
+    assert candidates(1000, 5, "fp64") == ["auto", "memory", "global", "cluster"]
     c = candidates(1000, 5, "fp32")
-    assert c[:4] == ["memory", "global", "cluster", "rcluster"] and c[4:] == ["registers%d" % k for k in range(1, 9)]
-    assert candidates(1000, 5, "fx64") == ["memory", "global", "cluster", "rcluster"] + [
+    assert c[:5] == ["auto", "memory", "global", "cluster", "rcluster"]
+    assert c[5:] == ["registers%d" % k for k in range(1, 9)]
+    assert candidates(1000, 5, "fx64") == ["auto", "memory", "global", "cluster", "rcluster"] + [
         "registers%d" % k for k in range(1, 7)]
 
 
