@@ -112,9 +112,15 @@ typedef struct {
                             the shared memory of a cluster of 2, 4 or 8 CTAs (the
                             smallest that holds them; EINVAL if 8 do not; chosen by 0
                             where the fields fit no registers and fit no single
-                            CTA's shared memory, and in FP32 mode also where they
-                            take more than 88 KB of it with R x C at most the SM
-                            count); FP32 and FX64 modes: 6 = the slot's fields in the
+                            CTA's shared memory, and also where they take more than
+                            88 KB of it (FP32) or more than 64 KB (FP64, FX64) with
+                            R x C at most the SM count; chosen by 0 in FP64 and FX64
+                            modes, C is then the largest of 2, 4, 8 with R x C at
+                            most 4 x the SM count and C^2 <= L / 128, at least the
+                            smallest that holds them; a batch with more than 16
+                            (FP32) or 4 (FP64, FX64) slots per SM gives such jobs the
+                            smallest C, or one CTA per slot where the fields fit one
+                            CTA); FP32 and FX64 modes: 6 = the slot's fields in the
                             registers of a cluster of 2, 4 or 8 CTAs (FP32: q <= 8, L <=
                             4320 C, or q <= 12, L <= 2400 C; FX64: q <= 7, L <= 2400 C;
                             the smallest C that holds them; EINVAL beyond L = 34560 or
